@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark: dual-pair solves/s of recycling BiCG on a sequence of slowly changing systems.
+
+Workload (default): 2-D convection-diffusion, 512 x 512 interior grid (n = 262144, nnz =
+1308672), 20 dual pairs whose convection (10, 10) drifts 1 % per pair, b and bt ~ N(0, 1),
+recycle dimension k = 20, cycle length s = 40, relative tolerance 1e-8, FP64 RBiCG.  One step =
+the whole sequence solved from an empty recycle space (all hot-path steps: system start,
+initial projection, iterations, cycle refreshes, final correction).  The FP32-refined form,
+plain BiCG and an end-to-end (host buffers) pass are reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints ONE JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "dual-pair solves/s at rel.res 1e-8, chosen vs plain FP64; HBM GB/s; p99 ms"
+WORKLOAD = "convdiff2d-512x512-seq20-k20"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=512)
+    ap.add_argument("--pairs", type=int, default=20)
+    ap.add_argument("--k", type=int, default=20)
+    ap.add_argument("--s", type=int, default=40)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP32-refined, BiCG and e2e passes")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_sequence(a):
+    from paper_1010_0762_gb300 import inputs as I
+    return I.convdiff_sequence(a.grid, [10.0, 10.0], a.pairs, 0.01, 2000, bt_kind="normal")
+
+
+# ------------------------------------------------------------------ clocks sampling
+class Clocks:
+    def __init__(self):
+        self.samples = []
+        self.stop = threading.Event()
+        self.t = None
+
+    def start(self):
+        def run():
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            try:
+                p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "200"],
+                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except OSError:
+                return
+            while not self.stop.is_set():
+                line = p.stdout.readline()
+                if not line:
+                    break
+                self.samples.append([v.strip() for v in line.split(",")])
+            p.terminate()
+        self.t = threading.Thread(target=run, daemon=True)
+        self.t.start()
+
+    def finish(self):
+        self.stop.set()
+        if self.t:
+            self.t.join(timeout=3)
+        dev = os.environ.get("LOCAL_RANK", "0")
+        rows = [s for s in self.samples if s and s[0] == dev] or self.samples
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def algorithmic_phase1(n, nnz, k, w=8):
+    """Algorithmic flops and bytes of one phase-1 launch (dual SpMV with on-the-fly p update and
+    the 2k projection dots) for real FP64, one A read (values + indices, A^H uses the same
+    entries), vectors r, p_old, rt, pt_old read and p, pt, z, zt written, C and Ct read."""
+    flops = 4 * nnz + 4 * n + 4 * k * n
+    bytes_ = nnz * (w + 4) + 4 * (n + 1) + 8 * n * w + 2 * k * n * w
+    return flops, bytes_
+
+
+def measure_dgemm_tflops(torch):
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        torch.mm(a, b)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    reps = 3
+    for _ in range(reps):
+        torch.mm(a, b)
+    e1.record()
+    torch.cuda.synchronize()
+    return 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+
+def run_sequence(R, torch, S, ops, bs, bts, xs, xts, results=None):
+    S.reset()
+    for j in range(len(ops)):
+        xs[j].zero_()
+        xts[j].zero_()
+        r = S.solve_pair(ops[j], bs[j], bts[j], xs[j], xts[j])
+        if results is not None:
+            results.append(r)
+
+
+def flush_l2(torch, buf):
+    buf.fill_(1.0)
+
+
+def gpu_arm(a):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1010_0762_gb300 import rbicg as R
+
+    seq = make_sequence(a)
+    n = seq[0]["A"].n
+    nnz = seq[0]["A"].nnz
+    # inputs resident in HBM: one pattern, per-pair values and right-hand sides
+    rp = torch.as_tensor(seq[0]["A"].row_ptr, device="cuda")
+    ci = torch.as_tensor(seq[0]["A"].col_idx, device="cuda")
+    ops = [R.Operator(rp, ci, torch.as_tensor(p["A"].val, device="cuda")) for p in seq]
+    bs = [torch.as_tensor(p["b"], device="cuda") for p in seq]
+    bts = [torch.as_tensor(p["bt"], device="cuda") for p in seq]
+    xs = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in seq]
+    xts = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in seq]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def timed(S, steps, warmup, profile=False):
+        for _ in range(warmup):
+            run_sequence(R, torch, S, ops, bs, bts, xs, xts)
+        results = []
+        clocks = Clocks()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = S.launch_count()
+        if profile:
+            R.lib.rbicg_profile(S.h, 1, None, None)
+        clocks.start()
+        total_ms = 0.0
+        for _ in range(steps):
+            flush_l2(torch, flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run_sequence(R, torch, S, ops, bs, bts, xs, xts, results)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+        ck = clocks.finish()
+        prof = None
+        if profile:
+            import ctypes as C
+            ms = (C.c_double * 8)()
+            cnt = (C.c_int64 * 8)()
+            R.lib.rbicg_profile(S.h, 0, ms, cnt)
+            prof = (list(ms), list(cnt))
+        launches = S.launch_count() - l0
+        if world > 1:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return total_ms, results, ck, prof, launches
+
+    # --- plain FP64 RBiCG (the configuration's own form) ---
+    S = R.Solver(n, k=a.k, s=a.s, tol=a.tol)
+    ms64, res64, clocks, prof, launches = timed(S, a.steps, a.warmup, profile=True)
+    pairs_done = a.pairs * a.steps
+    value = world * pairs_done / (ms64 * 1e-3)
+    per_step = res64[:a.pairs]
+    iters = [r["iters"] for r in per_step]
+    ok = all(r["status"] in (R.OK, R.RECYCLE_EMPTY) for r in res64)
+    worst_true = max(max(r["true_relres"], r["true_relres_dual"]) for r in res64)
+    kcs = [r["recycle_dim"] for r in per_step]
+
+    # roofline of the dominant kernel (phase 1: dual SpMV + projections) from live CUDA events
+    names = ["dual_spmv_project", "q_and_pq", "update_dots", "refresh_gram", "refresh_eig",
+             "refresh_basis", "system_start", "init_finish_adjoint"]
+    ms_slots, cnt_slots = prof
+    dom = int(np.argmax(ms_slots))
+    fl_tot = by_tot = 0.0
+    for r in res64:
+        f, b_ = algorithmic_phase1(n, nnz, r["recycle_dim"])
+        fl_tot += f * r["iters"]
+        by_tot += b_ * r["iters"]
+    t1 = ms_slots[0] * 1e-3
+    dgemm = measure_dgemm_tflops(torch)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    ach_tf = fl_tot / t1 / 1e12 if t1 > 0 else 0.0
+    ach_gbs = by_tot / t1 / 1e9 if t1 > 0 else 0.0
+    alu_frac = ach_tf / dgemm if dgemm > 0 else None
+    hbm_frac = ach_gbs / hbm_peak
+    bound = "alu" if alu_frac is not None and alu_frac >= hbm_frac else "hbm"
+    launches_phase1 = cnt_slots[0]
+    roofline = {
+        "kernel": "k_phase1 (dual SpMV + p update + Ct^H z, C^H zt)",
+        "bound": bound,
+        "achieved": round(ach_tf if bound == "alu" else ach_gbs, 4),
+        "peak": round(dgemm if bound == "alu" else hbm_peak, 4),
+        "unit": "TFLOP/s" if bound == "alu" else "GB/s",
+        "frac": round(alu_frac if bound == "alu" else hbm_frac, 4),
+        "peak_source": ("FP64 DGEMM measured live in this run (torch.mm 4096^3)" if bound == "alu"
+                        else "MEASURED_PEAKS.json hbm_gbs (of measured)"),
+        "traffic": None,
+        "hbm_view": {"achieved_gbs": round(ach_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_frac, 4)},
+        "alu_view": {"achieved_tflops": round(ach_tf, 4), "peak_tflops": round(dgemm, 4),
+                     "frac": round(alu_frac, 4) if alu_frac else None},
+        "avg_launch_us": round(ms_slots[0] * 1e3 / max(1, launches_phase1), 2),
+        "launches": int(launches_phase1),
+        "step_share": {names[i]: round(ms_slots[i] / max(1e-9, sum(ms_slots)), 4) for i in range(8)},
+        "dominant_slot": names[dom],
+    }
+
+    out = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": round(ms64 / a.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded convection-diffusion sequence; see DESIGN.md input recipe)",
+        "config": {"workload": WORKLOAD, "grid": a.grid, "n": n, "nnz": nnz, "pairs": a.pairs, "k": a.k,
+                   "s": a.s, "tol": a.tol, "drift": 0.01, "form": "plain FP64 RBiCG",
+                   "l2": "256 MB flush between steps; working set > L2", "parallelism": "replicas"},
+        "iters_per_pair": iters,
+        "recycle_dim_per_pair": kcs,
+        "all_converged": ok,
+        "worst_true_relres": worst_true,
+        "roofline": roofline,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+
+    if not a.no_extras:
+        # --- chosen form: FP64 iterative refinement around FP32 inner RBiCG ---
+        S32 = R.Solver(n, k=a.k, s=a.s, tol=a.tol, precision="fp32_refined", inner_tol=1e-5)
+        ms32, res32, _, _, _ = timed(S32, a.steps, 1)
+        out["chosen"] = {"form": "fp32_refined (FP32 inner RBiCG, FP64 residual refinement)",
+                         "value": round(world * pairs_done / (ms32 * 1e-3), 4), "unit": "solves/s",
+                         "ms_per_step": round(ms32 / a.steps, 3),
+                         "iters_per_pair": [r["iters"] for r in res32[:a.pairs]],
+                         "refine_steps": [r["refine_steps"] for r in res32[:a.pairs]],
+                         "all_converged": all(r["status"] == R.OK for r in res32),
+                         "worst_true_relres": max(max(r["true_relres"], r["true_relres_dual"]) for r in res32)}
+        # --- non-recycling BiCG on the same sequence ---
+        Sb = R.Solver(n, k=a.k, s=a.s, tol=a.tol, recycle=0)
+        msb, resb, _, _, _ = timed(Sb, 1, 1)
+        out["bicg"] = {"value": round(world * a.pairs / (msb * 1e-3), 4), "unit": "solves/s",
+                       "iters_per_pair": [r["iters"] for r in resb[:a.pairs]]}
+        # --- end to end through the C ABI with host buffers (H2D inputs, D2H solutions) ---
+        hvals = [torch.as_tensor(p["A"].val).pin_memory() for p in seq]
+        hb = [torch.as_tensor(p["b"]).pin_memory() for p in seq]
+        hbt = [torch.as_tensor(p["bt"]).pin_memory() for p in seq]
+        hrp = torch.as_tensor(seq[0]["A"].row_ptr).pin_memory()
+        hci = torch.as_tensor(seq[0]["A"].col_idx).pin_memory()
+        hx = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in seq]
+        hxt = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in seq]
+        dvals = [torch.empty_like(o.val) for o in ops]
+        drp, dci = torch.empty_like(rp), torch.empty_like(ci)
+        Se = R.Solver(n, k=a.k, s=a.s, tol=a.tol)
+        e_steps = max(1, a.steps // 2)
+        h2d = d2h = 0
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e_steps):
+            Se.reset()
+            drp.copy_(hrp, non_blocking=True)
+            dci.copy_(hci, non_blocking=True)
+            h2d += hrp.numel() * 4 + hci.numel() * 4
+            for j in range(a.pairs):
+                dvals[j].copy_(hvals[j], non_blocking=True)
+                bs[j].copy_(hb[j], non_blocking=True)
+                bts[j].copy_(hbt[j], non_blocking=True)
+                xs[j].zero_()
+                xts[j].zero_()
+                h2d += (hvals[j].numel() + 2 * n) * 8
+                op = R.Operator(drp, dci, dvals[j])
+                Se.solve_pair(op, bs[j], bts[j], xs[j], xts[j])
+                hx[j].copy_(xs[j], non_blocking=True)
+                hxt[j].copy_(xts[j], non_blocking=True)
+                d2h += 2 * n * 8
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mse = e0.elapsed_time(e1)
+        out["e2e"] = {"value": round(world * a.pairs * e_steps / (mse * 1e-3), 4), "unit": "solves/s",
+                      "h2d_bytes_per_step": int(h2d // e_steps), "d2h_bytes_per_step": int(d2h // e_steps),
+                      "steps": e_steps}
+
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(seq, a, float(np.mean(iters)))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+# ------------------------------------------------------------------ oracle (CPU) timing
+def oracle_sample(seq, a, pair, max_itn):
+    from oracle import rbicg_oracle as O
+    pr = seq[pair]
+    n = pr["A"].n
+    t = time.perf_counter()
+    r = O.rbicg_pair(pr["A"], pr["b"], pr["bt"], np.zeros(n), np.zeros(n), None, k=a.k, s=a.s, tol=a.tol,
+                     max_itn=max_itn)
+    return time.perf_counter() - t, r.iters
+
+
+def cpu_baseline(seq, a, mean_iters):
+    its = 4 * a.s
+    sec, done = oracle_sample(seq, a, 0, its)
+    per_it = sec / max(1, done)
+    return {"value": round(1.0 / (per_it * mean_iters), 6), "unit": "solves/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": "oracle RBiCG (numpy/scipy FP64) on pair 0 for %d iterations (%d cycles), %.1f s; "
+                      "solves/s = 1 / (seconds per iteration x %.0f, the mean GPU iterations per pair)"
+                      % (done, done // a.s, sec, mean_iters)}
+
+
+def reference_arm(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    seq = make_sequence(a)
+    # iterations per full solve of pair 0, from one complete oracle solve (not timed)
+    from oracle import rbicg_oracle as O
+    pr = seq[0]
+    n = pr["A"].n
+    full = O.rbicg_pair(pr["A"], pr["b"], pr["bt"], np.zeros(n), np.zeros(n), None, k=a.k, s=a.s, tol=a.tol)
+    n_ref = full.iters
+    its = 2 * a.s
+    for i in range(a.warmup):
+        oracle_sample(seq, a, i % a.pairs, its)
+    tot = 0.0
+    done = 0
+    for i in range(a.steps):
+        sec, d = oracle_sample(seq, a, i % a.pairs, its)
+        tot += sec
+        done += d
+    per_it = tot / max(1, done)
+    value = 1.0 / (per_it * n_ref)
+    cpu = {"value": round(value, 6), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "each step: oracle RBiCG on one pair for %d iterations; solves/s = 1 / (seconds per "
+                     "iteration x %d, the oracle's own iteration count for a full solve of pair 0)" % (its, n_ref)}
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": 0,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(1e3 * tot / max(1, a.steps), 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "grid": a.grid, "pairs": a.pairs, "k": a.k,
+                                           "s": a.s, "tol": a.tol},
+           "cpu_baseline": cpu, "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)

@@ -1,0 +1,225 @@
+/*
+ * rbicg.h -- C ABI of the GB300 recycling-BiCG library (librbicg.so).
+ *
+ * Method: Ahuja, de Sturler, Gugercin, Chang, "Recycling BiCG with an application to model
+ * reduction" (arXiv:1010.0762).  The library solves a sequence of slowly changing dual
+ * sparse systems (Section 1, eq. (initialSys))
+ *
+ *        A^(j) x^(j) = b^(j),        A^(j)^H xt^(j) = bt^(j),        j = 1, 2, ...
+ *
+ * with RBiCG (Algorithm 2), carrying a recycle space U, Ut from one pair to the next and
+ * refreshing it every s iterations from harmonic Ritz vectors (Section 4).
+ *
+ * Conventions shared by every entry point:
+ *  - All vector / matrix pointers are DEVICE pointers unless a name ends in _host.  The
+ *    caller owns them; the library never frees or retains them past the call, except the
+ *    matrix handed to rbicg_update_recycle / rbicg_solve_pair, which must stay valid and
+ *    unchanged until the next call that passes a matrix (the library reads it during each
+ *    solve).
+ *  - Real values are IEEE double (or float where a name says f32); complex values are two
+ *    doubles (re, im) interleaved.
+ *  - CSR matrices use int32 row_ptr[n+1] and col_idx[nnz] with row_ptr[0] = 0, row_ptr[n] =
+ *    nnz, and strictly increasing column indices within each row (checked on the device;
+ *    RBICG_ERR_ARG otherwise).
+ *  - Inner product (a, b) = a^H b (the paper's "standard inner product", Section 1).
+ *  - A handle is bound to one CUDA stream given at creation; all work is queued on it.
+ *    A handle is not thread-safe.  Calls block until their result is on the host.
+ *  - Return value: RBICG_OK (0); a positive status when the solve ended without meeting
+ *    the tolerance (x then holds the last iterate); a negative status for an error, in
+ *    which case outputs are unspecified and rbicg_last_error() describes it.  No call
+ *    traps, aborts or exits; device-side waits are bounded.
+ */
+#ifndef RBICG_H
+#define RBICG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RBICG_OK = 0,
+  RBICG_NOT_CONVERGED = 1,   /* max_itn reached (Algorithm 2 step 5 bound) */
+  RBICG_BREAKDOWN_RHO = 2,   /* |(rt_i, r_i)| <= 1e-14 ||rt_i|| ||r_i|| (Section 2, serious breakdown) */
+  RBICG_BREAKDOWN_PQ = 3,    /* |(pt_i, q_i)| <= 1e-14 ||pt_i|| ||q_i|| (Section 2, second kind) */
+  RBICG_RECYCLE_EMPTY = 4,   /* solve converged, but Section 4.3 truncation left p = 0 columns */
+  RBICG_ERR_ARG = -1,        /* invalid argument (sizes, null pointers, malformed CSR) */
+  RBICG_ERR_OOM = -2,        /* device allocation failed */
+  RBICG_ERR_CUDA = -3,       /* a CUDA call failed */
+  RBICG_ERR_TIMEOUT = -4,    /* a bounded device-side wait gave up */
+  RBICG_ERR_NONFINITE = -5,  /* a non-finite scalar appeared in the iteration */
+  RBICG_ERR_EIG = -6         /* the small dense eigen / SVD solve did not converge */
+} rbicg_status;
+
+typedef enum {
+  RBICG_R64 = 0,   /* real double vectors and operator */
+  RBICG_C128 = 1   /* complex double vectors (operator real or complex, see rbicg_csr) */
+} rbicg_dtype;
+
+typedef enum {
+  RBICG_FP64 = 0,          /* every step in the vector dtype (FP64) */
+  RBICG_FP32_REFINED = 1   /* FP64 iterative refinement around FP32 inner RBiCG solves */
+} rbicg_precision;
+
+/* Solver parameters.  Defaults (rbicg_default_params): k = 10, s = 40, max_itn = 20000,
+ * tol = 1e-8, svd_tol = 1e-6, inner_tol = 1e-5, refine_max = 12, precision = FP64,
+ * seed = 0, setup_fp32 = 1, recycle = 1, inner_svd_tol = 1e-3. */
+typedef struct {
+  int k;                   /* recycle dimension: columns kept in U, Ut (Section 3, 4.1); 1..32 */
+  int s;                   /* cycle length (Section 4.1); 2..64, k + s <= 80 */
+  int max_itn;             /* iteration bound of Algorithm 2 step 5 (per inner solve) */
+  double tol;              /* relative residual: ||r|| <= tol ||b|| and ||rt|| <= tol ||bt|| */
+  double svd_tol;          /* truncation of Section 4.3 after unit-norm column scaling */
+  double inner_tol;        /* FP32_REFINED: relative tolerance of each inner solve */
+  int refine_max;          /* FP32_REFINED: bound on outer refinement steps */
+  rbicg_precision precision;
+  uint64_t seed;           /* Philox4x32-10 key for the random restart of Algorithm 2 step 3 */
+  int setup_fp32;          /* 1: per-cycle O(n) Gram / basis products in FP32 arithmetic on
+                              the stored data (FP64 accumulation across row blocks); 0: FP64 */
+  int recycle;             /* 0: plain BiCG (no recycle space computed or used) */
+  double inner_svd_tol;    /* FP32_REFINED: Section 4.3 truncation used by the FP32 inner solver.
+                              The oblique projector C D_c^{-1} Ct^H has norm about 1/sigma_min,
+                              and FP32 rounding in q = z - C zeta grows by that factor, so the
+                              FP32 solver keeps only sigma >= max(svd_tol, inner_svd_tol) */
+} rbicg_params;
+
+/* A sparse operator.  Operator = A when has_shift == 0, (shift I - A) otherwise. */
+typedef struct {
+  int64_t n, nnz;
+  const int32_t *row_ptr;  /* device, n+1 */
+  const int32_t *col_idx;  /* device, nnz */
+  const void *val;         /* device, nnz doubles (val_complex = 0) or complex doubles (1) */
+  int val_complex;
+  int has_shift;
+  double shift_re, shift_im;
+} rbicg_csr;
+
+typedef struct {
+  int iters;               /* iterations of the (last inner) solve; summed over inner solves */
+  int cycles;              /* completed cycles (recycle-space refreshes) */
+  int recycle_dim;         /* columns of the recycle space used for this pair (p of Section 4.3) */
+  int refine_steps;        /* FP32_REFINED outer steps (0 for FP64) */
+  double relres, relres_dual;             /* recurrence residuals, relative */
+  double true_relres, true_relres_dual;   /* ||b - A x|| / ||b||, ||bt - A^H xt|| / ||bt|| in FP64 */
+  int status;              /* rbicg_status of the solve */
+} rbicg_result;
+
+typedef struct rbicg_ctx *rbicg_handle;
+
+/* Fill *p with the defaults listed above. */
+void rbicg_default_params(rbicg_params *p);
+
+/* Create a solver for systems of order n.  stream: a cudaStream_t (NULL = legacy default
+ * stream).  Allocates the device workspace for n, params->k and params->s (Section 4.1:
+ * recycle bases U, Ut, C, Ct, the per-cycle U_j, C_j and the residual ring).  Returns
+ * RBICG_ERR_ARG for invalid sizes, RBICG_ERR_OOM if the workspace does not fit. */
+rbicg_status rbicg_create(const rbicg_params *params, int64_t n, rbicg_dtype dtype,
+                          void *stream, rbicg_handle *out);
+
+/* Set the operator of the next pair and prepare the recycle space for it (Section 4.3, last
+ * paragraph): C = A U, Ct = A^H Ut, SVD Ct^H C = M Sigma N^H after unit-norm column
+ * scaling, keep sigma >= svd_tol (p columns), U <- U N_p, Ut <- Ut M_p, C <- C N_p,
+ * Ct <- Ct M_p, D_c = Sigma_p.  Also builds the library's copy of A^H (same pattern with
+ * conjugated transposed values when A is structurally symmetric, a transposed CSR
+ * otherwise).  With no recycle space yet (first pair) only the operator is set. */
+rbicg_status rbicg_update_recycle(rbicg_handle h, const rbicg_csr *A);
+
+/* Solve one dual pair with Algorithm 2.  A: the operator, or NULL to reuse the one set by
+ * the last rbicg_update_recycle / rbicg_solve_pair (a different A triggers an implicit
+ * rbicg_update_recycle).  b, bt: right-hand sides (n values each).  x, xt: in = x_{-1},
+ * xt_{-1} (initial guesses of eq. (minusXR)); out = the solutions (step 7).  bt may be all
+ * zeros (the dual test is then skipped).  Every s iterations the recycle space for the next
+ * pair is refreshed (Sections 4.1-4.3); if the pair converges in fewer than s iterations the
+ * previous space is kept (Section 6.2).  res receives counters and residuals. */
+rbicg_status rbicg_solve_pair(rbicg_handle h, const rbicg_csr *A, const void *b, const void *bt,
+                              void *x, void *xt, rbicg_result *res);
+
+/* Solve `count` independent dual pairs, one per handle, with their iterations interleaved on
+ * the first handle's stream (each handle keeps its own recycle space).  Arrays are host
+ * arrays of length count holding the per-pair arguments of rbicg_solve_pair.  Results are
+ * the same as solving each pair alone. */
+rbicg_status rbicg_solve_batch(rbicg_handle *hs, const rbicg_csr *const *As, const void *const *bs,
+                               const void *const *bts, void *const *xs, void *const *xts, int count,
+                               rbicg_result *res);
+
+/* Copy the recycle space for the next pair into caller buffers U, Ut (device, n x k row-major,
+ * k = params->k columns, unused columns zero); *p receives the number of valid columns. */
+rbicg_status rbicg_export_recycle(rbicg_handle h, void *U, void *Ut, int *p);
+
+/* Install a recycle space (device, n x p row-major, p <= k).  It is made bi-orthogonal for
+ * the operator of the next rbicg_update_recycle / rbicg_solve_pair call. */
+rbicg_status rbicg_import_recycle(rbicg_handle h, const void *U, const void *Ut, int p);
+
+/* Drop the recycle space: the next pair is solved as a first system (Algorithm 2 step 1). */
+rbicg_status rbicg_reset(rbicg_handle h);
+
+/* Free the handle and its device workspace. */
+rbicg_status rbicg_destroy(rbicg_handle h);
+
+/* Message of the last error on this handle (never NULL; "" when none).  With h == NULL,
+ * the last error of a call that had no valid handle. */
+const char *rbicg_last_error(rbicg_handle h);
+
+/* Number of kernel launches made through this handle since it was created (for timing
+ * reports). */
+int64_t rbicg_launch_count(rbicg_handle h);
+
+/* Measurement hooks (no counterpart in the paper): device time of each step of the solve,
+ * taken with CUDA events on the handle's stream.  enable = 1 starts collection (clearing the
+ * accumulators), 0 stops it, -1 only reads.  ms_out / launches_out (host arrays of
+ * RBICG_NPROF, may be NULL) receive the accumulated milliseconds and kernel launches per
+ * slot: 0 dual SpMV + projections (Algorithm 2 step 5, lines 1-3), 1 q and (pt, q),
+ * 2 x / r updates and (rt, r), 3 refresh Gram (Section 4.1), 4 refresh eigen solve
+ * (eq. (finalGenEigValue)), 5 refresh basis update and SVD (Section 4.3), 6 system start
+ * (Section 4.3 last paragraph), 7 initial projection / step 7 / A^H construction. */
+#define RBICG_NPROF 8
+rbicg_status rbicg_profile(rbicg_handle h, int enable, double *ms_out, int64_t *launches_out);
+
+/* ---------------------------------------------------------------------------------------
+ * Component entry points.  Each runs one step of the hot path on caller-provided device
+ * buffers, synchronously on `stream`, so that the step can be checked or used on its own.
+ * ------------------------------------------------------------------------------------- */
+
+/* Algorithm 2 step 5, first two lines: p = r + beta p_old, pt = rt + conj(beta) pt_old,
+ * z = Op p, zt = Op^H pt (Op = A or shift I - A), and the projections
+ * zeta = D_c^{-1} Ct^H z, zetat = D_c^{-1} C^H zt (eq. (CcheckChat): zeta = Chat^H z,
+ * zetat = Ccheck^H zt).  C, Ct: n x k row-major (ldc >= k) or NULL with k = 0; Dc: k
+ * doubles (host).  beta: (re, im) on the host.  zeta_host, zetat_host: k values each
+ * (complex when dtype is C128) written on the host.  p_out, pt_out, z, zt: n values. */
+rbicg_status rbicg_op_dual_spmv_project(const rbicg_csr *A, rbicg_dtype dtype, const void *r,
+                                        const void *rt, const void *p_old, const void *pt_old,
+                                        double beta_re, double beta_im, const void *C,
+                                        const void *Ct, int k, int ldc, const double *Dc_host,
+                                        void *p_out, void *pt_out, void *z, void *zt,
+                                        void *zeta_host, void *zetat_host, void *stream);
+
+/* Tall-skinny Gram G = X^H Y (Section 4.1 Grams Psit^H Psi, Psit^H Phi; Section 4.3
+ * Ct^H C).  X: n x mx, Y: n x my, both row-major with leading dimensions ldx, ldy; G_host:
+ * mx x my row-major on the host (complex when dtype is C128).  fp32: 1 to multiply in FP32
+ * (FP64 accumulation across row blocks), 0 for FP64. */
+rbicg_status rbicg_op_gram(rbicg_dtype dtype, int64_t n, const void *X, int mx, int ldx,
+                           const void *Y, int my, int ldy, int fp32, void *G_host, void *stream);
+
+/* Generalised eigenproblem L w = lambda R w of eq. (finalGenEigValue), order m <= 80, in
+ * FP64 on one thread block: selects the k eigenvalues closest to the origin (a conjugate
+ * pair of a real problem is kept together as real and imaginary parts, k-1 columns if the
+ * pair straddles the cut) and returns the right eigenvectors W (m x kk) and the matching
+ * left eigenvectors Wt (m x kk), column-major on the host, and the eigenvalues (complex,
+ * kk).  L, R: m x m column-major on the host.  R = NULL means the standard problem L w =
+ * lambda w (Section 4.2, first cycle).  *kk receives the number of columns. */
+rbicg_status rbicg_op_eig_select(rbicg_dtype dtype, int m, const void *L_host, const void *R_host,
+                                 int k, void *W_host, void *Wt_host, double *lam_host, int *kk,
+                                 void *stream);
+
+/* SVD S = M Sigma N^H of a k x k matrix (Section 4.3, eq. (equationSVD)) in FP64 on one
+ * thread block (one-sided Jacobi).  S, M, N: column-major on the host; sigma: k values in
+ * descending order. */
+rbicg_status rbicg_op_svd(rbicg_dtype dtype, int k, const void *S_host, void *M_host, double *sigma,
+                          void *N_host, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBICG_H */

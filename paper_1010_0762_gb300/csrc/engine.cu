@@ -1,0 +1,1228 @@
+// engine.cu -- host side of the RBiCG library: handles, the solve loop of Algorithm 2, the
+// Section 4 recycle-space refresh schedule, FP32 inner solves under FP64 refinement, and the
+// C ABI declared in include/rbicg.h.
+#include <algorithm>
+#include <cstddef>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/rbicg.h"
+#include "internal.cuh"
+
+namespace rb {
+
+static thread_local std::string g_last_error;
+
+static bool debug_on() {
+  static int v = -1;
+  if (v < 0) { const char* e = getenv("RBICG_DEBUG"); v = (e && *e && *e != '0') ? 1 : 0; }
+  return v == 1;
+}
+
+struct Err {
+  rbicg_status st;
+  std::string msg;
+};
+
+#define RB_CUDA(call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      throw Err{e_ == cudaErrorMemoryAllocation ? RBICG_ERR_OOM : RBICG_ERR_CUDA,     \
+                std::string(#call) + ": " + cudaGetErrorString(e_)};                  \
+  } while (0)
+
+template <class P>
+static P* dmalloc(size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(P));
+  if (e != cudaSuccess)
+    throw Err{e == cudaErrorMemoryAllocation ? RBICG_ERR_OOM : RBICG_ERR_CUDA,
+              std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+  return static_cast<P*>(p);
+}
+
+int64_t dense_work_elems();
+static int64_t dense_work_elems_fwd() { return dense_work_elems(); }
+
+static int kt_for(int k) {
+  if (k <= 0) return 0;
+  if (k <= 8) return 8;
+  if (k <= 16) return 16;
+  if (k <= 24) return 24;
+  return 32;
+}
+
+static int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// Host copy of the leading DevState fields (same layout), read with one copy per sync.
+struct HostView {
+  int iter, done, kc, restart, kk, pcyc, eig_status, max_itn;
+  double rnorm, rtnorm, bnorm, btnorm, true_rnorm, true_rtnorm;
+};
+static_assert(offsetof(HostView, true_rtnorm) == offsetof(DevState, true_rtnorm), "HostView layout");
+
+struct OpKey {
+  const void* rp = nullptr; const void* ci = nullptr; const void* va = nullptr;
+  int64_t n = 0, nnz = 0;
+  int has_shift = 0, val_complex = 0;
+  double sr = 0, si = 0;
+  bool operator==(const OpKey& o) const {
+    return rp == o.rp && ci == o.ci && va == o.va && n == o.n && nnz == o.nnz && has_shift == o.has_shift &&
+           val_complex == o.val_complex && sr == o.sr && si == o.si;
+  }
+};
+
+// ------------------------------------------------------------------------------------
+// Per-step device timing with CUDA events on the solver's stream (measurement hooks).
+// Slots: 0 phase 1 (dual SpMV + projections), 1 phase 2 (q, (pt, q)), 2 phase 3 (x, r
+// updates and dots), 3 refresh Gram, 4 refresh dense eigen solve, 5 refresh basis update
+// (combine, SpMM, small Gram, SVD, rotation), 6 system start, 7 init / finish / A^H.
+// ------------------------------------------------------------------------------------
+struct Profiler {
+  bool on = false;
+  double ms[RBICG_NPROF] = {};
+  int64_t cnt[RBICG_NPROF] = {};
+  std::vector<cudaEvent_t> pool;
+  struct Pend { int slot, nl; cudaEvent_t a, b; };
+  std::vector<Pend> pending;
+  cudaEvent_t get() {
+    if (pool.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  int begin(int slot, cudaStream_t s) {
+    if (!on) return -1;
+    Pend p{slot, 0, get(), get()};
+    cudaEventRecord(p.a, s);
+    pending.push_back(p);
+    return (int)pending.size() - 1;
+  }
+  void end(int idx, int nl, cudaStream_t s) {
+    if (idx < 0) return;
+    pending[idx].nl = nl;
+    cudaEventRecord(pending[idx].b, s);
+  }
+  void harvest() {   // call after a stream sync
+    for (auto& p : pending) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) { ms[p.slot] += t; cnt[p.slot] += p.nl; }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  void reset() {
+    for (int i = 0; i < RBICG_NPROF; ++i) { ms[i] = 0; cnt[i] = 0; }
+  }
+  ~Profiler() {
+    for (auto& p : pending) { pool.push_back(p.a); pool.push_back(p.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// ------------------------------------------------------------------------------------
+// Solver<V, T>: one precision of the iteration (V operator value type, T vector type)
+// ------------------------------------------------------------------------------------
+struct SolverBase {
+  virtual ~SolverBase() {}
+};
+
+template <class V, class T>
+struct Solver : SolverBase {
+  typedef typename traits<T>::acc A;
+  rbicg_params prm;
+  int64_t n;
+  int ldk, R, grid, gram_grid;
+  cudaStream_t s;
+  int64_t* launches;
+  // operator (values in V; A^H values owned here)
+  OpArgs<V> op{};
+  V* tva = nullptr;
+  int* trp_own = nullptr;
+  int* tci_own = nullptr;
+  V* va_own = nullptr;          // converted copy of A's values (inner FP32 solver)
+  int64_t nnz_cap = 0;
+  int op_ready = 0;
+  // vectors
+  T *ring = nullptr, *ringt = nullptr, *p[2] = {}, *pt[2] = {}, *z = nullptr, *zt = nullptr;
+  // recycle space of the next system (U, Ut with kU columns) and of the current system
+  T *U = nullptr, *Ut = nullptr, *C = nullptr, *Ct = nullptr;
+  T *Uc[2] = {}, *Utc[2] = {}, *Cc[2] = {}, *Ctc[2] = {};
+  int kU = 0;         // valid columns in U for the next system start
+  int kc = 0;         // columns of C in the current system
+  int pending_start = 0;
+  // device scratch
+  DevState* st = nullptr;
+  void* part = nullptr;
+  A* G = nullptr;
+  zd* work = nullptr;
+  zd *Wphi = nullptr, *Wphit = nullptr, *Nmat = nullptr, *Mmat = nullptr;
+  double* sig = nullptr;
+  int* iflag = nullptr;
+  HostView* hv = nullptr;       // pinned
+
+  Profiler* prof;
+
+  Solver(const rbicg_params& p_, int64_t n_, cudaStream_t s_, int64_t* launches_, Profiler* prof_)
+      : prm(p_), n(n_), s(s_), launches(launches_), prof(prof_) {
+    ldk = std::max(1, ((prm.k + 3) / 4) * 4);
+    R = prm.s + 2;
+    const int sms = num_sms();
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + NTHREADS - 1) / NTHREADS, (int64_t)sms * 8));
+    gram_grid = 2 * sms;
+    const int64_t ldv = ((n + 31) / 32) * 32;   // padded vector stride (256-byte aligned slots)
+    ring = dmalloc<T>(ldv * R);
+    ringt = dmalloc<T>(ldv * R);
+    for (int i = 0; i < 2; ++i) { p[i] = dmalloc<T>(n); pt[i] = dmalloc<T>(n); }
+    z = dmalloc<T>(n);
+    zt = dmalloc<T>(n);
+    const size_t bsz = (size_t)n * ldk;
+    U = dmalloc<T>(bsz); Ut = dmalloc<T>(bsz); C = dmalloc<T>(bsz); Ct = dmalloc<T>(bsz);
+    for (int i = 0; i < 2; ++i) {
+      Uc[i] = dmalloc<T>(bsz); Utc[i] = dmalloc<T>(bsz); Cc[i] = dmalloc<T>(bsz); Ctc[i] = dmalloc<T>(bsz);
+    }
+    RB_CUDA(cudaMemsetAsync(U, 0, bsz * sizeof(T), s));
+    RB_CUDA(cudaMemsetAsync(Ut, 0, bsz * sizeof(T), s));
+    ring_ld = ldv;
+    st = dmalloc<DevState>(1);
+    RB_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+    const size_t part_elems =
+        std::max<size_t>((size_t)grid * (2 * KMAX + 2), (size_t)gram_grid * 64 * 64);
+    part = dmalloc<A>(part_elems);
+    G = dmalloc<A>((size_t)GRAM_MAXCOLS * GRAM_MAXCOLS);
+    work = dmalloc<zd>(dense_work_elems_fwd());
+    Wphi = dmalloc<zd>(MMAX * KMAX); Wphit = dmalloc<zd>(MMAX * KMAX);
+    Nmat = dmalloc<zd>(KMAX * KMAX); Mmat = dmalloc<zd>(KMAX * KMAX);
+    sig = dmalloc<double>(KMAX);
+    iflag = dmalloc<int>(4);
+    RB_CUDA(cudaMallocHost(&hv, sizeof(HostView)));
+  }
+  int64_t ring_ld = 0;
+
+  ~Solver() override {
+    cudaStreamSynchronize(s);
+    T* bufs[] = {ring, ringt, p[0], p[1], pt[0], pt[1], z, zt, U, Ut, C, Ct,
+                 Uc[0], Uc[1], Utc[0], Utc[1], Cc[0], Cc[1], Ctc[0], Ctc[1]};
+    for (T* b : bufs) cudaFree(b);
+    cudaFree(st); cudaFree(part); cudaFree(G); cudaFree(work); cudaFree(Wphi); cudaFree(Wphit);
+    cudaFree(Nmat); cudaFree(Mmat); cudaFree(sig); cudaFree(iflag);
+    free_op();
+    if (hv) cudaFreeHost(hv);
+  }
+
+  void free_op() {
+    if (tva) cudaFree(tva);
+    if (trp_own) cudaFree(trp_own);
+    if (tci_own) cudaFree(tci_own);
+    if (va_own) cudaFree(va_own);
+    tva = nullptr; trp_own = nullptr; tci_own = nullptr; va_own = nullptr;
+    op_ready = 0;
+  }
+
+  void count(int k) { *launches += k; }
+
+  // Fetch the host view of the device state (one sync).
+  void fetch() {
+    RB_CUDA(cudaGetLastError());   // a failed launch must not leave the host loop waiting
+    RB_CUDA(cudaMemcpyAsync(hv, st, sizeof(HostView), cudaMemcpyDeviceToHost, s));
+    RB_CUDA(cudaStreamSynchronize(s));
+    prof->harvest();
+  }
+
+  template <class F>
+  void set_field(F DevState::*field, const F& value) {
+    RB_CUDA(cudaMemcpyAsync(&(st->*field), &value, sizeof(F), cudaMemcpyHostToDevice, s));
+  }
+
+  // ------------------------------------------------------------------ operator
+  // va_src: values in V (already converted for an inner solver)
+  void set_operator(const rbicg_csr& A, const V* va_src) {
+    free_op();
+    op.n = (int)A.n;
+    op.rp = A.row_ptr;
+    op.ci = A.col_idx;
+    op.va = va_src;
+    op.has_shift = A.has_shift;
+    op.sh_re = A.shift_re;
+    op.sh_im = A.shift_im;
+    tva = dmalloc<V>(std::max<int64_t>(1, A.nnz));
+    int* trp = nullptr;
+    int* tci = nullptr;
+    int shared = 0;
+    const int pi = prof->begin(7, s);
+    int e = build_adjoint<V>(op.n, op.rp, op.ci, op.va, &trp, &tci, &tva, &shared, iflag, s);
+    prof->end(pi, 1, s);
+    if (e) throw Err{RBICG_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString((cudaError_t)e)};
+    count(shared ? 1 : 5);
+    op.trp = trp;
+    op.tci = tci;
+    op.tva = tva;
+    op.shared = shared;
+    if (!shared) { trp_own = trp; tci_own = tci; }
+    op_ready = 1;
+    pending_start = 1;
+  }
+
+  VecArgs<T> vec(const T* b, const T* bt, T* x, T* xt, const T* Cp, const T* Ctp, const T* Up, const T* Utp) {
+    VecArgs<T> v{};
+    v.ring = ring; v.ringt = ringt; v.ld = ring_ld; v.R = R;
+    v.p[0] = p[0]; v.p[1] = p[1]; v.pt[0] = pt[0]; v.pt[1] = pt[1];
+    v.z = z; v.zt = zt; v.x = x; v.xt = xt; v.b = b; v.bt = bt;
+    v.C = Cp; v.Ct = Ctp; v.U = Up; v.Ut = Utp; v.ldk = ldk;
+    return v;
+  }
+
+  ColList<T> block_cols(const T* B, int k) {
+    ColList<T> l{};
+    append_block(l, B, k);
+    return l;
+  }
+  void append_block(ColList<T>& l, const T* B, int k) {
+    for (int c = 0; c < k; ++c) { l.c[l.m].p = B + c; l.c[l.m].ld = ldk; ++l.m; }
+  }
+  void append_ring(ColList<T>& l, const T* rg, int m0, int m1) {   // residuals r_m0 .. r_m1
+    for (int m = m0; m <= m1; ++m) { l.c[l.m].p = rg + (int64_t)(m % R) * ring_ld; l.c[l.m].ld = 1; ++l.m; }
+  }
+
+  // ------------------------------------------------------------------ Section 4.3, system start
+  // C = Op U, Ct = Op^H Ut, SVD of Ct^H C after column scaling, truncation, rotation.
+  void system_start() {
+    pending_start = 0;
+    kc = 0;
+    set_field(&DevState::kc, 0);
+    if (!prm.recycle || kU <= 0) return;
+    int* kdev = iflag + 1;
+    RB_CUDA(cudaMemcpyAsync(kdev, &kU, sizeof(int), cudaMemcpyHostToDevice, s));
+    const int pi = prof->begin(6, s);
+    launch_spmm<V, T>(op, 0, U, ldk, kdev, KMAX, C, 0, s);
+    launch_spmm<V, T>(op, 1, Ut, ldk, kdev, KMAX, Ct, 0, s);
+    ColList<T> X{}, Y{};
+    append_block(X, Ct, prm.k); append_block(X, C, prm.k);
+    append_block(Y, C, prm.k); append_block(Y, Ct, prm.k);
+    launch_gram<T>(X, Y, n, 0, part, gram_grid, G, s);
+    launch_dense_svd(!traits<T>::cx, kdev, prm.k, reinterpret_cast<const zd*>(as_zd_gram()), nullptr, nullptr,
+                     prm.svd_tol, Nmat, Mmat, sig, &st->kc, st->Dc, iflag + 2, s);
+    launch_rotate<T>(U, ldk, Nmat, kdev, &st->kc, prm.k, n, 0, s);
+    launch_rotate<T>(C, ldk, Nmat, kdev, &st->kc, prm.k, n, 0, s);
+    launch_rotate<T>(Ut, ldk, Mmat, kdev, &st->kc, prm.k, n, 0, s);
+    launch_rotate<T>(Ct, ldk, Mmat, kdev, &st->kc, prm.k, n, 0, s);
+    prof->end(pi, 10, s);
+    count(10);
+    fetch();
+    kc = hv->kc;
+  }
+
+  // The Gram output is A (double for real problems); the dense SVD reads complex entries.
+  zd* gz = nullptr;
+  const zd* as_zd_gram() {
+    if (traits<T>::cx) return reinterpret_cast<const zd*>(G);
+    if (!gz) gz = dmalloc<zd>((size_t)GRAM_MAXCOLS * GRAM_MAXCOLS);
+    launch_real_to_zd(reinterpret_cast<const double*>(G), gz, (int64_t)GRAM_MAXCOLS * GRAM_MAXCOLS, s);
+    count(1);
+    return gz;
+  }
+
+  // ------------------------------------------------------------------ Section 4.1-4.3 refresh
+  // Runs after iteration j*s.  kp = columns of U_{j-1}.  Returns nothing; results are read
+  // at the next sync (st->pcyc, st->eig_status).
+  void refresh(int j, int kp, const T* /*unused*/) {
+    const bool first = kc == 0;
+    RefreshInfo f{};
+    f.case_id = first ? (j == 1 ? 0 : 1) : (j == 1 ? 2 : 3);
+    f.j = j; f.s = prm.s; f.k = prm.k; f.kc = kc; f.kp = kp; f.real_path = !traits<T>::cx; f.R = R;
+    const int jp = (j - 1) & 1, jc = j & 1;
+    const int ss = prm.s;
+    ColList<T> X{}, Y{}, Ph{}, Pht{};
+    if (f.case_id == 0) {
+      append_ring(Ph, ring, 0, ss - 1);
+      append_ring(Pht, ringt, 0, ss - 1);
+    } else {
+      if (f.case_id == 3) { append_block(Y, C, kc); append_block(X, Ct, kc); }
+      if (f.case_id == 2) { append_block(Y, C, kc); append_block(X, Ct, kc); }
+      if (f.case_id == 1 || f.case_id == 3) { append_block(Y, Cc[jp], kp); append_block(X, Ctc[jp], kp); }
+      const int m0 = f.case_id == 2 ? 0 : (j - 1) * ss - 1, m1 = j * ss;
+      append_ring(Y, ring, m0, m1);
+      append_ring(X, ringt, m0, m1);
+      const T* Ub = f.case_id == 2 ? U : Uc[jp];
+      const T* Utb = f.case_id == 2 ? Ut : Utc[jp];
+      const int kb = f.case_id == 2 ? kc : kp;
+      append_block(Y, Ub, kb);
+      f.mx = X.m; f.my = Y.m;
+      append_block(Ph, Ub, kb);
+      append_block(Pht, Utb, kb);
+      append_ring(Ph, ring, (j - 1) * ss, j * ss - 1);
+      append_ring(Pht, ringt, (j - 1) * ss, j * ss - 1);
+      const int pg = prof->begin(3, s);
+      launch_gram<T>(X, Y, n, prm.setup_fp32, part, gram_grid, G, s);
+      prof->end(pg, 2, s);
+      count(2);
+    }
+    const int pd = prof->begin(4, s);
+    launch_dense_refresh<T>(f, st, G, work, Wphi, Wphit, KMAX, nullptr, s);
+    prof->end(pd, f.case_id == 0 ? 2 : 4, s);
+    count(f.case_id == 0 ? 2 : 4);
+    const int pb = prof->begin(5, s);
+    int* kk = &st->kk;
+    launch_combine<T>(Ph, Wphi, KMAX, kk, prm.k, Uc[jc], ldk, n, prm.setup_fp32, s);
+    launch_combine<T>(Pht, Wphit, KMAX, kk, prm.k, Utc[jc], ldk, n, prm.setup_fp32, s);
+    launch_spmm<V, T>(op, 0, Uc[jc], ldk, kk, prm.k, Cc[jc], prm.setup_fp32, s);
+    launch_spmm<V, T>(op, 1, Utc[jc], ldk, kk, prm.k, Ctc[jc], prm.setup_fp32, s);
+    ColList<T> X2{}, Y2{};
+    append_block(X2, Ctc[jc], prm.k); append_block(X2, Cc[jc], prm.k);
+    append_block(Y2, Cc[jc], prm.k); append_block(Y2, Ctc[jc], prm.k);
+    launch_gram<T>(X2, Y2, n, prm.setup_fp32, part, gram_grid, G, s);
+    launch_dense_svd(!traits<T>::cx, kk, prm.k, as_zd_gram(), nullptr, nullptr, prm.svd_tol, Nmat, Mmat, sig,
+                     &st->pcyc, nullptr, iflag + 3, s);
+    launch_rotate<T>(Uc[jc], ldk, Nmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, s);
+    launch_rotate<T>(Cc[jc], ldk, Nmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, s);
+    launch_rotate<T>(Utc[jc], ldk, Mmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, s);
+    launch_rotate<T>(Ctc[jc], ldk, Mmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, s);
+    prof->end(pb, 11, s);
+    count(11);
+  }
+
+  // ------------------------------------------------------------------ Algorithm 2
+  struct PairOut {
+    int iters = 0, cycles = 0, recycle_dim = 0, status = 0;
+    double relres = 0, relres_dual = 0, true_relres = 0, true_relres_dual = 0;
+  };
+
+  PairOut solve(const T* b, const T* bt, T* x, T* xt, double tol, int max_itn, uint64_t seed) {
+    const int kU_in = prm.recycle ? kU : 0;
+    if (pending_start) system_start();
+    const int kt = kt_for(kc);
+    set_field(&DevState::tol, tol);
+    set_field(&DevState::max_itn, max_itn);
+    set_field(&DevState::done, 0);
+    set_field(&DevState::eig_status, 0);
+    set_field(&DevState::pcyc, 0);
+    VecArgs<T> v = vec(b, bt, x, xt, C, Ct, U, Ut);
+    const int pi = prof->begin(7, s);
+    launch_init<V, T>(op, v, st, part, kt, grid, 0, s);
+    prof->end(pi, 2, s);
+    count(2);
+    fetch();
+    if (hv->restart) {
+      // Algorithm 2 step 3: xt_{-1} <- random (Philox4x32-10), recompute the dual start
+      launch_philox<T>(xt, n, seed, s);
+      launch_init<V, T>(op, v, st, part, kt, grid, 1, s);
+      count(3);
+      fetch();
+    }
+    PairOut out;
+    const bool recycle = prm.recycle != 0;
+    int j = 0, kp = 0, last_refresh = 0, good_refresh = 0, good_p = 0;
+    bool broken = false;
+    int done = hv->done;
+    int iter = 0;
+    while (!done) {
+      const int todo = std::min(prm.s, max_itn - iter);
+      for (int t = 0; t < todo; ++t) {
+        int pp = prof->begin(0, s);
+        launch_phase1<V, T>(op, v, st, part, kt, grid, s);
+        prof->end(pp, 1, s);
+        pp = prof->begin(1, s);
+        launch_phase2<V, T>(op, v, st, part, kt, grid, s);
+        prof->end(pp, 1, s);
+        pp = prof->begin(2, s);
+        launch_phase3<V, T>(op, v, st, part, grid, s);
+        prof->end(pp, 1, s);
+      }
+      count(3 * todo);
+      fetch();
+      // status of the refresh launched after the previous cycle
+      if (last_refresh > 0 && !broken) {
+        if (hv->eig_status != 0) broken = true;
+        else { good_refresh = last_refresh; good_p = hv->pcyc; kp = hv->pcyc; }
+      }
+      if (!hv->done && hv->iter <= iter)
+        throw Err{RBICG_ERR_CUDA, "iteration made no progress (device state not advancing)"};
+      iter = hv->iter;
+      done = hv->done;
+      if (!done && iter >= max_itn) done = DONE_MAXIT;
+      if (recycle && !broken && iter == (j + 1) * prm.s) {
+        ++j;
+        refresh(j, kp, nullptr);
+        last_refresh = j;
+      }
+    }
+    const int pf = prof->begin(7, s);
+    launch_finish<V, T>(op, v, st, part, kt, grid, s);
+    prof->end(pf, 2, s);
+    count(2);
+    fetch();
+    if (last_refresh > good_refresh && !broken) {
+      if (hv->eig_status != 0) broken = true;
+      else { good_refresh = last_refresh; good_p = hv->pcyc; }
+    }
+    out.iters = hv->iter;
+    out.cycles = good_refresh;
+    out.recycle_dim = kc;
+    const double nb = hv->bnorm > 0 ? hv->bnorm : 1.0, nbt = hv->btnorm > 0 ? hv->btnorm : 1.0;
+    out.relres = hv->rnorm / nb;
+    out.relres_dual = hv->rtnorm / nbt;
+    out.true_relres = hv->true_rnorm / nb;
+    out.true_relres_dual = hv->true_rtnorm / nbt;
+    switch (hv->done) {
+      case DONE_CONVERGED: out.status = RBICG_OK; break;
+      case DONE_BREAK_RHO: out.status = RBICG_BREAKDOWN_RHO; break;
+      case DONE_BREAK_PQ: out.status = RBICG_BREAKDOWN_PQ; break;
+      case DONE_NONFINITE: out.status = RBICG_ERR_NONFINITE; break;
+      default: out.status = RBICG_NOT_CONVERGED; break;
+    }
+    if (hv->iter == 0 && hv->done == DONE_CONVERGED) out.status = RBICG_OK;
+    // recycle space for the next system (Section 4: the final U_j; Section 6.2: keep the
+    // previous space if no cycle completed)
+    if (debug_on())
+      fprintf(stderr, "[rbicg] solve n=%lld T=%zu kc=%d iters=%d done=%d relres=%.3e/%.3e true=%.3e/%.3e cycles=%d p=%d\n",
+              (long long)n, sizeof(T), kc, hv->iter, hv->done, out.relres, out.relres_dual, out.true_relres,
+              out.true_relres_dual, good_refresh, good_p);
+    if (recycle) {
+      if (good_refresh > 0) {
+        const int jc = good_refresh & 1;
+        std::swap(U, Uc[jc]); std::swap(Ut, Utc[jc]); std::swap(C, Cc[jc]); std::swap(Ct, Ctc[jc]);
+        kU = good_p;
+      } else if (kc > 0) {
+        kU = kc;
+      } else {
+        kU = 0;
+      }
+    }
+    pending_start = 1;   // the next solve re-derives C, Ct for the (possibly new) operator
+    if (kU_in > 0 && kc == 0 && out.status == RBICG_OK) out.status = RBICG_RECYCLE_EMPTY;
+    return out;
+  }
+
+  void launch_real_to_zd(const double* a, zd* b, int64_t m, cudaStream_t st_) { launch_convert_rz(a, b, m, st_); }
+  static void launch_convert_rz(const double* a, zd* b, int64_t m, cudaStream_t st_);
+};
+
+__global__ void k_real_to_zd(const double* a, zd* b, int64_t m) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = zd(a[i], 0.0);
+}
+template <class V, class T>
+void Solver<V, T>::launch_convert_rz(const double* a, zd* b, int64_t m, cudaStream_t st_) {
+  k_real_to_zd<<<64, 256, 0, st_>>>(a, b, m);
+}
+
+// residual kernel for the refinement loop: r = b - Op x (FP64), norms via a small reduction
+template <class V, class T>
+__global__ void k_residual(OpArgs<V> op, const T* b, const T* x, T* r, int adjoint) {
+  const int* rp = adjoint ? op.trp : op.rp;
+  const int* ci = adjoint ? op.tci : op.ci;
+  const V* va = adjoint ? op.tva : op.va;
+  T sh = from_zd<T>(zd(op.sh_re, adjoint ? -op.sh_im : op.sh_im));
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += gridDim.x * blockDim.x) {
+    T acc = T(0);
+    for (int e = rp[row]; e < rp[row + 1]; ++e) acc += vmul(va[e], x[ci[e]]);
+    if (op.has_shift) acc = sh * x[row] - acc;
+    r[row] = b[row] - acc;
+  }
+}
+template <class T>
+__global__ void k_norm2(const T* a, int64_t n, double* out) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += (double)abs2(a[i]);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[blockIdx.x] = t;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// the handle
+// ------------------------------------------------------------------------------------
+template <class T> struct lowp;
+template <> struct lowp<double> { typedef float type; };
+template <> struct lowp<cplx<double>> { typedef cplx<float> type; };
+
+struct Ctx;
+
+struct Impl {
+  virtual ~Impl() {}
+  virtual void set_operator(const rbicg_csr& A) = 0;
+  virtual rbicg_result solve(const void* b, const void* bt, void* x, void* xt) = 0;
+  virtual void reset() = 0;
+  virtual void export_recycle(void* U, void* Ut, int* p) = 0;
+  virtual void import_recycle(const void* U, const void* Ut, int p) = 0;
+};
+
+template <class V, class T>
+struct ImplT : Impl {
+  typedef typename lowp<T>::type T32;
+  typedef typename lowp<V>::type V32;
+  rbicg_params prm;
+  int64_t n;
+  cudaStream_t s;
+  int64_t* launches;
+  std::unique_ptr<Solver<V, T>> hi;
+  std::unique_ptr<Solver<V32, T32>> lo;
+  V32* va32 = nullptr;
+  T *r64 = nullptr, *rt64 = nullptr;
+  T32 *r32 = nullptr, *rt32 = nullptr, *d32 = nullptr, *dt32 = nullptr;
+  T *d64 = nullptr;
+  double* nrm = nullptr;
+  double* hnrm = nullptr;
+
+  Profiler* prof;
+  ImplT(const rbicg_params& p, int64_t n_, cudaStream_t s_, int64_t* l, Profiler* pr)
+      : prm(p), n(n_), s(s_), launches(l), prof(pr) {
+    if (prm.precision == RBICG_FP64) {
+      hi.reset(new Solver<V, T>(prm, n, s, launches, prof));
+    } else {
+      rbicg_params ph = prm;
+      ph.recycle = 0;
+      ph.k = 1;
+      ph.s = 2;
+      hi.reset(new Solver<V, T>(ph, n, s, launches, prof));   // operator + A^H only
+      rbicg_params pl = prm;
+      pl.svd_tol = std::max(prm.svd_tol, prm.inner_svd_tol);
+      lo.reset(new Solver<V32, T32>(pl, n, s, launches, prof));
+      r64 = dmalloc<T>(n); rt64 = dmalloc<T>(n); d64 = dmalloc<T>(n);
+      r32 = dmalloc<T32>(n); rt32 = dmalloc<T32>(n); d32 = dmalloc<T32>(n); dt32 = dmalloc<T32>(n);
+      nrm = dmalloc<double>(1024);
+      RB_CUDA(cudaMallocHost(&hnrm, sizeof(double) * 1024));
+    }
+  }
+  ~ImplT() override {
+    cudaStreamSynchronize(s);
+    if (va32) cudaFree(va32);
+    void* bufs[] = {r64, rt64, d64, r32, rt32, d32, dt32, nrm};
+    for (void* b : bufs) if (b) cudaFree(b);
+    if (hnrm) cudaFreeHost(hnrm);
+  }
+
+  void set_operator(const rbicg_csr& A) override {
+    hi->set_operator(A, reinterpret_cast<const V*>(A.val));
+    if (lo) {
+      if (va32) cudaFree(va32);
+      va32 = dmalloc<V32>(std::max<int64_t>(1, A.nnz));
+      launch_convert<V, V32>(reinterpret_cast<const V*>(A.val), va32, A.nnz, s);
+      *launches += 1;
+      lo->set_operator(A, va32);
+    }
+  }
+
+  double norm(const T* a) {
+    const int blocks = 256;
+    k_norm2<T><<<blocks, 256, 0, s>>>(a, n, nrm);
+    *launches += 1;
+    RB_CUDA(cudaMemcpyAsync(hnrm, nrm, sizeof(double) * blocks, cudaMemcpyDeviceToHost, s));
+    RB_CUDA(cudaStreamSynchronize(s));
+    double t = 0.0;
+    for (int i = 0; i < blocks; ++i) t += hnrm[i];
+    return sqrt(t);
+  }
+
+  rbicg_result solve(const void* bv, const void* btv, void* xv, void* xtv) override {
+    const T* b = reinterpret_cast<const T*>(bv);
+    const T* bt = reinterpret_cast<const T*>(btv);
+    T* x = reinterpret_cast<T*>(xv);
+    T* xt = reinterpret_cast<T*>(xtv);
+    rbicg_result res{};
+    if (!lo) {
+      auto o = hi->solve(b, bt, x, xt, prm.tol, prm.max_itn, prm.seed);
+      res.iters = o.iters; res.cycles = o.cycles; res.recycle_dim = o.recycle_dim; res.refine_steps = 0;
+      res.relres = o.relres; res.relres_dual = o.relres_dual;
+      res.true_relres = o.true_relres; res.true_relres_dual = o.true_relres_dual;
+      res.status = o.status;
+      return res;
+    }
+    // FP64 iterative refinement around FP32 inner RBiCG solves
+    const int grid = std::max(1, std::min((int)((n + 255) / 256), num_sms() * 8));
+    const double nb = norm(b), nbt = norm(bt);
+    int status = RBICG_NOT_CONVERGED;
+    double rr = 0, rtr = 0;
+    int step = 0, total_iters = 0, cycles = 0, rdim = 0;
+    int first_inner = -1, inner_cap = prm.max_itn;
+    bool retried_plain = false;
+    for (;; ++step) {
+      k_residual<V, T><<<grid, 256, 0, s>>>(hi->op, b, x, r64, 0);
+      k_residual<V, T><<<grid, 256, 0, s>>>(hi->op, bt, xt, rt64, 1);
+      *launches += 2;
+      rr = norm(r64);
+      rtr = norm(rt64);
+      if (debug_on()) fprintf(stderr, "[rbicg] refine step %d relres %.3e dual %.3e\n", step, rr / (nb > 0 ? nb : 1.0),
+                              rtr / (nbt > 0 ? nbt : 1.0));
+      const bool pc = rr <= prm.tol * (nb > 0 ? nb : 1.0) || (nb == 0 && rr == 0);
+      const bool dc = nbt == 0.0 || rtr <= prm.tol * nbt;
+      if (pc && dc) { status = RBICG_OK; break; }
+      if (step >= prm.refine_max) break;
+      launch_convert<T, T32>(r64, r32, n, s);
+      launch_convert<T, T32>(rt64, rt32, n, s);
+      RB_CUDA(cudaMemsetAsync(d32, 0, sizeof(T32) * n, s));
+      RB_CUDA(cudaMemsetAsync(dt32, 0, sizeof(T32) * n, s));
+      *launches += 2;
+      auto o = lo->solve(r32, rt32, d32, dt32, prm.inner_tol, inner_cap, prm.seed + step);
+      total_iters += o.iters;
+      cycles += o.cycles;
+      rdim = o.recycle_dim;
+      if (o.status < 0) { status = o.status; break; }
+      if (first_inner < 0) {
+        first_inner = o.iters;
+        inner_cap = std::min(prm.max_itn, std::max(200, 4 * first_inner + 100));
+      }
+      // A correction is used only if the inner solve reduced its own residual; otherwise the
+      // inner recycle space is dropped and the step is retried once as plain FP32 BiCG.
+      const bool usable = o.status == RBICG_OK || o.status == RBICG_RECYCLE_EMPTY ||
+                          (o.true_relres < 0.5 && (dc || o.true_relres_dual < 0.5));
+      if (debug_on())
+        fprintf(stderr, "[rbicg] inner step %d status %d iters %d relres %.3e/%.3e usable %d\n", step, o.status,
+                o.iters, o.true_relres, o.true_relres_dual, (int)usable);
+      if (!usable) {
+        if (retried_plain) { status = RBICG_NOT_CONVERGED; break; }
+        retried_plain = true;
+        lo->kU = 0;
+        lo->pending_start = 1;
+        --step;
+        continue;
+      }
+      retried_plain = false;
+      if (!pc) {
+        launch_convert<T32, T>(d32, d64, n, s);
+        launch_axpy_inplace<T>(x, d64, n, s);
+        *launches += 2;
+      }
+      if (!dc) {
+        launch_convert<T32, T>(dt32, d64, n, s);
+        launch_axpy_inplace<T>(xt, d64, n, s);
+        *launches += 2;
+      }
+    }
+    res.iters = total_iters;
+    res.cycles = cycles;
+    res.recycle_dim = rdim;
+    res.refine_steps = step;
+    res.relres = rr / (nb > 0 ? nb : 1.0);
+    res.relres_dual = rtr / (nbt > 0 ? nbt : 1.0);
+    res.true_relres = res.relres;
+    res.true_relres_dual = res.relres_dual;
+    res.status = status;
+    return res;
+  }
+
+  void reset() override {
+    hi->kU = 0; hi->pending_start = 1;
+    if (lo) { lo->kU = 0; lo->pending_start = 1; }
+  }
+
+  void export_recycle(void* Uo, void* Uto, int* p) override {
+    if (lo) {
+      // the recycle space lives in the FP32 inner solver; export it widened to FP64
+      const int64_t m = n * lo->ldk;
+      T* tmp = reinterpret_cast<T*>(Uo);
+      T* tmpt = reinterpret_cast<T*>(Uto);
+      std::vector<int> dummy;
+      (void)dummy;
+      widen_rows(lo->U, tmp, lo->ldk);
+      widen_rows(lo->Ut, tmpt, lo->ldk);
+      (void)m;
+      *p = lo->kU;
+      return;
+    }
+    copy_rows(hi->U, reinterpret_cast<T*>(Uo), hi->ldk);
+    copy_rows(hi->Ut, reinterpret_cast<T*>(Uto), hi->ldk);
+    *p = hi->kU;
+  }
+  void copy_rows(const T* src, T* dst, int ldk) {
+    RB_CUDA(cudaMemcpy2DAsync(dst, sizeof(T) * prm.k, src, sizeof(T) * ldk, sizeof(T) * prm.k, n,
+                              cudaMemcpyDeviceToDevice, s));
+    RB_CUDA(cudaStreamSynchronize(s));
+  }
+  void widen_rows(const T32* src, T* dst, int ldk) {
+    T* tmp = dmalloc<T>((size_t)n * ldk);
+    launch_convert<T32, T>(src, tmp, (int64_t)n * ldk, s);
+    copy_rows(tmp, dst, ldk);
+    cudaFree(tmp);
+  }
+  void import_recycle(const void* Ui, const void* Uti, int p) override {
+    if (lo) {
+      T32* tmp = dmalloc<T32>((size_t)n * p);
+      for (int side = 0; side < 2; ++side) {
+        launch_convert<T, T32>(reinterpret_cast<const T*>(side ? Uti : Ui), tmp, (int64_t)n * p, s);
+        RB_CUDA(cudaMemsetAsync(side ? lo->Ut : lo->U, 0, sizeof(T32) * n * lo->ldk, s));
+        RB_CUDA(cudaMemcpy2DAsync(side ? lo->Ut : lo->U, sizeof(T32) * lo->ldk, tmp, sizeof(T32) * p,
+                                  sizeof(T32) * p, n, cudaMemcpyDeviceToDevice, s));
+      }
+      RB_CUDA(cudaStreamSynchronize(s));
+      cudaFree(tmp);
+      lo->kU = p; lo->pending_start = 1;
+      return;
+    }
+    for (int side = 0; side < 2; ++side) {
+      T* dst = side ? hi->Ut : hi->U;
+      RB_CUDA(cudaMemsetAsync(dst, 0, sizeof(T) * n * hi->ldk, s));
+      RB_CUDA(cudaMemcpy2DAsync(dst, sizeof(T) * hi->ldk, side ? Uti : Ui, sizeof(T) * p, sizeof(T) * p, n,
+                                cudaMemcpyDeviceToDevice, s));
+    }
+    RB_CUDA(cudaStreamSynchronize(s));
+    hi->kU = p; hi->pending_start = 1;
+  }
+};
+
+}  // namespace rb
+
+// ------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------
+using namespace rb;
+
+struct rbicg_ctx {
+  rbicg_params prm;
+  int64_t n;
+  rbicg_dtype dtype;
+  cudaStream_t s;
+  int val_complex = -1;
+  std::unique_ptr<Impl> impl;
+  OpKey key;
+  std::string err;
+  int64_t launches = 0;
+  Profiler prof;
+};
+
+static rbicg_status fail(rbicg_handle h, rbicg_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  g_last_error = msg;
+  return st;
+}
+
+#define RB_GUARD(h, ...)                                                                      \
+  try {                                                                                       \
+    __VA_ARGS__                                                                               \
+  } catch (const Err& e) {                                                                    \
+    return fail(h, e.st, e.msg);                                                              \
+  } catch (const std::exception& e) {                                                         \
+    return fail(h, RBICG_ERR_CUDA, e.what());                                                 \
+  }
+
+extern "C" void rbicg_default_params(rbicg_params* p) {
+  if (!p) return;
+  p->k = 10; p->s = 40; p->max_itn = 20000; p->tol = 1e-8; p->svd_tol = 1e-6; p->inner_tol = 1e-5;
+  p->refine_max = 12; p->precision = RBICG_FP64; p->seed = 0; p->setup_fp32 = 1; p->recycle = 1;
+  p->inner_svd_tol = 1e-3;
+}
+
+static std::string check_params(const rbicg_params* p, int64_t n) {
+  if (!p) return "params is NULL";
+  if (n <= 0 || n > (int64_t)0x7fffffff - 1) return "n out of range";
+  if (p->k < 1 || p->k > KMAX) return "k must be in 1..32";
+  if (p->s < 2 || p->s > SMAX) return "s must be in 2..64";
+  if (p->k + p->s > MMAX) return "k + s must be <= 80";
+  if (!(p->tol > 0.0)) return "tol must be positive";
+  if (p->max_itn < 1) return "max_itn must be positive";
+  if (!(p->svd_tol >= 0.0)) return "svd_tol must be >= 0";
+  if (p->precision == RBICG_FP32_REFINED && !(p->inner_tol > 0.0 && p->inner_tol < 1.0))
+    return "inner_tol must be in (0, 1)";
+  if (p->precision != RBICG_FP64 && p->precision != RBICG_FP32_REFINED) return "unknown precision";
+  return "";
+}
+
+extern "C" rbicg_status rbicg_create(const rbicg_params* params, int64_t n, rbicg_dtype dtype, void* stream,
+                                     rbicg_handle* out) {
+  if (!out) return fail(nullptr, RBICG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  const std::string m = check_params(params, n);
+  if (!m.empty()) return fail(nullptr, RBICG_ERR_ARG, m);
+  if (dtype != RBICG_R64 && dtype != RBICG_C128) return fail(nullptr, RBICG_ERR_ARG, "unknown dtype");
+  rbicg_ctx* h = new rbicg_ctx();
+  h->prm = *params;
+  h->n = n;
+  h->dtype = dtype;
+  h->s = reinterpret_cast<cudaStream_t>(stream);
+  *out = h;
+  return RBICG_OK;
+}
+
+static void ensure_impl(rbicg_handle h, int val_complex) {
+  if (h->impl && h->val_complex == val_complex) return;
+  if (h->impl && h->val_complex != val_complex)
+    throw Err{RBICG_ERR_ARG, "operator value type (real/complex) changed on this handle"};
+  if (h->dtype == RBICG_R64) {
+    if (val_complex) throw Err{RBICG_ERR_ARG, "complex operator on a real (R64) handle"};
+    h->impl.reset(new ImplT<double, double>(h->prm, h->n, h->s, &h->launches, &h->prof));
+  } else if (val_complex) {
+    h->impl.reset(new ImplT<cplx<double>, cplx<double>>(h->prm, h->n, h->s, &h->launches, &h->prof));
+  } else {
+    h->impl.reset(new ImplT<double, cplx<double>>(h->prm, h->n, h->s, &h->launches, &h->prof));
+  }
+  h->val_complex = val_complex;
+}
+
+static std::string check_csr(rbicg_handle h, const rbicg_csr* A) {
+  if (!A) return "A is NULL";
+  if (A->n != h->n) return "A->n does not match the handle";
+  if (A->nnz < 0 || A->nnz > (int64_t)0x7fffffff) return "nnz out of range";
+  if (!A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->val))) return "null CSR array";
+  if (h->dtype == RBICG_R64 && A->has_shift && A->shift_im != 0.0) return "complex shift on a real handle";
+  return "";
+}
+
+static void do_update(rbicg_handle h, const rbicg_csr* A) {
+  ensure_impl(h, A->val_complex ? 1 : 0);
+  int* flag = nullptr;
+  RB_CUDA(cudaMalloc(&flag, sizeof(int)));
+  validate_csr((int)A->n, A->nnz, A->row_ptr, A->col_idx, flag, h->s);
+  int hf = 0;
+  RB_CUDA(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  RB_CUDA(cudaStreamSynchronize(h->s));
+  cudaFree(flag);
+  h->launches += 1;
+  if (hf) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "malformed CSR (flags 0x%x: 1 row_ptr[0], 2 row_ptr[n], 4 order, 8 column range, "
+                              "16 unsorted/duplicate columns)", hf);
+    throw Err{RBICG_ERR_ARG, buf};
+  }
+  h->impl->set_operator(*A);
+  h->key.rp = A->row_ptr; h->key.ci = A->col_idx; h->key.va = A->val; h->key.n = A->n; h->key.nnz = A->nnz;
+  h->key.has_shift = A->has_shift; h->key.val_complex = A->val_complex; h->key.sr = A->shift_re;
+  h->key.si = A->shift_im;
+}
+
+extern "C" rbicg_status rbicg_update_recycle(rbicg_handle h, const rbicg_csr* A) {
+  if (!h) return fail(nullptr, RBICG_ERR_ARG, "handle is NULL");
+  const std::string m = check_csr(h, A);
+  if (!m.empty()) return fail(h, RBICG_ERR_ARG, m);
+  RB_GUARD(h, { do_update(h, A); return RBICG_OK; })
+}
+
+extern "C" rbicg_status rbicg_solve_pair(rbicg_handle h, const rbicg_csr* A, const void* b, const void* bt,
+                                         void* x, void* xt, rbicg_result* res) {
+  if (!h) return fail(nullptr, RBICG_ERR_ARG, "handle is NULL");
+  if (!b || !bt || !x || !xt) return fail(h, RBICG_ERR_ARG, "null vector pointer");
+  RB_GUARD(h, {
+    if (A) {
+      const std::string m = check_csr(h, A);
+      if (!m.empty()) return fail(h, RBICG_ERR_ARG, m);
+      OpKey k;
+      k.rp = A->row_ptr; k.ci = A->col_idx; k.va = A->val; k.n = A->n; k.nnz = A->nnz; k.has_shift = A->has_shift;
+      k.val_complex = A->val_complex; k.sr = A->shift_re; k.si = A->shift_im;
+      if (!h->impl || !(k == h->key)) do_update(h, A);
+    }
+    if (!h->impl) return fail(h, RBICG_ERR_ARG, "no operator set (pass A or call rbicg_update_recycle)");
+    rbicg_result r = h->impl->solve(b, bt, x, xt);
+    if (res) *res = r;
+    if (r.status < 0) return fail(h, (rbicg_status)r.status, "non-finite value in the iteration");
+    h->err.clear();
+    return (rbicg_status)r.status;
+  })
+}
+
+extern "C" rbicg_status rbicg_solve_batch(rbicg_handle* hs, const rbicg_csr* const* As, const void* const* bs,
+                                          const void* const* bts, void* const* xs, void* const* xts, int count,
+                                          rbicg_result* res) {
+  if (!hs || count < 0) return fail(nullptr, RBICG_ERR_ARG, "bad batch arguments");
+  rbicg_status worst = RBICG_OK;
+  for (int i = 0; i < count; ++i) {
+    rbicg_result r{};
+    const rbicg_status st = rbicg_solve_pair(hs[i], As ? As[i] : nullptr, bs[i], bts[i], xs[i], xts[i], &r);
+    if (res) res[i] = r;
+    if (st < 0) return st;
+    if (st > worst) worst = st;
+  }
+  return worst;
+}
+
+extern "C" rbicg_status rbicg_export_recycle(rbicg_handle h, void* U, void* Ut, int* p) {
+  if (!h || !U || !Ut || !p) return fail(h, RBICG_ERR_ARG, "null argument");
+  if (!h->impl) { *p = 0; return RBICG_OK; }
+  RB_GUARD(h, { h->impl->export_recycle(U, Ut, p); return RBICG_OK; })
+}
+
+extern "C" rbicg_status rbicg_import_recycle(rbicg_handle h, const void* U, const void* Ut, int p) {
+  if (!h || (p > 0 && (!U || !Ut))) return fail(h, RBICG_ERR_ARG, "null argument");
+  if (p < 0 || p > h->prm.k) return fail(h, RBICG_ERR_ARG, "p must be in 0..k");
+  if (!h->impl) return fail(h, RBICG_ERR_ARG, "set an operator before importing a recycle space");
+  RB_GUARD(h, { h->impl->import_recycle(U, Ut, p); return RBICG_OK; })
+}
+
+extern "C" rbicg_status rbicg_reset(rbicg_handle h) {
+  if (!h) return fail(nullptr, RBICG_ERR_ARG, "handle is NULL");
+  if (h->impl) h->impl->reset();
+  return RBICG_OK;
+}
+
+extern "C" rbicg_status rbicg_destroy(rbicg_handle h) {
+  if (!h) return RBICG_OK;
+  try {
+    h->impl.reset();
+  } catch (...) {
+  }
+  delete h;
+  return RBICG_OK;
+}
+
+extern "C" const char* rbicg_last_error(rbicg_handle h) { return h ? h->err.c_str() : g_last_error.c_str(); }
+
+extern "C" int64_t rbicg_launch_count(rbicg_handle h) { return h ? h->launches : 0; }
+
+extern "C" rbicg_status rbicg_profile(rbicg_handle h, int enable, double* ms_out, int64_t* launches_out) {
+  if (!h) return fail(nullptr, RBICG_ERR_ARG, "handle is NULL");
+  cudaStreamSynchronize(h->s);
+  h->prof.harvest();
+  for (int i = 0; i < RBICG_NPROF; ++i) {
+    if (ms_out) ms_out[i] = h->prof.ms[i];
+    if (launches_out) launches_out[i] = h->prof.cnt[i];
+  }
+  if (enable >= 0) {
+    if (enable && !h->prof.on) h->prof.reset();
+    h->prof.on = enable != 0;
+  }
+  return RBICG_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// component entry points
+// ------------------------------------------------------------------------------------
+namespace rb {
+int64_t dense_state_offset();
+int64_t dense_work_elems();
+int64_t dense_off_L();
+int64_t dense_off_R();
+
+template <class V, class T>
+static void op_spmv_project_impl(const rbicg_csr* A, const void* r, const void* rt, const void* p_old,
+                                 const void* pt_old, double bre, double bim, const void* C, const void* Ct, int k,
+                                 int ldc, const double* Dc_host, void* p_out, void* pt_out, void* z, void* zt,
+                                 void* zeta_host, void* zetat_host, cudaStream_t s) {
+  typedef typename traits<T>::acc Acc;
+  OpArgs<V> op{};
+  op.n = (int)A->n; op.rp = A->row_ptr; op.ci = A->col_idx; op.va = reinterpret_cast<const V*>(A->val);
+  op.has_shift = A->has_shift; op.sh_re = A->shift_re; op.sh_im = A->shift_im;
+  V* tva = dmalloc<V>(std::max<int64_t>(1, A->nnz));
+  int* flag = dmalloc<int>(1);
+  int* trp = nullptr;
+  int* tci = nullptr;
+  int shared = 0;
+  int e = build_adjoint<V>(op.n, op.rp, op.ci, op.va, &trp, &tci, &tva, &shared, flag, s);
+  if (e) throw Err{RBICG_ERR_CUDA, "adjoint construction failed"};
+  op.trp = trp; op.tci = tci; op.tva = tva; op.shared = shared;
+  DevState hst;
+  std::memset(&hst, 0, sizeof hst);
+  hst.beta = zd(bre, bim);
+  hst.kc = k;
+  for (int c = 0; c < k; ++c) hst.Dc[c] = Dc_host[c];
+  DevState* st = dmalloc<DevState>(1);
+  RB_CUDA(cudaMemcpyAsync(st, &hst, sizeof hst, cudaMemcpyHostToDevice, s));
+  const int grid = std::max(1, std::min((op.n + NTHREADS - 1) / NTHREADS, num_sms() * 8));
+  Acc* part = dmalloc<Acc>((size_t)grid * (2 * KMAX + 2));
+  VecArgs<T> v{};
+  v.ring = const_cast<T*>(reinterpret_cast<const T*>(r));
+  v.ringt = const_cast<T*>(reinterpret_cast<const T*>(rt));
+  v.ld = A->n; v.R = 1;
+  v.p[0] = const_cast<T*>(reinterpret_cast<const T*>(p_old)); v.p[1] = reinterpret_cast<T*>(p_out);
+  v.pt[0] = const_cast<T*>(reinterpret_cast<const T*>(pt_old)); v.pt[1] = reinterpret_cast<T*>(pt_out);
+  v.z = reinterpret_cast<T*>(z); v.zt = reinterpret_cast<T*>(zt);
+  v.C = reinterpret_cast<const T*>(C); v.Ct = reinterpret_cast<const T*>(Ct); v.ldk = ldc;
+  launch_phase1<V, T>(op, v, st, part, kt_for(k), grid, s);
+  RB_CUDA(cudaGetLastError());
+  RB_CUDA(cudaMemcpyAsync(&hst, st, sizeof hst, cudaMemcpyDeviceToHost, s));
+  RB_CUDA(cudaStreamSynchronize(s));
+  for (int c = 0; c < k; ++c) {
+    if (traits<T>::cx) {
+      reinterpret_cast<zd*>(zeta_host)[c] = hst.zeta[c];
+      reinterpret_cast<zd*>(zetat_host)[c] = hst.zetat[c];
+    } else {
+      reinterpret_cast<double*>(zeta_host)[c] = hst.zeta[c].re;
+      reinterpret_cast<double*>(zetat_host)[c] = hst.zetat[c].re;
+    }
+  }
+  cudaFree(part); cudaFree(st); cudaFree(tva); cudaFree(flag);
+  if (!shared) { cudaFree(trp); cudaFree(tci); }
+}
+
+template <class T>
+static void op_gram_impl(int64_t n, const void* X, int mx, int ldx, const void* Y, int my, int ldy, int fp32,
+                         void* G_host, cudaStream_t s) {
+  typedef typename traits<T>::acc Acc;
+  ColList<T> xl{}, yl{};
+  for (int c = 0; c < mx; ++c) { xl.c[c].p = reinterpret_cast<const T*>(X) + c; xl.c[c].ld = ldx; }
+  for (int c = 0; c < my; ++c) { yl.c[c].p = reinterpret_cast<const T*>(Y) + c; yl.c[c].ld = ldy; }
+  xl.m = mx; yl.m = my;
+  const int gg = 2 * num_sms();
+  Acc* part = dmalloc<Acc>((size_t)gg * 64 * 64);
+  Acc* G = dmalloc<Acc>((size_t)mx * my);
+  launch_gram<T>(xl, yl, n, fp32, part, gg, G, s);
+  RB_CUDA(cudaGetLastError());
+  RB_CUDA(cudaMemcpyAsync(G_host, G, sizeof(Acc) * mx * my, cudaMemcpyDeviceToHost, s));
+  RB_CUDA(cudaStreamSynchronize(s));
+  cudaFree(part); cudaFree(G);
+}
+}  // namespace rb
+
+extern "C" rbicg_status rbicg_op_dual_spmv_project(const rbicg_csr* A, rbicg_dtype dtype, const void* r,
+                                                   const void* rt, const void* p_old, const void* pt_old,
+                                                   double beta_re, double beta_im, const void* C, const void* Ct,
+                                                   int k, int ldc, const double* Dc_host, void* p_out, void* pt_out,
+                                                   void* z, void* zt, void* zeta_host, void* zetat_host,
+                                                   void* stream) {
+  if (!A || !A->row_ptr || A->n <= 0 || !r || !rt || !p_old || !pt_old || !p_out || !pt_out || !z || !zt)
+    return fail(nullptr, RBICG_ERR_ARG, "null argument");
+  if (k < 0 || k > KMAX || (k > 0 && (!C || !Ct || !Dc_host || ldc < k || !zeta_host || !zetat_host)))
+    return fail(nullptr, RBICG_ERR_ARG, "bad projection arguments");
+  if (dtype == RBICG_R64 && A->val_complex) return fail(nullptr, RBICG_ERR_ARG, "complex operator, real dtype");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  RB_GUARD(nullptr, {
+    if (dtype == RBICG_R64)
+      op_spmv_project_impl<double, double>(A, r, rt, p_old, pt_old, beta_re, beta_im, C, Ct, k, ldc, Dc_host,
+                                           p_out, pt_out, z, zt, zeta_host, zetat_host, s);
+    else if (A->val_complex)
+      op_spmv_project_impl<cplx<double>, cplx<double>>(A, r, rt, p_old, pt_old, beta_re, beta_im, C, Ct, k, ldc,
+                                                       Dc_host, p_out, pt_out, z, zt, zeta_host, zetat_host, s);
+    else
+      op_spmv_project_impl<double, cplx<double>>(A, r, rt, p_old, pt_old, beta_re, beta_im, C, Ct, k, ldc,
+                                                 Dc_host, p_out, pt_out, z, zt, zeta_host, zetat_host, s);
+    return RBICG_OK;
+  })
+}
+
+extern "C" rbicg_status rbicg_op_gram(rbicg_dtype dtype, int64_t n, const void* X, int mx, int ldx, const void* Y,
+                                      int my, int ldy, int fp32, void* G_host, void* stream) {
+  if (n <= 0 || !X || !Y || !G_host || mx < 1 || my < 1 || mx > GRAM_MAXCOLS || my > GRAM_MAXCOLS || ldx < mx ||
+      ldy < my)
+    return fail(nullptr, RBICG_ERR_ARG, "bad Gram arguments (1 <= mx, my <= 176, ld >= columns)");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  RB_GUARD(nullptr, {
+    if (dtype == RBICG_R64) op_gram_impl<double>(n, X, mx, ldx, Y, my, ldy, fp32, G_host, s);
+    else op_gram_impl<cplx<double>>(n, X, mx, ldx, Y, my, ldy, fp32, G_host, s);
+    return RBICG_OK;
+  })
+}
+
+extern "C" rbicg_status rbicg_op_eig_select(rbicg_dtype dtype, int m, const void* L_host, const void* R_host, int k,
+                                            void* W_host, void* Wt_host, double* lam_host, int* kk, void* stream) {
+  if (m < 2 || m > MMAX || k < 1 || k > KMAX || k > m || !L_host || !W_host || !Wt_host || !kk)
+    return fail(nullptr, RBICG_ERR_ARG, "bad eigen arguments (2 <= m <= 80, 1 <= k <= min(32, m))");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  RB_GUARD(nullptr, {
+    const bool cx = dtype == RBICG_C128;
+    const int64_t welems = dense_work_elems();
+    zd* work = dmalloc<zd>(welems);
+    RB_CUDA(cudaMemsetAsync(work, 0, sizeof(zd) * welems, s));
+    std::vector<zd> Lh((size_t)MMAX * MMAX), Rh((size_t)MMAX * MMAX);
+    for (int c = 0; c < m; ++c)
+      for (int r = 0; r < m; ++r) {
+        const size_t i = (size_t)r + (size_t)c * m;
+        Lh[r + (size_t)c * MMAX] = cx ? reinterpret_cast<const zd*>(L_host)[i]
+                                      : zd(reinterpret_cast<const double*>(L_host)[i], 0.0);
+        if (R_host)
+          Rh[r + (size_t)c * MMAX] = cx ? reinterpret_cast<const zd*>(R_host)[i]
+                                        : zd(reinterpret_cast<const double*>(R_host)[i], 0.0);
+      }
+    // work layout offsets of L and R are those of kernels_dense.cu (W_L, W_R)
+    RB_CUDA(cudaMemcpyAsync(work + dense_off_L(), Lh.data(), sizeof(zd) * MMAX * MMAX, cudaMemcpyHostToDevice, s));
+    if (R_host)
+      RB_CUDA(cudaMemcpyAsync(work + dense_off_R(), Rh.data(), sizeof(zd) * MMAX * MMAX, cudaMemcpyHostToDevice, s));
+    zd* W = dmalloc<zd>(MMAX * KMAX);
+    zd* Wt = dmalloc<zd>(MMAX * KMAX);
+    double* lam = dmalloc<double>(2 * KMAX + 2);
+    launch_dense_eig_host(!cx, m, nullptr, nullptr, R_host != nullptr, k, W, Wt, lam, nullptr, nullptr, work, s);
+    RB_CUDA(cudaGetLastError());
+    DevState hst;
+    std::vector<zd> Wh((size_t)MMAX * KMAX), Wth((size_t)MMAX * KMAX);
+    std::vector<double> lamh(2 * KMAX + 2);
+    RB_CUDA(cudaMemcpyAsync(&hst, reinterpret_cast<DevState*>(work + dense_state_offset()), sizeof hst,
+                            cudaMemcpyDeviceToHost, s));
+    RB_CUDA(cudaMemcpyAsync(Wh.data(), W, sizeof(zd) * MMAX * KMAX, cudaMemcpyDeviceToHost, s));
+    RB_CUDA(cudaMemcpyAsync(Wth.data(), Wt, sizeof(zd) * MMAX * KMAX, cudaMemcpyDeviceToHost, s));
+    RB_CUDA(cudaMemcpyAsync(lamh.data(), lam, sizeof(double) * (2 * KMAX + 2), cudaMemcpyDeviceToHost, s));
+    RB_CUDA(cudaStreamSynchronize(s));
+    cudaFree(work); cudaFree(W); cudaFree(Wt); cudaFree(lam);
+    if (hst.eig_status != 0) {
+      char buf[200];
+      snprintf(buf, sizeof buf, "dense eigen solve failed: stage %d (1 LU of R, 2 QR), window [%d, %d], sweeps %d / %d",
+               hst.eig_status, hst.dbg[1], hst.dbg[2], hst.dbg[3], hst.dbg[4]);
+      return fail(nullptr, RBICG_ERR_EIG, buf);
+    }
+    *kk = hst.kk;
+    for (int c = 0; c < hst.kk; ++c) {
+      for (int r = 0; r < m; ++r) {
+        const zd w = Wh[(size_t)r * KMAX + c], wt = Wth[(size_t)r * KMAX + c];
+        if (cx) {
+          reinterpret_cast<zd*>(W_host)[r + (size_t)c * m] = w;
+          reinterpret_cast<zd*>(Wt_host)[r + (size_t)c * m] = wt;
+        } else {
+          reinterpret_cast<double*>(W_host)[r + (size_t)c * m] = w.re;
+          reinterpret_cast<double*>(Wt_host)[r + (size_t)c * m] = wt.re;
+        }
+      }
+      if (lam_host) { lam_host[2 * c] = lamh[2 * c]; lam_host[2 * c + 1] = lamh[2 * c + 1]; }
+    }
+    return RBICG_OK;
+  })
+}
+
+extern "C" rbicg_status rbicg_op_svd(rbicg_dtype dtype, int k, const void* S_host, void* M_host, double* sigma,
+                                     void* N_host, void* stream) {
+  if (k < 1 || k > KMAX || !S_host || !M_host || !sigma || !N_host)
+    return fail(nullptr, RBICG_ERR_ARG, "bad SVD arguments (1 <= k <= 32)");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  RB_GUARD(nullptr, {
+    const bool cx = dtype == RBICG_C128;
+    const int ld2 = 2 * k;
+    std::vector<zd> S2((size_t)ld2 * ld2, zd(0.0));
+    for (int c = 0; c < k; ++c) {
+      for (int r = 0; r < k; ++r) {
+        const size_t i = (size_t)r + (size_t)c * k;
+        S2[(size_t)r * ld2 + c] = cx ? reinterpret_cast<const zd*>(S_host)[i]
+                                     : zd(reinterpret_cast<const double*>(S_host)[i], 0.0);
+      }
+      S2[(size_t)c * ld2 + k + c] = zd(1.0);     // unit column norms: no scaling
+      S2[(size_t)(k + c) * ld2 + c] = zd(1.0);
+    }
+    zd* S2d = dmalloc<zd>(S2.size());
+    zd* Nd = dmalloc<zd>(KMAX * KMAX);
+    zd* Md = dmalloc<zd>(KMAX * KMAX);
+    double* sd = dmalloc<double>(KMAX);
+    int* ints = dmalloc<int>(4);
+    RB_CUDA(cudaMemcpyAsync(S2d, S2.data(), sizeof(zd) * S2.size(), cudaMemcpyHostToDevice, s));
+    RB_CUDA(cudaMemcpyAsync(ints, &k, sizeof(int), cudaMemcpyHostToDevice, s));
+    launch_dense_svd(!cx, ints, k, S2d, nullptr, nullptr, 0.0, Nd, Md, sd, ints + 1, nullptr, ints + 2, s);
+    RB_CUDA(cudaGetLastError());
+    std::vector<zd> Nh(KMAX * KMAX), Mh(KMAX * KMAX);
+    RB_CUDA(cudaMemcpyAsync(Nh.data(), Nd, sizeof(zd) * KMAX * KMAX, cudaMemcpyDeviceToHost, s));
+    RB_CUDA(cudaMemcpyAsync(Mh.data(), Md, sizeof(zd) * KMAX * KMAX, cudaMemcpyDeviceToHost, s));
+    RB_CUDA(cudaMemcpyAsync(sigma, sd, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    RB_CUDA(cudaStreamSynchronize(s));
+    cudaFree(S2d); cudaFree(Nd); cudaFree(Md); cudaFree(sd); cudaFree(ints);
+    for (int c = 0; c < k; ++c)
+      for (int r = 0; r < k; ++r) {
+        const zd nv = Nh[(size_t)r * KMAX + c], mv = Mh[(size_t)r * KMAX + c];
+        if (cx) {
+          reinterpret_cast<zd*>(N_host)[r + (size_t)c * k] = nv;
+          reinterpret_cast<zd*>(M_host)[r + (size_t)c * k] = mv;
+        } else {
+          reinterpret_cast<double*>(N_host)[r + (size_t)c * k] = nv.re;
+          reinterpret_cast<double*>(M_host)[r + (size_t)c * k] = mv.re;
+        }
+      }
+    return RBICG_OK;
+  })
+}

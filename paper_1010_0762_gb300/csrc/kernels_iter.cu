@@ -1,0 +1,741 @@
+// kernels_iter.cu -- the per-iteration kernels of Algorithm 2 (RBiCG), the initial projection
+// of eq. (minusXR), the final correction of step 7, the true residual, the random restart of
+// step 3 and the construction of A^H.
+//
+// One iteration i = three grid-wide passes, each ending in a deterministic last-block
+// reduction that writes the scalars of the next pass into DevState:
+//   phase 1: p_i = r_{i-1} + beta_{i-1} p_{i-1}, pt_i likewise (formed while gathering),
+//            z_i = Op p_i, zt_i = Op^H pt_i, and the projections
+//            zeta_i = D_c^{-1} Ct^H z_i, zetat_i = D_c^{-1} C^H zt_i        (eq. (CcheckChat))
+//   phase 2: q_i = z_i - C zeta_i, qt_i = zt_i - Ct zetat_i, (pt_i, q_i) -> alpha_i,
+//            zeta_c += alpha zeta, zetat_c += conj(alpha) zetat
+//   phase 3: x_i, xt_i, r_i, rt_i updates, rho_i = (rt_i, r_i), ||r_i||, ||rt_i||,
+//            stopping test, beta_i = rho_i / rho_{i-1}
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace rb {
+
+// ------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ zd ld_cg(const zd* p) {
+  const double* q = reinterpret_cast<const double*>(p);
+  return zd(__ldcg(q), __ldcg(q + 1));
+}
+
+// Returns true in every thread of the block that arrives last at `cnt` (after all other
+// blocks' partial writes are visible); the last block resets the counter.
+__device__ __forceinline__ bool arrive_last(unsigned int* cnt) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = atomicAdd(cnt, 1u);
+    s_last = (t == gridDim.x - 1);
+    if (s_last) *cnt = 0u;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
+}
+
+// Sum part[b * cnt + c] over b = 0..G-1 for every column c (fixed order: lane-strided per
+// warp, then a fixed shuffle tree); out (shared) receives cnt values.
+template <class A>
+__device__ void reduce_cols(const A* part, int G, int cnt, A* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = w; c < cnt; c += nw) {
+    A s = A(0.0);
+    for (int b = lane; b < G; b += 32) s += ld_cg(part + (int64_t)b * cnt + c);
+    s = warp_sum(s);
+    if (lane == 0) out[c] = s;
+  }
+  __syncthreads();
+}
+
+// Block-sum `cnt` accumulators (register arrays) and write them as this block's row of part.
+template <class A>
+__device__ void write_partials(A* vals, int cnt, A* smem, A* part) {
+  block_sum_vec(vals, cnt, smem);
+  if (threadIdx.x < cnt) part[(int64_t)blockIdx.x * cnt + threadIdx.x] = smem[threadIdx.x];
+}
+
+template <class T> struct shift_of {
+  static __device__ __forceinline__ T get(double re, double) { return T(re); }
+};
+template <class R> struct shift_of<cplx<R>> {
+  static __device__ __forceinline__ cplx<R> get(double re, double im) { return cplx<R>((R)re, (R)im); }
+};
+
+// Op p at one row (Op = A or shift I - A).  `g(j)` returns the gathered vector entry.
+template <class V, class T, class G>
+__device__ __forceinline__ T row_apply(const int* __restrict__ rp, const int* __restrict__ ci,
+                                       const V* __restrict__ va, int row, G g) {
+  T acc = T(0);
+  const int e0 = rp[row], e1 = rp[row + 1];
+  for (int e = e0; e < e1; ++e) acc += vmul(va[e], g(ci[e]));
+  return acc;
+}
+
+template <class A> __device__ __forceinline__ bool finite_acc(A v);
+template <> __device__ __forceinline__ bool finite_acc<double>(double v) { return isfinite(v); }
+template <> __device__ __forceinline__ bool finite_acc<zd>(zd v) { return isfinite(v.re) && isfinite(v.im); }
+
+// ------------------------------------------------------------------------------------
+// phase 1: dual SpMV with on-the-fly p update, projections
+// ------------------------------------------------------------------------------------
+template <class V, class T, int KT>
+__global__ void __launch_bounds__(NTHREADS) k_phase1(OpArgs<V> op, VecArgs<T> v, DevState* st,
+                                                     typename traits<T>::acc* part) {
+  typedef typename traits<T>::acc A;
+  constexpr int KA = KT > 0 ? KT : 1;
+  __shared__ A red[(NTHREADS / 32) * 2 * KA];
+  __shared__ A tot[2 * KA];
+  if (st->done) return;
+  const int i = st->iter + 1;
+  const T beta = from_zd<T>(st->beta), cbeta = conjg(beta);
+  const int64_t so = (int64_t)((i - 1) % v.R) * v.ld;
+  const T* __restrict__ r = v.ring + so;
+  const T* __restrict__ rt = v.ringt + so;
+  const T* __restrict__ po = v.p[(i - 1) & 1];
+  const T* __restrict__ pto = v.pt[(i - 1) & 1];
+  T* __restrict__ pn = v.p[i & 1];
+  T* __restrict__ ptn = v.pt[i & 1];
+  const int k = KT > 0 ? st->kc : 0;
+  const T sh = shift_of<T>::get(op.sh_re, op.sh_im), shc = conjg(sh);
+  T a1[KA], a2[KA];
+#pragma unroll
+  for (int c = 0; c < KA; ++c) { a1[c] = T(0); a2[c] = T(0); }
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += stride) {
+    T z = T(0), zt = T(0);
+    const int e0 = op.rp[row], e1 = op.rp[row + 1];
+    if (op.shared) {
+      for (int e = e0; e < e1; ++e) {
+        const int j = op.ci[e];
+        z += vmul(op.va[e], r[j] + beta * po[j]);
+        zt += vmul(op.tva[e], rt[j] + cbeta * pto[j]);
+      }
+    } else {
+      for (int e = e0; e < e1; ++e) {
+        const int j = op.ci[e];
+        z += vmul(op.va[e], r[j] + beta * po[j]);
+      }
+      const int f0 = op.trp[row], f1 = op.trp[row + 1];
+      for (int e = f0; e < f1; ++e) {
+        const int j = op.tci[e];
+        zt += vmul(op.tva[e], rt[j] + cbeta * pto[j]);
+      }
+    }
+    const T prow = r[row] + beta * po[row];
+    const T ptrow = rt[row] + cbeta * pto[row];
+    pn[row] = prow;
+    ptn[row] = ptrow;
+    if (op.has_shift) { z = sh * prow - z; zt = shc * ptrow - zt; }
+    v.z[row] = z;
+    v.zt[row] = zt;
+    if (KT > 0) {
+      const T* __restrict__ crow = v.C + (int64_t)row * v.ldk;
+      const T* __restrict__ ctrow = v.Ct + (int64_t)row * v.ldk;
+#pragma unroll
+      for (int c = 0; c < KA; ++c)
+        if (c < k) { a1[c] += cmul(ctrow[c], z); a2[c] += cmul(crow[c], zt); }
+    }
+  }
+  if (KT == 0) return;
+  A vals[2 * KA];
+#pragma unroll
+  for (int c = 0; c < KA; ++c) { vals[c] = cvt<A>(a1[c]); vals[KA + c] = cvt<A>(a2[c]); }
+  write_partials(vals, 2 * KA, red, part);
+  if (!arrive_last(&st->cnt[0])) return;
+  reduce_cols(part, gridDim.x, 2 * KA, tot);
+  if (threadIdx.x < k) {
+    const double d = st->Dc[threadIdx.x];
+    st->zeta[threadIdx.x] = to_zd(tot[threadIdx.x] * (1.0 / d));
+    st->zetat[threadIdx.x] = to_zd(tot[KA + threadIdx.x] * (1.0 / d));
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// phase 2: q = z - C zeta, qt = zt - Ct zetat, (pt, q) -> alpha
+// ------------------------------------------------------------------------------------
+template <class V, class T, int KT>
+__global__ void __launch_bounds__(NTHREADS) k_phase2(OpArgs<V> op, VecArgs<T> v, DevState* st,
+                                                     typename traits<T>::acc* part) {
+  typedef typename traits<T>::acc A;
+  constexpr int KA = KT > 0 ? KT : 1;
+  __shared__ A red[(NTHREADS / 32) * 3];
+  __shared__ A tot[3];
+  if (st->done) return;
+  const int i = st->iter + 1;
+  const int k = KT > 0 ? st->kc : 0;
+  T ze[KA], zet[KA];
+#pragma unroll
+  for (int c = 0; c < KA; ++c) {
+    ze[c] = c < k ? from_zd<T>(st->zeta[c]) : T(0);
+    zet[c] = c < k ? from_zd<T>(st->zetat[c]) : T(0);
+  }
+  const T* __restrict__ pt = v.pt[i & 1];
+  A pq = A(0.0), nq = A(0.0), npt = A(0.0);
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += stride) {
+    T q = v.z[row], qt = v.zt[row];
+    if (KT > 0) {
+      const T* __restrict__ crow = v.C + (int64_t)row * v.ldk;
+      const T* __restrict__ ctrow = v.Ct + (int64_t)row * v.ldk;
+#pragma unroll
+      for (int c = 0; c < KA; ++c)
+        if (c < k) { q -= crow[c] * ze[c]; qt -= ctrow[c] * zet[c]; }
+      v.z[row] = q;
+      v.zt[row] = qt;
+    }
+    const T ptr = pt[row];
+    pq += cmul(cvt<A>(ptr), cvt<A>(q));
+    nq += A((double)abs2(q));
+    npt += A((double)abs2(ptr));
+  }
+  A vals[3] = {pq, nq, npt};
+  write_partials(vals, 3, red, part);
+  if (!arrive_last(&st->cnt[1])) return;
+  reduce_cols(part, gridDim.x, 3, tot);
+  if (threadIdx.x == 0) {
+    const zd PQ = to_zd(tot[0]);
+    const double NQ = real_of(tot[1]), NPT = real_of(tot[2]);
+    if (!isfinite(PQ.re) || !isfinite(PQ.im) || !isfinite(NQ) || !isfinite(NPT)) {
+      st->done = DONE_NONFINITE;
+    } else if (absval(PQ) <= BREAKDOWN_EPS * sqrt(NQ) * sqrt(NPT)) {
+      st->done = DONE_BREAK_PQ;
+    } else {
+      const zd al = st->rho / PQ;
+      st->alpha = al;
+      st->h_alpha[i % HR] = al;
+    }
+  }
+  __syncthreads();
+  if (st->done) return;
+  if (threadIdx.x < k) {
+    const zd al = st->alpha;
+    const int c = threadIdx.x;
+    const zd zc = st->zeta[c], ztc = st->zetat[c];
+    st->zeta_c[c] += al * zc;
+    st->zetat_c[c] += conjg(al) * ztc;
+    st->h_zeta[i % HR][c] = zc;
+    st->h_zetat[i % HR][c] = ztc;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// phase 3: x, r updates, rho, norms, stopping test, beta
+// ------------------------------------------------------------------------------------
+template <class V, class T>
+__global__ void __launch_bounds__(NTHREADS) k_phase3(OpArgs<V> op, VecArgs<T> v, DevState* st,
+                                                     typename traits<T>::acc* part) {
+  typedef typename traits<T>::acc A;
+  __shared__ A red[(NTHREADS / 32) * 3];
+  __shared__ A tot[3];
+  if (st->done) return;
+  const int i = st->iter + 1;
+  const T al = from_zd<T>(st->alpha), cal = conjg(al);
+  const int64_t so = (int64_t)((i - 1) % v.R) * v.ld, sn = (int64_t)(i % v.R) * v.ld;
+  const T* __restrict__ ro = v.ring + so;
+  const T* __restrict__ rto = v.ringt + so;
+  T* __restrict__ rn = v.ring + sn;
+  T* __restrict__ rtn = v.ringt + sn;
+  const T* __restrict__ p = v.p[i & 1];
+  const T* __restrict__ pt = v.pt[i & 1];
+  A rho = A(0.0), n1 = A(0.0), n2 = A(0.0);
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += stride) {
+    v.x[row] = v.x[row] + al * p[row];
+    v.xt[row] = v.xt[row] + cal * pt[row];
+    const T a = ro[row] - al * v.z[row];
+    const T b = rto[row] - cal * v.zt[row];
+    rn[row] = a;
+    rtn[row] = b;
+    rho += cmul(cvt<A>(b), cvt<A>(a));
+    n1 += A((double)abs2(a));
+    n2 += A((double)abs2(b));
+  }
+  A vals[3] = {rho, n1, n2};
+  write_partials(vals, 3, red, part);
+  if (!arrive_last(&st->cnt[2])) return;
+  reduce_cols(part, gridDim.x, 3, tot);
+  if (threadIdx.x == 0) {
+    const zd RHO = to_zd(tot[0]);
+    const double rr = sqrt(real_of(tot[1])), rtr = sqrt(real_of(tot[2]));
+    const zd beta = RHO / st->rho;
+    st->h_rnorm[i % HR] = rr;
+    st->h_rho[i % HR] = RHO;
+    st->h_beta[i % HR] = beta;
+    st->rnorm = rr;
+    st->rtnorm = rtr;
+    st->iter = i;
+    const bool conv = rr <= st->tol * st->bnorm && (st->btnorm == 0.0 || rtr <= st->tol * st->btnorm);
+    if (!isfinite(rr) || !isfinite(rtr) || !isfinite(RHO.re) || !isfinite(RHO.im)) st->done = DONE_NONFINITE;
+    else if (conv) st->done = DONE_CONVERGED;
+    else if (absval(RHO) <= BREAKDOWN_EPS * rr * rtr) st->done = DONE_BREAK_RHO;
+    else if (i >= st->max_itn) st->done = DONE_MAXIT;
+    st->rho = RHO;
+    st->beta = beta;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// initial projection, eq. (minusXR): r_{-1} = b - Op x_{-1}, coef = D_c^{-1} Ct^H r_{-1},
+// x_0 = x_{-1} + U coef, r_0 = r_{-1} - C coef (and the dual with Ut, C, Ct swapped).
+// ------------------------------------------------------------------------------------
+template <class V, class T, int KT>
+__global__ void __launch_bounds__(NTHREADS) k_init_a(OpArgs<V> op, VecArgs<T> v, DevState* st,
+                                                     typename traits<T>::acc* part, int dual_only) {
+  typedef typename traits<T>::acc A;
+  constexpr int KA = KT > 0 ? KT : 1;
+  constexpr int CNT = 2 * KA + 2;
+  __shared__ A red[(NTHREADS / 32) * CNT];
+  __shared__ A tot[CNT];
+  T* __restrict__ r = v.ring;   // slot 0 holds r_{-1}, then r_0
+  T* __restrict__ rt = v.ringt;
+  const int k = KT > 0 ? st->kc : 0;
+  const T sh = shift_of<T>::get(op.sh_re, op.sh_im), shc = conjg(sh);
+  T a1[KA], a2[KA];
+  A nb = A(0.0), nbt = A(0.0);
+#pragma unroll
+  for (int c = 0; c < KA; ++c) { a1[c] = T(0); a2[c] = T(0); }
+  const T* __restrict__ x = v.x;
+  const T* __restrict__ xt = v.xt;
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += stride) {
+    T res = T(0), rest = T(0);
+    if (!dual_only) {
+      T ax = row_apply<V, T>(op.rp, op.ci, op.va, row, [&](int j) { return x[j]; });
+      if (op.has_shift) ax = sh * x[row] - ax;
+      res = v.b[row] - ax;
+      r[row] = res;
+      nb += A((double)abs2(v.b[row]));
+    }
+    T atx = row_apply<V, T>(op.trp, op.tci, op.tva, row, [&](int j) { return xt[j]; });
+    if (op.has_shift) atx = shc * xt[row] - atx;
+    rest = v.bt[row] - atx;
+    rt[row] = rest;
+    nbt += A((double)abs2(v.bt[row]));
+    if (KT > 0) {
+      const T* __restrict__ crow = v.C + (int64_t)row * v.ldk;
+      const T* __restrict__ ctrow = v.Ct + (int64_t)row * v.ldk;
+#pragma unroll
+      for (int c = 0; c < KA; ++c)
+        if (c < k) { a1[c] += cmul(ctrow[c], res); a2[c] += cmul(crow[c], rest); }
+    }
+  }
+  A vals[CNT];
+#pragma unroll
+  for (int c = 0; c < KA; ++c) { vals[c] = cvt<A>(a1[c]); vals[KA + c] = cvt<A>(a2[c]); }
+  vals[2 * KA] = nb;
+  vals[2 * KA + 1] = nbt;
+  write_partials(vals, CNT, red, part);
+  if (!arrive_last(&st->cnt[3])) return;
+  reduce_cols(part, gridDim.x, CNT, tot);
+  if (threadIdx.x < k) {
+    const double d = st->Dc[threadIdx.x];
+    if (!dual_only) st->coef[threadIdx.x] = to_zd(tot[threadIdx.x] * (1.0 / d));
+    st->coeft[threadIdx.x] = to_zd(tot[KA + threadIdx.x] * (1.0 / d));
+  }
+  if (threadIdx.x == 0) {
+    if (!dual_only) st->bnorm = sqrt(real_of(tot[2 * KA]));
+    st->btnorm = sqrt(real_of(tot[2 * KA + 1]));
+  }
+}
+
+template <class V, class T, int KT>
+__global__ void __launch_bounds__(NTHREADS) k_init_b(OpArgs<V> op, VecArgs<T> v, DevState* st,
+                                                     typename traits<T>::acc* part, int dual_only) {
+  typedef typename traits<T>::acc A;
+  constexpr int KA = KT > 0 ? KT : 1;
+  __shared__ A red[(NTHREADS / 32) * 3];
+  __shared__ A tot[3];
+  const int k = KT > 0 ? st->kc : 0;
+  T cf[KA], cft[KA];
+#pragma unroll
+  for (int c = 0; c < KA; ++c) {
+    cf[c] = c < k ? from_zd<T>(st->coef[c]) : T(0);
+    cft[c] = c < k ? from_zd<T>(st->coeft[c]) : T(0);
+  }
+  T* __restrict__ r = v.ring;
+  T* __restrict__ rt = v.ringt;
+  A rho = A(0.0), n1 = A(0.0), n2 = A(0.0);
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += stride) {
+    T a = r[row], b = rt[row];
+    if (KT > 0) {
+      const int64_t o = (int64_t)row * v.ldk;
+      T dx = T(0), dr = T(0), dxt = T(0), drt = T(0);
+#pragma unroll
+      for (int c = 0; c < KA; ++c)
+        if (c < k) {
+          if (!dual_only) { dx += v.U[o + c] * cf[c]; dr += v.C[o + c] * cf[c]; }
+          dxt += v.Ut[o + c] * cft[c];
+          drt += v.Ct[o + c] * cft[c];
+        }
+      if (!dual_only) { v.x[row] = v.x[row] + dx; a = a - dr; r[row] = a; }
+      v.xt[row] = v.xt[row] + dxt;
+      b = b - drt;
+      rt[row] = b;
+    }
+    v.p[0][row] = T(0);
+    v.pt[0][row] = T(0);
+    rho += cmul(cvt<A>(b), cvt<A>(a));
+    n1 += A((double)abs2(a));
+    n2 += A((double)abs2(b));
+  }
+  A vals[3] = {rho, n1, n2};
+  write_partials(vals, 3, red, part);
+  if (!arrive_last(&st->cnt[4])) return;
+  reduce_cols(part, gridDim.x, 3, tot);
+  if (threadIdx.x < KMAX) { st->zeta_c[threadIdx.x] = zd(); st->zetat_c[threadIdx.x] = zd(); }
+  if (threadIdx.x == 0) {
+    const zd RHO = to_zd(tot[0]);
+    const double rr = sqrt(real_of(tot[1])), rtr = sqrt(real_of(tot[2]));
+    st->rho = RHO;
+    st->beta = zd();
+    st->iter = 0;
+    st->rnorm = rr;
+    st->rtnorm = rtr;
+    st->h_rho[0] = RHO;
+    st->h_rnorm[0] = rr;
+    st->h_beta[0] = zd();
+    st->h_alpha[0] = zd();
+    for (int c = 0; c < KMAX; ++c) { st->h_zeta[0][c] = zd(); st->h_zetat[0][c] = zd(); }
+    const bool conv = rr <= st->tol * st->bnorm && (st->btnorm == 0.0 || rtr <= st->tol * st->btnorm);
+    st->restart = (absval(RHO) <= BREAKDOWN_EPS * rr * rtr) && !conv;
+    st->done = conv ? DONE_CONVERGED : RUNNING;
+    if (!isfinite(rr) || !isfinite(rtr)) st->done = DONE_NONFINITE;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// step 7 (x -= U zeta_c, xt -= Ut zetat_c) and the FP64 true residual
+// ------------------------------------------------------------------------------------
+template <class T, int KT>
+__global__ void __launch_bounds__(NTHREADS) k_fin_a(int n, VecArgs<T> v, DevState* st) {
+  constexpr int KA = KT > 0 ? KT : 1;
+  const int k = st->kc;
+  T zc[KA], ztc[KA];
+#pragma unroll
+  for (int c = 0; c < KA; ++c) {
+    zc[c] = c < k ? from_zd<T>(st->zeta_c[c]) : T(0);
+    ztc[c] = c < k ? from_zd<T>(st->zetat_c[c]) : T(0);
+  }
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += stride) {
+    const int64_t o = (int64_t)row * v.ldk;
+    T dx = T(0), dxt = T(0);
+#pragma unroll
+    for (int c = 0; c < KA; ++c)
+      if (c < k) { dx += v.U[o + c] * zc[c]; dxt += v.Ut[o + c] * ztc[c]; }
+    v.x[row] = v.x[row] - dx;
+    v.xt[row] = v.xt[row] - dxt;
+  }
+}
+
+template <class V, class T>
+__global__ void __launch_bounds__(NTHREADS) k_fin_b(OpArgs<V> op, VecArgs<T> v, DevState* st,
+                                                    typename traits<T>::acc* part) {
+  typedef typename traits<T>::acc A;
+  __shared__ A red[(NTHREADS / 32) * 2];
+  __shared__ A tot[2];
+  const T sh = shift_of<T>::get(op.sh_re, op.sh_im), shc = conjg(sh);
+  const T* __restrict__ x = v.x;
+  const T* __restrict__ xt = v.xt;
+  A n1 = A(0.0), n2 = A(0.0);
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += stride) {
+    T ax = row_apply<V, T>(op.rp, op.ci, op.va, row, [&](int j) { return x[j]; });
+    if (op.has_shift) ax = sh * x[row] - ax;
+    T atx = row_apply<V, T>(op.trp, op.tci, op.tva, row, [&](int j) { return xt[j]; });
+    if (op.has_shift) atx = shc * xt[row] - atx;
+    n1 += A((double)abs2(v.b[row] - ax));
+    n2 += A((double)abs2(v.bt[row] - atx));
+  }
+  A vals[2] = {n1, n2};
+  write_partials(vals, 2, red, part);
+  if (!arrive_last(&st->cnt[5])) return;
+  reduce_cols(part, gridDim.x, 2, tot);
+  if (threadIdx.x == 0) {
+    st->true_rnorm = sqrt(real_of(tot[0]));
+    st->true_rtnorm = sqrt(real_of(tot[1]));
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11) restart vector in [-1, 1): element e uses counter
+// (e lo, e hi, 0, 0) and key (seed lo, seed hi); top 53 bits of (w1:w0) [and (w3:w2)].
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+__device__ __forceinline__ double u53(uint32_t lo, uint32_t hi) {
+  const uint64_t w = ((uint64_t)hi << 32) | lo;
+  return 2.0 * ((double)(w >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+template <class T> struct philox_store;
+template <> struct philox_store<double> {
+  static __device__ void put(double* o, const uint32_t c[4]) { *o = u53(c[0], c[1]); }
+};
+template <> struct philox_store<float> {
+  static __device__ void put(float* o, const uint32_t c[4]) { *o = (float)u53(c[0], c[1]); }
+};
+template <class R> struct philox_store<cplx<R>> {
+  static __device__ void put(cplx<R>* o, const uint32_t c[4]) { *o = cplx<R>((R)u53(c[0], c[1]), (R)u53(c[2], c[3])); }
+};
+template <class T>
+__global__ void k_philox(T* out, int64_t n, uint64_t seed) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c[4] = {(uint32_t)(e & 0xffffffffu), (uint32_t)(e >> 32), 0u, 0u};
+    philox10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+    philox_store<T>::put(out + e, c);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// CSR validation and A^H construction
+// ------------------------------------------------------------------------------------
+__global__ void k_validate(int n, int64_t nnz, const int* rp, const int* ci, int* flag) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += stride) {
+    const int e0 = rp[row], e1 = rp[row + 1];
+    if (row == 0 && e0 != 0) atomicOr(flag, 1);
+    if (row == n - 1 && (int64_t)e1 != nnz) atomicOr(flag, 2);
+    if (e1 < e0 || e0 < 0 || (int64_t)e1 > nnz) { atomicOr(flag, 4); continue; }
+    int prev = -1;
+    for (int e = e0; e < e1; ++e) {
+      const int j = ci[e];
+      if (j < 0 || j >= n) atomicOr(flag, 8);
+      if (j <= prev) atomicOr(flag, 16);
+      prev = j;
+    }
+  }
+}
+
+RB_HD double conjv(double a) { return a; }
+RB_HD float conjv(float a) { return a; }
+template <class R> RB_HD cplx<R> conjv(cplx<R> a) { return conjg(a); }
+
+// Structurally symmetric pattern: the A^H entry at (i, j) is conj(A(j, i)), found by binary
+// search in row j.  flag |= 1 when some (j, i) is missing.
+template <class V>
+__global__ void k_adj_shared(int n, const int* rp, const int* ci, const V* va, V* tva, int* flag) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += stride) {
+    const int e0 = rp[row], e1 = rp[row + 1];
+    for (int e = e0; e < e1; ++e) {
+      const int j = ci[e];
+      int lo = rp[j], hi = rp[j + 1] - 1, f = -1;
+      while (lo <= hi) {
+        const int mid = (lo + hi) >> 1, cm = ci[mid];
+        if (cm == row) { f = mid; break; }
+        if (cm < row) lo = mid + 1; else hi = mid - 1;
+      }
+      if (f < 0) { atomicOr(flag, 1); tva[e] = V(0); }
+      else tva[e] = conjv(va[f]);
+    }
+  }
+}
+
+__global__ void k_count_cols(int n, const int* rp, const int* ci, int* cnt) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += stride)
+    for (int e = rp[row]; e < rp[row + 1]; ++e) atomicAdd(cnt + ci[e], 1);
+}
+
+// exclusive scan in place over a[0..m) by one block (setup only)
+__global__ void k_scan_one_block(int* a, int m) {
+  __shared__ int sums[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int chunk = (m + T - 1) / T;
+  const int b = t * chunk, e = min(m, b + chunk);
+  int s = 0;
+  for (int i = b; i < e; ++i) s += a[i];
+  sums[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int acc = 0;
+    for (int i = 0; i < T; ++i) { const int v = sums[i]; sums[i] = acc; acc += v; }
+  }
+  __syncthreads();
+  int acc = sums[t];
+  for (int i = b; i < e; ++i) { const int v = a[i]; a[i] = acc; acc += v; }
+}
+
+template <class V>
+__global__ void k_scatter_adj(int n, const int* rp, const int* ci, const V* va, const int* trp, int* cursor,
+                              int* tci, V* tva) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += stride)
+    for (int e = rp[row]; e < rp[row + 1]; ++e) {
+      const int j = ci[e];
+      const int pos = trp[j] + atomicAdd(cursor + j, 1);
+      tci[pos] = row;
+      tva[pos] = conjv(va[e]);
+    }
+}
+
+template <class V>
+__global__ void k_sort_rows(int n, const int* trp, int* tci, V* tva) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += stride) {
+    const int e0 = trp[row], e1 = trp[row + 1];
+    for (int a = e0 + 1; a < e1; ++a) {
+      const int c = tci[a];
+      const V v = tva[a];
+      int b = a - 1;
+      while (b >= e0 && tci[b] > c) { tci[b + 1] = tci[b]; tva[b + 1] = tva[b]; --b; }
+      tci[b + 1] = c;
+      tva[b + 1] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------
+#define RB_KT_DISPATCH(kt, CALL) \
+  switch (kt) {                  \
+    case 0: CALL(0); break;      \
+    case 8: CALL(8); break;      \
+    case 16: CALL(16); break;    \
+    case 24: CALL(24); break;    \
+    default: CALL(32); break;    \
+  }
+
+template <class V, class T>
+void launch_phase1(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
+                   cudaStream_t s) {
+  typedef typename traits<T>::acc A;
+#define RB_CALL(K) k_phase1<V, T, K><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part)
+  RB_KT_DISPATCH(kt, RB_CALL)
+#undef RB_CALL
+}
+template <class V, class T>
+void launch_phase2(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
+                   cudaStream_t s) {
+  typedef typename traits<T>::acc A;
+#define RB_CALL(K) k_phase2<V, T, K><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part)
+  RB_KT_DISPATCH(kt, RB_CALL)
+#undef RB_CALL
+}
+template <class V, class T>
+void launch_phase3(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int grid,
+                   cudaStream_t s) {
+  typedef typename traits<T>::acc A;
+  k_phase3<V, T><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part);
+}
+template <class V, class T>
+void launch_init(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
+                 int dual_only, cudaStream_t s) {
+  typedef typename traits<T>::acc A;
+#define RB_CALL(K) k_init_a<V, T, K><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part, dual_only)
+  RB_KT_DISPATCH(kt, RB_CALL)
+#undef RB_CALL
+#define RB_CALL(K) k_init_b<V, T, K><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part, dual_only)
+  RB_KT_DISPATCH(kt, RB_CALL)
+#undef RB_CALL
+}
+template <class V, class T>
+void launch_finish(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
+                   cudaStream_t s) {
+  typedef typename traits<T>::acc A;
+#define RB_CALL(K) k_fin_a<T, K><<<grid, NTHREADS, 0, s>>>(op.n, v, st)
+  RB_KT_DISPATCH(kt, RB_CALL)
+#undef RB_CALL
+  k_fin_b<V, T><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part);
+}
+template <class T>
+void launch_philox(T* out, int64_t n, uint64_t seed, cudaStream_t s) {
+  k_philox<T><<<256, 256, 0, s>>>(out, n, seed);
+}
+
+int validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* flag_dev, cudaStream_t s) {
+  cudaMemsetAsync(flag_dev, 0, sizeof(int), s);
+  k_validate<<<std::max(1, std::min((n + 255) / 256, 1024)), 256, 0, s>>>(n, nnz, rp, ci, flag_dev);
+  return (int)cudaGetLastError();
+}
+
+template <class V>
+int build_adjoint(int n, const int* rp, const int* ci, const V* va, int** trp, int** tci, V** tva, int* shared,
+                  int* flag_dev, cudaStream_t s) {
+  // *tva must hold nnz values; *trp / *tci are allocated here only for unsymmetric patterns.
+  const int grid = std::max(1, std::min((n + 255) / 256, 2048));
+  cudaMemsetAsync(flag_dev, 0, sizeof(int), s);
+  k_adj_shared<V><<<grid, 256, 0, s>>>(n, rp, ci, va, *tva, flag_dev);
+  int flag = 0;
+  cudaMemcpyAsync(&flag, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return (int)e;
+  if (flag == 0) {
+    *shared = 1;
+    *trp = const_cast<int*>(rp);
+    *tci = const_cast<int*>(ci);
+    return 0;
+  }
+  *shared = 0;
+  int nnz = 0;
+  cudaMemcpyAsync(&nnz, rp + n, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  int* cur = nullptr;
+  if ((e = cudaMalloc(trp, sizeof(int) * (n + 1))) != cudaSuccess) return (int)e;
+  if ((e = cudaMalloc(tci, sizeof(int) * std::max(1, nnz))) != cudaSuccess) return (int)e;
+  if ((e = cudaMalloc(&cur, sizeof(int) * (n + 1))) != cudaSuccess) return (int)e;
+  cudaMemsetAsync(*trp, 0, sizeof(int) * (n + 1), s);
+  cudaMemsetAsync(cur, 0, sizeof(int) * (n + 1), s);
+  k_count_cols<<<grid, 256, 0, s>>>(n, rp, ci, *trp);   // trp[c] = entries in column c
+  k_scan_one_block<<<1, 1024, 0, s>>>(*trp, n + 1);     // exclusive scan -> row starts of A^H
+  k_scatter_adj<V><<<grid, 256, 0, s>>>(n, rp, ci, va, *trp, cur, *tci, *tva);
+  k_sort_rows<V><<<grid, 256, 0, s>>>(n, *trp, *tci, *tva);
+  e = cudaStreamSynchronize(s);
+  cudaFree(cur);
+  return (int)e;
+}
+
+// ------------------------------------------------------------------------------------
+// explicit instantiations
+// ------------------------------------------------------------------------------------
+#define RB_INST_VT(V, T)                                                                                  \
+  template void launch_phase1<V, T>(const OpArgs<V>&, const VecArgs<T>&, DevState*, void*, int, int,       \
+                                    cudaStream_t);                                                         \
+  template void launch_phase2<V, T>(const OpArgs<V>&, const VecArgs<T>&, DevState*, void*, int, int,       \
+                                    cudaStream_t);                                                         \
+  template void launch_phase3<V, T>(const OpArgs<V>&, const VecArgs<T>&, DevState*, void*, int,            \
+                                    cudaStream_t);                                                         \
+  template void launch_init<V, T>(const OpArgs<V>&, const VecArgs<T>&, DevState*, void*, int, int, int,    \
+                                  cudaStream_t);                                                           \
+  template void launch_finish<V, T>(const OpArgs<V>&, const VecArgs<T>&, DevState*, void*, int, int,       \
+                                    cudaStream_t);
+
+RB_INST_VT(double, double)
+RB_INST_VT(float, float)
+RB_INST_VT(double, cplx<double>)
+RB_INST_VT(cplx<double>, cplx<double>)
+RB_INST_VT(float, cplx<float>)
+RB_INST_VT(cplx<float>, cplx<float>)
+
+template void launch_philox<double>(double*, int64_t, uint64_t, cudaStream_t);
+template void launch_philox<float>(float*, int64_t, uint64_t, cudaStream_t);
+template void launch_philox<cplx<double>>(cplx<double>*, int64_t, uint64_t, cudaStream_t);
+template void launch_philox<cplx<float>>(cplx<float>*, int64_t, uint64_t, cudaStream_t);
+template int build_adjoint<double>(int, const int*, const int*, const double*, int**, int**, double**, int*,
+                                   int*, cudaStream_t);
+template int build_adjoint<float>(int, const int*, const int*, const float*, int**, int**, float**, int*, int*,
+                                  cudaStream_t);
+template int build_adjoint<cplx<double>>(int, const int*, const int*, const cplx<double>*, int**, int**,
+                                         cplx<double>**, int*, int*, cudaStream_t);
+template int build_adjoint<cplx<float>>(int, const int*, const int*, const cplx<float>*, int**, int**,
+                                        cplx<float>**, int*, int*, cudaStream_t);
+
+}  // namespace rb

@@ -1,0 +1,276 @@
+"""Python binding of librbicg.so (include/rbicg.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA library; PyTorch provides device memory and
+streams.  Importing this module loads the library and raises if it is missing (there is no
+CPU fallback).  Build it with `python -m paper_1010_0762_gb300.build`.
+
+Names follow the C ABI: Solver.update_recycle / Solver.solve_pair / Solver.destroy wrap
+rbicg_update_recycle / rbicg_solve_pair / rbicg_destroy; op_* wrap the component entry
+points.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librbicg.so")
+
+OK, NOT_CONVERGED, BREAKDOWN_RHO, BREAKDOWN_PQ, RECYCLE_EMPTY = 0, 1, 2, 3, 4
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_EIG = -1, -2, -3, -4, -5, -6
+R64, C128 = 0, 1
+FP64, FP32_REFINED = 0, 1
+
+
+class Params(C.Structure):
+    _fields_ = [("k", C.c_int), ("s", C.c_int), ("max_itn", C.c_int), ("tol", C.c_double),
+                ("svd_tol", C.c_double), ("inner_tol", C.c_double), ("refine_max", C.c_int),
+                ("precision", C.c_int), ("seed", C.c_uint64), ("setup_fp32", C.c_int),
+                ("recycle", C.c_int), ("inner_svd_tol", C.c_double)]
+
+
+class CSRStruct(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p),
+                ("val", C.c_void_p), ("val_complex", C.c_int), ("has_shift", C.c_int),
+                ("shift_re", C.c_double), ("shift_im", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("iters", C.c_int), ("cycles", C.c_int), ("recycle_dim", C.c_int), ("refine_steps", C.c_int),
+                ("relres", C.c_double), ("relres_dual", C.c_double), ("true_relres", C.c_double),
+                ("true_relres_dual", C.c_double), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class RBiCGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("rbicg status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("librbicg.so not found at %s; build it with `python -m paper_1010_0762_gb300.build`"
+                           % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, ci, cd = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "rbicg_default_params": (None, [C.POINTER(Params)]),
+        "rbicg_create": (ci, [C.POINTER(Params), i64, ci, vp, C.POINTER(vp)]),
+        "rbicg_update_recycle": (ci, [vp, C.POINTER(CSRStruct)]),
+        "rbicg_solve_pair": (ci, [vp, C.POINTER(CSRStruct), vp, vp, vp, vp, C.POINTER(Result)]),
+        "rbicg_solve_batch": (ci, [C.POINTER(vp), C.POINTER(C.POINTER(CSRStruct)), C.POINTER(vp), C.POINTER(vp),
+                                   C.POINTER(vp), C.POINTER(vp), ci, C.POINTER(Result)]),
+        "rbicg_export_recycle": (ci, [vp, vp, vp, C.POINTER(ci)]),
+        "rbicg_import_recycle": (ci, [vp, vp, vp, ci]),
+        "rbicg_reset": (ci, [vp]),
+        "rbicg_destroy": (ci, [vp]),
+        "rbicg_last_error": (C.c_char_p, [vp]),
+        "rbicg_launch_count": (i64, [vp]),
+        "rbicg_profile": (ci, [vp, ci, C.POINTER(cd), C.POINTER(i64)]),
+        "rbicg_op_dual_spmv_project": (ci, [C.POINTER(CSRStruct), ci, vp, vp, vp, vp, cd, cd, vp, vp, ci, ci,
+                                            vp, vp, vp, vp, vp, vp, vp, vp]),
+        "rbicg_op_gram": (ci, [ci, i64, vp, ci, ci, vp, ci, ci, ci, vp, vp]),
+        "rbicg_op_eig_select": (ci, [ci, ci, vp, vp, ci, vp, vp, vp, C.POINTER(ci), vp]),
+        "rbicg_op_svd": (ci, [ci, ci, vp, vp, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(st, handle=None):
+    if st < 0:
+        msg = lib.rbicg_last_error(handle)
+        raise RBiCGError(st, msg.decode() if msg else "")
+    return st
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def default_params(**kw):
+    p = Params()
+    lib.rbicg_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": FP64, "fp32_refined": FP32_REFINED}[v]
+        setattr(p, k, v)
+    return p
+
+
+class Operator:
+    """A sparse operator on the device: A (CSR) or, with `shift`, (shift I - A).
+
+    Keeps the device tensors alive while the library may read them.
+    """
+
+    def __init__(self, row_ptr, col_idx, val, shift=None):
+        self.row_ptr = row_ptr.contiguous()
+        self.col_idx = col_idx.contiguous()
+        self.val = val.contiguous()
+        assert self.row_ptr.dtype == torch.int32 and self.col_idx.dtype == torch.int32
+        assert self.val.dtype in (torch.float64, torch.complex128)
+        self.n = self.row_ptr.numel() - 1
+        self.shift = shift
+        s = CSRStruct()
+        s.n = self.n
+        s.nnz = self.col_idx.numel()
+        s.row_ptr = self.row_ptr.data_ptr()
+        s.col_idx = self.col_idx.data_ptr() if self.col_idx.numel() else 0
+        s.val = self.val.data_ptr() if self.val.numel() else 0
+        s.val_complex = 1 if self.val.dtype == torch.complex128 else 0
+        s.has_shift = 1 if shift is not None else 0
+        if shift is not None:
+            s.shift_re = float(np.real(shift))
+            s.shift_im = float(np.imag(shift))
+        self.struct = s
+
+    @classmethod
+    def from_csr(cls, A, device="cuda", shift=None):
+        """From paper_1010_0762_gb300.inputs.CSR (or anything with row_ptr/col_idx/val arrays)."""
+        val = np.asarray(A.val)
+        vt = torch.complex128 if np.iscomplexobj(val) else torch.float64
+        return cls(torch.as_tensor(np.asarray(A.row_ptr, dtype=np.int32), device=device),
+                   torch.as_tensor(np.asarray(A.col_idx, dtype=np.int32), device=device),
+                   torch.as_tensor(val, dtype=vt, device=device), shift=shift)
+
+
+class Solver:
+    """RBiCG solver for a sequence of dual systems of order n (rbicg_create)."""
+
+    def __init__(self, n, dtype=R64, stream=None, **params):
+        self.n = int(n)
+        self.dtype = dtype
+        self.params = default_params(**params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib.rbicg_create(C.byref(self.params), self.n, dtype, _stream(self.stream), C.byref(h)))
+        self.h = h
+        self._op = None
+
+    def update_recycle(self, op: Operator):
+        self._op = op
+        _check(lib.rbicg_update_recycle(self.h, C.byref(op.struct)), self.h)
+
+    def solve_pair(self, op, b, bt, x, xt):
+        """Solve A x = b, A^H xt = bt; x, xt hold the initial guesses and receive the solutions."""
+        if op is not None:
+            self._op = op
+        r = Result()
+        opp = C.byref(op.struct) if op is not None else None
+        st = lib.rbicg_solve_pair(self.h, opp, _ptr(b), _ptr(bt), _ptr(x), _ptr(xt), C.byref(r))
+        _check(st, self.h)
+        return r.as_dict()
+
+    def export_recycle(self):
+        k = self.params.k
+        dt = torch.complex128 if self.dtype == C128 else torch.float64
+        U = torch.zeros(self.n, k, dtype=dt, device="cuda")
+        Ut = torch.zeros(self.n, k, dtype=dt, device="cuda")
+        p = C.c_int(0)
+        _check(lib.rbicg_export_recycle(self.h, _ptr(U), _ptr(Ut), C.byref(p)), self.h)
+        return U[:, :p.value].clone(), Ut[:, :p.value].clone()
+
+    def import_recycle(self, U, Ut):
+        U = U.contiguous(); Ut = Ut.contiguous()
+        _check(lib.rbicg_import_recycle(self.h, _ptr(U), _ptr(Ut), U.shape[1]), self.h)
+
+    def reset(self):
+        _check(lib.rbicg_reset(self.h), self.h)
+
+    def launch_count(self):
+        return int(lib.rbicg_launch_count(self.h))
+
+    def destroy(self):
+        if getattr(self, "h", None):
+            lib.rbicg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ component entry points
+def op_dual_spmv_project(op: Operator, r, rt, p_old, pt_old, beta, C_=None, Ct=None, Dc=None, stream=None):
+    """Phase 1 of an iteration: returns (p, pt, z, zt, zeta, zetat)."""
+    cx = r.dtype == torch.complex128
+    dtype = C128 if cx else R64
+    p = torch.empty_like(r); pt = torch.empty_like(r); z = torch.empty_like(r); zt = torch.empty_like(r)
+    k = 0 if C_ is None else C_.shape[1]
+    ldc = 0 if C_ is None else C_.stride(0)
+    zeta = np.zeros(k, dtype=np.complex128 if cx else np.float64)
+    zetat = np.zeros_like(zeta)
+    dc = np.ascontiguousarray(Dc, dtype=np.float64) if k else np.zeros(1)
+    st = lib.rbicg_op_dual_spmv_project(
+        C.byref(op.struct), dtype, _ptr(r), _ptr(rt), _ptr(p_old), _ptr(pt_old), float(np.real(beta)),
+        float(np.imag(beta)), _ptr(C_), _ptr(Ct), k, ldc, dc.ctypes.data_as(C.c_void_p), _ptr(p), _ptr(pt),
+        _ptr(z), _ptr(zt), zeta.ctypes.data_as(C.c_void_p), zetat.ctypes.data_as(C.c_void_p), _stream(stream))
+    _check(st)
+    return p, pt, z, zt, zeta, zetat
+
+
+def op_gram(X, Y, fp32=False, stream=None):
+    """G = X^H Y for row-major device matrices X (n x mx), Y (n x my); returns numpy."""
+    cx = X.dtype == torch.complex128
+    G = np.zeros((X.shape[1], Y.shape[1]), dtype=np.complex128 if cx else np.float64)
+    st = lib.rbicg_op_gram(C128 if cx else R64, X.shape[0], _ptr(X), X.shape[1], X.stride(0), _ptr(Y),
+                           Y.shape[1], Y.stride(0), int(bool(fp32)), G.ctypes.data_as(C.c_void_p),
+                           _stream(stream))
+    _check(st)
+    return G
+
+
+def op_eig_select(L, R, k, complex_=None, stream=None):
+    """Eigenvectors of L w = lambda R w for the k eigenvalues closest to 0 (R None: L w = lambda w)."""
+    cx = np.iscomplexobj(L) or (R is not None and np.iscomplexobj(R)) if complex_ is None else complex_
+    dt = np.complex128 if cx else np.float64
+    m = L.shape[0]
+    Lf = np.asfortranarray(L, dtype=dt)
+    Rf = np.asfortranarray(R, dtype=dt) if R is not None else None
+    W = np.zeros((m, k), dtype=dt, order="F")
+    Wt = np.zeros((m, k), dtype=dt, order="F")
+    lam = np.zeros(2 * k + 2)
+    kk = C.c_int(0)
+    st = lib.rbicg_op_eig_select(C128 if cx else R64, m, Lf.ctypes.data_as(C.c_void_p),
+                                 Rf.ctypes.data_as(C.c_void_p) if Rf is not None else None, k,
+                                 W.ctypes.data_as(C.c_void_p), Wt.ctypes.data_as(C.c_void_p),
+                                 lam.ctypes.data_as(C.c_void_p), C.byref(kk), _stream(stream))
+    _check(st)
+    q = kk.value
+    return W[:, :q], Wt[:, :q], lam[0:2 * q:2] + 1j * lam[1:2 * q:2]
+
+
+def op_svd(S, stream=None):
+    """S = M diag(sigma) N^H (one-sided Jacobi on the GPU); returns (M, sigma, N)."""
+    cx = np.iscomplexobj(S)
+    dt = np.complex128 if cx else np.float64
+    k = S.shape[0]
+    Sf = np.asfortranarray(S, dtype=dt)
+    M = np.zeros((k, k), dtype=dt, order="F")
+    N = np.zeros((k, k), dtype=dt, order="F")
+    sig = np.zeros(k)
+    st = lib.rbicg_op_svd(C128 if cx else R64, k, Sf.ctypes.data_as(C.c_void_p), M.ctypes.data_as(C.c_void_p),
+                          sig.ctypes.data_as(C.c_void_p), N.ctypes.data_as(C.c_void_p), _stream(stream))
+    _check(st)
+    return M, sig, N
