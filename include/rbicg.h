@@ -218,6 +218,22 @@ rbicg_status rbicg_op_eig_select(rbicg_dtype dtype, int m, const void *L_host, c
 rbicg_status rbicg_op_svd(rbicg_dtype dtype, int k, const void *S_host, void *M_host, double *sigma,
                           void *N_host, void *stream);
 
+/* Allocation-free variant of rbicg_op_gram (the paper has no counterpart): G = X^H Y with X
+ * n x mx, Y n x my (row-major, leading dimensions ldx, ldy) and G an mx x my row-major DEVICE
+ * output (doubles, or complex doubles for C128), computed on `stream` without allocating any
+ * device memory.  It serves callers that must not allocate behind their back: a runtime that
+ * reserves the device memory up front and forbids hidden allocations, or a latency-critical
+ * caller that cannot afford cudaMalloc / cudaFree and the synchronisation they imply.
+ * Limits: 1 <= mx, my <= 64 (larger sizes return RBICG_ERR_ARG).  The partial sums live in one
+ * fixed 8 MiB device array inside the library, which every GPU that loads the library holds
+ * until the process exits.  The first call on a device looks up that array's device address
+ * (once per device, with the device current); make that first call before any stream capture.
+ * All calls share the array and each call overwrites it, so calls that overlap on the GPU
+ * (on different streams or from different threads) race; serialise them.  The call returns
+ * once the work is queued; synchronise `stream` before reading G. */
+rbicg_status rbicg_op_gram_noalloc(rbicg_dtype dtype, int64_t n, const void *X, int mx, int ldx,
+                                   const void *Y, int my, int ldy, int fp32, void *G, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,6 +17,8 @@ namespace rb {
 
 static thread_local std::string g_last_error;
 
+void set_global_error(const char* msg) { g_last_error = msg; }
+
 static bool debug_on() {
   static int v = -1;
   if (v < 0) { const char* e = getenv("RBICG_DEBUG"); v = (e && *e && *e != '0') ? 1 : 0; }
