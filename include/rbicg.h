@@ -59,12 +59,17 @@ typedef enum {
 
 typedef enum {
   RBICG_FP64 = 0,          /* every step in the vector dtype (FP64) */
-  RBICG_FP32_REFINED = 1   /* FP64 iterative refinement around FP32 inner RBiCG solves */
+  RBICG_FP32_REFINED = 1   /* FP64 iterative refinement around FP32 inner RBiCG solves.  If an
+                              inner solve fails twice in a row (no residual reduction, even
+                              without a recycle space; an inner residual above 1e6 ||b||; or
+                              no new residual minimum for max(1000, 25 s) iterations),
+                              the handle solves this and later pairs with FP64 RBiCG from the
+                              refined iterate (rbicg_result.fallback = 2) until rbicg_reset */
 } rbicg_precision;
 
 /* Solver parameters.  Defaults (rbicg_default_params): k = 10, s = 40, max_itn = 20000,
  * tol = 1e-8, svd_tol = 1e-6, inner_tol = 1e-5, refine_max = 12, precision = FP64,
- * seed = 0, setup_fp32 = 1, recycle = 1, inner_svd_tol = 1e-3. */
+ * seed = 0, setup_fp32 = 1, recycle = 1, inner_svd_tol = 1e-3, guard = 1.5. */
 typedef struct {
   int k;                   /* recycle dimension: columns kept in U, Ut (Section 3, 4.1); 1..32 */
   int s;                   /* cycle length (Section 4.1); 2..64, k + s <= 80 */
@@ -82,6 +87,12 @@ typedef struct {
                               The oblique projector C D_c^{-1} Ct^H has norm about 1/sigma_min,
                               and FP32 rounding in q = z - C zeta grows by that factor, so the
                               FP32 solver keeps only sigma >= max(svd_tol, inner_svd_tol) */
+  double guard;            /* stagnation guard (not in the paper): a pair solved with a recycle
+                              space that has not converged after guard x (iterations of the last
+                              pair this handle solved without one) iterations applies step 7 to
+                              its current iterate and continues from it as plain BiCG (Algorithm 2
+                              with an empty recycle space); rbicg_result.fallback reports it.
+                              0 disables the guard. */
 } rbicg_params;
 
 /* A sparse operator.  Operator = A when has_shift == 0, (shift I - A) otherwise. */
@@ -103,6 +114,8 @@ typedef struct {
   double relres, relres_dual;             /* recurrence residuals, relative */
   double true_relres, true_relres_dual;   /* ||b - A x|| / ||b||, ||bt - A^H xt|| / ||bt|| in FP64 */
   int status;              /* rbicg_status of the solve */
+  int fallback;            /* 1: the stagnation guard dropped the recycle space during the solve;
+                              2: an FP32_REFINED handle solved the pair in FP64 */
 } rbicg_result;
 
 typedef struct rbicg_ctx *rbicg_handle;

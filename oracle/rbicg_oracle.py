@@ -579,14 +579,19 @@ def _blockmat(rows, dt):
 # ----------------------------------------------------------------------------------------
 
 def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, seed=0,
-                   x_1=None, xt_1=None, recycle=True, on_pair=None):
+                   x_1=None, xt_1=None, recycle=True, on_pair=None, guard=0.0):
     """Solve a sequence of dual pairs [{A, b, bt}, ...], carrying the recycle space.
 
     recycle=False gives plain BiCG on every pair (RBiCG with an empty recycle space).
-    Returns a list of PairResult.
+    guard > 0 reproduces the CUDA library's stagnation guard, which is NOT part of the paper:
+    a pair solved with a recycle space that has not converged after guard x (iterations of
+    the last pair solved without one) iterations applies step 7 to its iterate and continues
+    from it as plain BiCG (Algorithm 2 with an empty recycle space).
+    Returns a list of PairResult (iters counts both legs of a guarded pair; hist["fallback"]).
     """
     out = []
     Uc = Utc = None
+    last_plain = 0
     for j, pr in enumerate(problems):
         A = as_scipy(pr["A"])
         b, bt = pr["b"], pr["bt"]
@@ -596,8 +601,23 @@ def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, 
         rec = None
         if recycle and Uc is not None and Uc.shape[1] > 0:
             rec = biorth_recycle(A, Uc, Utc, svd_tol)
-        res = rbicg_pair(A, b, bt, x0, xt0, recycle=rec, k=k, s=s, tol=tol, max_itn=max_itn,
+        limit = max_itn
+        if guard > 0 and rec is not None and rec[0].shape[1] > 0 and last_plain > 0:
+            limit = min(max_itn, int(guard * last_plain))
+        res = rbicg_pair(A, b, bt, x0, xt0, recycle=rec, k=k, s=s, tol=tol, max_itn=limit,
                          svd_tol=svd_tol, seed=seed + j, refresh=recycle)
+        res.hist["fallback"] = False
+        if limit < max_itn and res.status != STATUS_OK:
+            first = res
+            res = rbicg_pair(A, b, bt, first.x, first.xt, recycle=None, k=k, s=s, tol=tol,
+                             max_itn=max_itn - first.iters, svd_tol=svd_tol, seed=seed + j,
+                             refresh=recycle)
+            res.iters += first.iters
+            res.hist["fallback"] = True
+            res.recycle_dim = 0
+            last_plain = res.iters - first.iters
+        elif rec is None or rec[0].shape[1] == 0:
+            last_plain = res.iters
         if rec is not None and rec[0].shape[1] == 0 and res.status == STATUS_OK:
             res.status = STATUS_RECYCLE_EMPTY
         out.append(res)

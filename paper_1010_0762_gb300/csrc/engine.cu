@@ -172,6 +172,11 @@ struct Solver : SolverBase {
   T *Uc[2] = {}, *Utc[2] = {}, *Cc[2] = {}, *Ctc[2] = {};
   int kU = 0;         // valid columns in U for the next system start
   int kc = 0;         // columns of C in the current system
+  int last_plain_iters = 0;   // iterations of the last solve without a recycle space (guard)
+  double diverge = 0.0;       // > 0: stop once ||r|| > diverge ||b|| (inner FP32 solves)
+  int stall_window = 0;       // > 0: stop once ||r|| has not reached a new minimum for this
+                              // many iterations (inner FP32 solves)
+  T *x_save = nullptr, *xt_save = nullptr;   // initial guesses kept while the guard is armed
   int pending_start = 0;
   // device scratch
   DevState* st = nullptr;
@@ -228,6 +233,9 @@ struct Solver : SolverBase {
     for (T* b : bufs) cudaFree(b);
     cudaFree(st); cudaFree(part); cudaFree(G); cudaFree(work); cudaFree(Wphi); cudaFree(Wphit);
     cudaFree(Nmat); cudaFree(Mmat); cudaFree(sig); cudaFree(iflag);
+    if (x_save) cudaFree(x_save);
+    if (xt_save) cudaFree(xt_save);
+    if (gz) cudaFree(gz);
     free_op();
     if (hv) cudaFreeHost(hv);
   }
@@ -287,6 +295,7 @@ struct Solver : SolverBase {
 
   VecArgs<T> vec(const T* b, const T* bt, T* x, T* xt, const T* Cp, const T* Ctp, const T* Up, const T* Utp) {
     VecArgs<T> v{};
+    v.n = n;
     v.ring = ring; v.ringt = ringt; v.ld = ring_ld; v.R = R;
     v.p[0] = p[0]; v.p[1] = p[1]; v.pt[0] = pt[0]; v.pt[1] = pt[1];
     v.z = z; v.zt = zt; v.x = x; v.xt = xt; v.b = b; v.bt = bt;
@@ -405,14 +414,14 @@ struct Solver : SolverBase {
 
   // ------------------------------------------------------------------ Algorithm 2
   struct PairOut {
-    int iters = 0, cycles = 0, recycle_dim = 0, status = 0;
+    int iters = 0, cycles = 0, recycle_dim = 0, status = 0, fallback = 0;
     double relres = 0, relres_dual = 0, true_relres = 0, true_relres_dual = 0;
   };
 
   PairOut solve(const T* b, const T* bt, T* x, T* xt, double tol, int max_itn, uint64_t seed) {
     const int kU_in = prm.recycle ? kU : 0;
     if (pending_start) system_start();
-    const int kt = kt_for(kc);
+    int kt = kt_for(kc);
     set_field(&DevState::tol, tol);
     set_field(&DevState::max_itn, max_itn);
     set_field(&DevState::done, 0);
@@ -436,9 +445,19 @@ struct Solver : SolverBase {
     int j = 0, kp = 0, last_refresh = 0, good_refresh = 0, good_p = 0;
     bool broken = false;
     int done = hv->done;
-    int iter = 0;
+    int iter = 0, iter_before = 0;
+    double best_r = hv->rnorm;
+    int best_at = 0;
+    // stagnation guard (not in the paper): see rbicg_params.guard
+    int guard_limit = (kc > 0 && prm.guard > 0.0 && last_plain_iters > 0)
+                          ? (int)std::min<double>(2e9, prm.guard * last_plain_iters) : 0x7fffffff;
+    if (guard_limit != 0x7fffffff) {
+      if (!x_save) { x_save = dmalloc<T>(n); xt_save = dmalloc<T>(n); }
+      RB_CUDA(cudaMemcpyAsync(x_save, x, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+      RB_CUDA(cudaMemcpyAsync(xt_save, xt, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+    }
     while (!done) {
-      const int todo = std::min(prm.s, max_itn - iter);
+      const int todo = std::min(prm.s, max_itn - iter_before - iter);
       for (int t = 0; t < todo; ++t) {
         int pp = prof->begin(0, s);
         launch_phase1<V, T>(op, v, st, part, kt, grid, s);
@@ -461,7 +480,46 @@ struct Solver : SolverBase {
         throw Err{RBICG_ERR_CUDA, "iteration made no progress (device state not advancing)"};
       iter = hv->iter;
       done = hv->done;
-      if (!done && iter >= max_itn) done = DONE_MAXIT;
+      if (!done && iter_before + iter >= max_itn) done = DONE_MAXIT;
+      if (!done && diverge > 0.0 && hv->rnorm > diverge * (hv->bnorm > 0 ? hv->bnorm : 1.0)) done = DONE_MAXIT;
+      if (hv->rnorm < best_r) { best_r = hv->rnorm; best_at = iter_before + iter; }
+      if (!done && stall_window > 0 && iter_before + iter - best_at > stall_window) done = DONE_MAXIT;
+      const bool bad_end = done == DONE_BREAK_RHO || done == DONE_BREAK_PQ || done == DONE_NONFINITE;
+      const bool stalled = !done && iter >= guard_limit;
+      if (guard_limit != 0x7fffffff && (stalled || bad_end)) {
+        if (done == DONE_NONFINITE) {
+          // the iterate may hold non-finite values: restart from the saved initial guess
+          RB_CUDA(cudaMemcpyAsync(x, x_save, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+          RB_CUDA(cudaMemcpyAsync(xt, xt_save, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+        }
+
+        // step 7 on the current iterate, then restart from it without the recycle space
+        if (done != DONE_NONFINITE) {
+          launch_finish_a<T>(v, st, kt, grid, s);
+          count(1);
+        }
+        iter_before += iter;
+        kc = 0;
+        set_field(&DevState::kc, 0);
+        out.fallback = 1;
+        guard_limit = 0x7fffffff;
+        const int pi2 = prof->begin(7, s);
+        launch_init<V, T>(op, v, st, part, 0, grid, 0, s);
+        prof->end(pi2, 2, s);
+        count(2);
+        fetch();
+        if (hv->restart) {
+          launch_philox<T>(xt, n, seed, s);
+          launch_init<V, T>(op, v, st, part, 0, grid, 1, s);
+          count(3);
+          fetch();
+        }
+        kt = 0;
+        j = 0; kp = 0; last_refresh = 0; good_refresh = 0; good_p = 0; broken = false;
+        iter = 0;
+        done = hv->done;
+        continue;
+      }
       if (recycle && !broken && iter == (j + 1) * prm.s) {
         ++j;
         refresh(j, kp, nullptr);
@@ -477,9 +535,10 @@ struct Solver : SolverBase {
       if (hv->eig_status != 0) broken = true;
       else { good_refresh = last_refresh; good_p = hv->pcyc; }
     }
-    out.iters = hv->iter;
+    out.iters = iter_before + hv->iter;
     out.cycles = good_refresh;
-    out.recycle_dim = kc;
+    out.recycle_dim = out.fallback ? 0 : kc;
+    if (out.fallback || kU_in == 0) last_plain_iters = hv->iter;
     const double nb = hv->bnorm > 0 ? hv->bnorm : 1.0, nbt = hv->btnorm > 0 ? hv->btnorm : 1.0;
     out.relres = hv->rnorm / nb;
     out.relres_dual = hv->rtnorm / nbt;
@@ -599,14 +658,18 @@ struct ImplT : Impl {
     if (prm.precision == RBICG_FP64) {
       hi.reset(new Solver<V, T>(prm, n, s, launches, prof));
     } else {
+      // hi: the FP64 operator for the residuals, and the FP64 RBiCG solver this handle falls
+      // back to when the FP32 inner recurrence cannot reach inner_tol
       rbicg_params ph = prm;
-      ph.recycle = 0;
-      ph.k = 1;
-      ph.s = 2;
-      hi.reset(new Solver<V, T>(ph, n, s, launches, prof));   // operator + A^H only
+      ph.precision = RBICG_FP64;
+      hi.reset(new Solver<V, T>(ph, n, s, launches, prof));
       rbicg_params pl = prm;
       pl.svd_tol = std::max(prm.svd_tol, prm.inner_svd_tol);
       lo.reset(new Solver<V32, T32>(pl, n, s, launches, prof));
+      // an inner residual this far above ||b||, or no new minimum for this long, means the FP32
+      // recurrence has lost its way (FP64 BiCG residuals of these problems peak near 1e3 ||b||)
+      lo->diverge = 1e6;
+      lo->stall_window = std::max(1000, 25 * prm.s);
       r64 = dmalloc<T>(n); rt64 = dmalloc<T>(n); d64 = dmalloc<T>(n);
       r32 = dmalloc<T32>(n); rt32 = dmalloc<T32>(n); d32 = dmalloc<T32>(n); dt32 = dmalloc<T32>(n);
       nrm = dmalloc<double>(1024);
@@ -649,14 +712,7 @@ struct ImplT : Impl {
     T* x = reinterpret_cast<T*>(xv);
     T* xt = reinterpret_cast<T*>(xtv);
     rbicg_result res{};
-    if (!lo) {
-      auto o = hi->solve(b, bt, x, xt, prm.tol, prm.max_itn, prm.seed);
-      res.iters = o.iters; res.cycles = o.cycles; res.recycle_dim = o.recycle_dim; res.refine_steps = 0;
-      res.relres = o.relres; res.relres_dual = o.relres_dual;
-      res.true_relres = o.true_relres; res.true_relres_dual = o.true_relres_dual;
-      res.status = o.status;
-      return res;
-    }
+    if (!lo || fp64_only) return solve_fp64(b, bt, x, xt, 0, 0);
     // FP64 iterative refinement around FP32 inner RBiCG solves
     const int grid = std::max(1, std::min((int)((n + 255) / 256), num_sms() * 8));
     const double nb = norm(b), nbt = norm(bt);
@@ -686,20 +742,27 @@ struct ImplT : Impl {
       total_iters += o.iters;
       cycles += o.cycles;
       rdim = o.recycle_dim;
-      if (o.status < 0) { status = o.status; break; }
+      // a non-finite inner solve is treated like an unusable correction (retried as plain BiCG)
+      if (o.status < 0 && o.status != RBICG_ERR_NONFINITE) { status = o.status; break; }
       if (first_inner < 0) {
         first_inner = o.iters;
         inner_cap = std::min(prm.max_itn, std::max(200, 4 * first_inner + 100));
       }
       // A correction is used only if the inner solve reduced its own residual; otherwise the
       // inner recycle space is dropped and the step is retried once as plain FP32 BiCG.
-      const bool usable = o.status == RBICG_OK || o.status == RBICG_RECYCLE_EMPTY ||
-                          (o.true_relres < 0.5 && (dc || o.true_relres_dual < 0.5));
+      const bool usable = o.status != RBICG_ERR_NONFINITE &&
+                          (o.status == RBICG_OK || o.status == RBICG_RECYCLE_EMPTY ||
+                           (o.true_relres < 0.5 && (dc || o.true_relres_dual < 0.5)));
       if (debug_on())
         fprintf(stderr, "[rbicg] inner step %d status %d iters %d relres %.3e/%.3e usable %d\n", step, o.status,
                 o.iters, o.true_relres, o.true_relres_dual, (int)usable);
       if (!usable) {
-        if (retried_plain) { status = RBICG_NOT_CONVERGED; break; }
+        if (retried_plain) {
+          // the FP32 recurrence does not converge on this problem even without a recycle
+          // space: this handle continues in FP64 RBiCG from the refined iterate
+          fp64_only = true;
+          return solve_fp64(b, bt, x, xt, total_iters, step);
+        }
         retried_plain = true;
         lo->kU = 0;
         lo->pending_start = 1;
@@ -730,13 +793,28 @@ struct ImplT : Impl {
     return res;
   }
 
+  bool fp64_only = false;   // FP32_REFINED handle that fell back to FP64 (until rbicg_reset)
+
+  rbicg_result solve_fp64(const T* b, const T* bt, T* x, T* xt, int iters_before, int steps_before) {
+    rbicg_result res{};
+    auto o = hi->solve(b, bt, x, xt, prm.tol, prm.max_itn, prm.seed);
+    res.iters = iters_before + o.iters; res.cycles = o.cycles; res.recycle_dim = o.recycle_dim;
+    res.refine_steps = steps_before;
+    res.relres = o.relres; res.relres_dual = o.relres_dual;
+    res.true_relres = o.true_relres; res.true_relres_dual = o.true_relres_dual;
+    res.status = o.status;
+    res.fallback = lo ? 2 : o.fallback;
+    return res;
+  }
+
   void reset() override {
     hi->kU = 0; hi->pending_start = 1;
     if (lo) { lo->kU = 0; lo->pending_start = 1; }
+    fp64_only = false;
   }
 
   void export_recycle(void* Uo, void* Uto, int* p) override {
-    if (lo) {
+    if (lo && !fp64_only) {
       // the recycle space lives in the FP32 inner solver; export it widened to FP64
       const int64_t m = n * lo->ldk;
       T* tmp = reinterpret_cast<T*>(Uo);
@@ -765,7 +843,7 @@ struct ImplT : Impl {
     cudaFree(tmp);
   }
   void import_recycle(const void* Ui, const void* Uti, int p) override {
-    if (lo) {
+    if (lo && !fp64_only) {
       T32* tmp = dmalloc<T32>((size_t)n * p);
       for (int side = 0; side < 2; ++side) {
         launch_convert<T, T32>(reinterpret_cast<const T*>(side ? Uti : Ui), tmp, (int64_t)n * p, s);
@@ -829,6 +907,7 @@ extern "C" void rbicg_default_params(rbicg_params* p) {
   p->k = 10; p->s = 40; p->max_itn = 20000; p->tol = 1e-8; p->svd_tol = 1e-6; p->inner_tol = 1e-5;
   p->refine_max = 12; p->precision = RBICG_FP64; p->seed = 0; p->setup_fp32 = 1; p->recycle = 1;
   p->inner_svd_tol = 1e-3;
+  p->guard = 1.5;
 }
 
 static std::string check_params(const rbicg_params* p, int64_t n) {
@@ -840,6 +919,7 @@ static std::string check_params(const rbicg_params* p, int64_t n) {
   if (!(p->tol > 0.0)) return "tol must be positive";
   if (p->max_itn < 1) return "max_itn must be positive";
   if (!(p->svd_tol >= 0.0)) return "svd_tol must be >= 0";
+  if (!(p->guard >= 0.0)) return "guard must be >= 0";
   if (p->precision == RBICG_FP32_REFINED && !(p->inner_tol > 0.0 && p->inner_tol < 1.0))
     return "inner_tol must be in (0, 1)";
   if (p->precision != RBICG_FP64 && p->precision != RBICG_FP32_REFINED) return "unknown precision";
@@ -1036,13 +1116,26 @@ static void op_spmv_project_impl(const rbicg_csr* A, const void* r, const void* 
   const int grid = std::max(1, std::min((op.n + NTHREADS - 1) / NTHREADS, num_sms() * 8));
   Acc* part = dmalloc<Acc>((size_t)grid * (2 * KMAX + 2));
   VecArgs<T> v{};
+  v.n = A->n;
   v.ring = const_cast<T*>(reinterpret_cast<const T*>(r));
   v.ringt = const_cast<T*>(reinterpret_cast<const T*>(rt));
   v.ld = A->n; v.R = 1;
   v.p[0] = const_cast<T*>(reinterpret_cast<const T*>(p_old)); v.p[1] = reinterpret_cast<T*>(p_out);
   v.pt[0] = const_cast<T*>(reinterpret_cast<const T*>(pt_old)); v.pt[1] = reinterpret_cast<T*>(pt_out);
   v.z = reinterpret_cast<T*>(z); v.zt = reinterpret_cast<T*>(zt);
-  v.C = reinterpret_cast<const T*>(C); v.Ct = reinterpret_cast<const T*>(Ct); v.ldk = ldc;
+  // the projection pass walks the bases with a row stride that is a multiple of 4: repack
+  // (zero-padded columns) when the caller's stride is not that
+  const int ldp = std::max(4, ((k + 3) / 4) * 4);
+  T *Cp = nullptr, *Ctp = nullptr;
+  if (k > 0) {
+    Cp = dmalloc<T>((size_t)A->n * ldp);
+    Ctp = dmalloc<T>((size_t)A->n * ldp);
+    RB_CUDA(cudaMemsetAsync(Cp, 0, sizeof(T) * A->n * ldp, s));
+    RB_CUDA(cudaMemsetAsync(Ctp, 0, sizeof(T) * A->n * ldp, s));
+    RB_CUDA(cudaMemcpy2DAsync(Cp, sizeof(T) * ldp, C, sizeof(T) * ldc, sizeof(T) * k, A->n, cudaMemcpyDeviceToDevice, s));
+    RB_CUDA(cudaMemcpy2DAsync(Ctp, sizeof(T) * ldp, Ct, sizeof(T) * ldc, sizeof(T) * k, A->n, cudaMemcpyDeviceToDevice, s));
+  }
+  v.C = Cp; v.Ct = Ctp; v.ldk = ldp;
   launch_phase1<V, T>(op, v, st, part, kt_for(k), grid, s);
   RB_CUDA(cudaGetLastError());
   RB_CUDA(cudaMemcpyAsync(&hst, st, sizeof hst, cudaMemcpyDeviceToHost, s));
@@ -1057,6 +1150,8 @@ static void op_spmv_project_impl(const rbicg_csr* A, const void* r, const void* 
     }
   }
   cudaFree(part); cudaFree(st); cudaFree(tva); cudaFree(flag);
+  if (Cp) cudaFree(Cp);
+  if (Ctp) cudaFree(Ctp);
   if (!shared) { cudaFree(trp); cudaFree(tci); }
 }
 

@@ -71,6 +71,7 @@ struct OpArgs {
 // Vectors of one solve.
 template <class T>
 struct VecArgs {
+  int64_t n;                                     // rows
   T* ring; T* ringt; int64_t ld; int R;          // residual rings: r_m at slot m mod R
   T* p[2]; T* pt[2];                             // p_i at p[i & 1]
   T* z; T* zt;                                   // z_i (overwritten by q_i)
@@ -105,6 +106,8 @@ void launch_init(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* p
 template <class V, class T>
 void launch_finish(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
                    cudaStream_t s);
+template <class T>
+void launch_finish_a(const VecArgs<T>& v, DevState* st, int kt, int grid, cudaStream_t s);   // x -= U zeta_c
 template <class T>
 void launch_philox(T* out, int64_t n, uint64_t seed, cudaStream_t s);
 template <class V>

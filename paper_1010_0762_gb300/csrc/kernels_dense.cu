@@ -115,8 +115,13 @@ __device__ int phi_ycol(const Layout& L, int b) {
 // work layout (zd): Hd [PSIMAX x MMAX], Htd [PSIMAX x MMAX], GH [PSIMAX x MMAX],
 // Lm [MMAX x MMAX], Rm [MMAX x MMAX] (column-major), then eig scratch.
 constexpr int64_t W_HD = 0, W_HTD = W_HD + PSIMAX * MMAX, W_GH = W_HTD + PSIMAX * MMAX,
-                  W_L = W_GH + PSIMAX * MMAX, W_R = W_L + MMAX * MMAX, W_LU = W_R + MMAX * MMAX,
-                  W_Y = W_LU + MMAX * MMAX, W_YL = W_Y + MMAX * KMAX, W_END = W_YL + MMAX * KMAX;
+                  W_L = W_GH + PSIMAX * MMAX, W_R = W_L + MMAX * MMAX,
+                  W_Y = W_R + MMAX * MMAX, W_YL = W_Y + MMAX * (KMAX + 8), W_LAM = W_YL + MMAX * (KMAX + 8),
+                  W_LAM2 = W_LAM + KMAX + 8, W_INT = W_LAM2 + KMAX + 8,
+                  W_END = W_INT + (MMAX + 2 * KMAX + 8 + 3) / 4 + 1;
+static_assert(PSIMAX * MMAX >= 2 * MMAX * KMAX, "k_eig_c keeps the selected vectors in the GH area");
+// integer area at W_INT: piv[MMAX], sel[KMAX], pair[KMAX], units, cols, ncand
+constexpr int NCAND_EXTRA = 8;   // candidates beyond k refined before the final selection
 
 template <class A>
 __global__ void k_build_h(RefreshInfo f, const DevState* st, zd* work) {
@@ -131,24 +136,28 @@ __global__ void k_build_h(RefreshInfo f, const DevState* st, zd* work) {
 }
 
 // GH[a, b] = sum_c Gs[a, c] H[c, b], Gs[a, c] = conj(sct_a) G[a, c] sc_c  (a, c over Psi)
+// Lanczos scalings of all Psi columns, once per block (shared memory)
+__device__ void load_psi_scales(const DevState* st, const Layout& L, zd* sc, zd* sct) {
+  for (int a = threadIdx.x; a < L.nPsi; a += blockDim.x) psi_scale(st, L, a, &sc[a], &sct[a]);
+  __syncthreads();
+}
+
 template <class A>
 __global__ void k_gh(RefreshInfo f, const DevState* st, const A* G, zd* work) {
+  __shared__ zd sc[PSIMAX], sct[PSIMAX];
   const Layout L = make_layout(f);
+  load_psi_scales(st, L, sc, sct);
   const zd* Hd = work + W_HD;
   zd* GH = work + W_GH;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < L.nPsi * L.nPhi; e += gridDim.x * blockDim.x) {
     const int a = e % L.nPsi, b = e / L.nPsi;
-    zd sa, sta;
-    psi_scale(st, L, a, &sa, &sta);
     zd s = zd();
     for (int c = 0; c < L.nPsi; ++c) {
       const zd h = Hd[c + b * PSIMAX];
       if (h.re == 0.0 && h.im == 0.0) continue;
-      zd sc, stc;
-      psi_scale(st, L, c, &sc, &stc);
-      s += to_zd(G[(int64_t)a * f.my + c]) * sc * h;
+      s += to_zd(G[(int64_t)a * f.my + c]) * sc[c] * h;
     }
-    GH[a + b * PSIMAX] = conjg(sta) * s;
+    GH[a + b * PSIMAX] = conjg(sct[a]) * s;
   }
 }
 
@@ -161,20 +170,19 @@ __global__ void k_lr(RefreshInfo f, const DevState* st, const A* G, zd* work) {
   zd* Lm = work + W_L;
   zd* Rm = work + W_R;
   const int m = L.nPhi;
+  __shared__ zd sc[PSIMAX], sct[PSIMAX];
+  load_psi_scales(st, L, sc, sct);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
     const int c = e % m, b = e / m;
     const int yc = phi_ycol(L, b);
-    zd sy, sty;
-    if (yc < L.nPsi) psi_scale(st, L, yc, &sy, &sty); else sy = zd(1.0);
+    const zd sy = yc < L.nPsi ? sc[yc] : zd(1.0);
     zd sl = zd(), sr = zd();
     for (int a = 0; a < L.nPsi; ++a) {
       const zd h = Htd[a + c * PSIMAX];
       if (h.re == 0.0 && h.im == 0.0) continue;
-      zd sa, sta;
-      psi_scale(st, L, a, &sa, &sta);
       const zd hc = conjg(h);
       sl += hc * GH[a + b * PSIMAX];
-      sr += hc * (conjg(sta) * to_zd(G[(int64_t)a * f.my + yc]) * sy);
+      sr += hc * (conjg(sct[a]) * to_zd(G[(int64_t)a * f.my + yc]) * sy);
     }
     Lm[c + b * MMAX] = sl;
     Rm[c + b * MMAX] = sr;
@@ -195,40 +203,28 @@ __global__ void k_t1(RefreshInfo f, const DevState* st, zd* work) {
 // one-block dense eigen solver (complex FP64)
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ double cabs_(zd a) { return hypot(a.re, a.im); }
+typedef cplx<float> zf;
+__device__ __forceinline__ float cabs_(zf a) { return hypotf(a.re, a.im); }
 
-// Givens G = [[c, s], [-conj(s), c]] with G [a; b] = [r; 0]
-__device__ void givens(zd a, zd b, double* c, zd* s) {
-  const double ab = cabs_(b);
-  if (ab == 0.0) { *c = 1.0; *s = zd(); return; }
-  const double aa = cabs_(a);
-  if (aa == 0.0) { *c = 0.0; *s = conjg(b) * (1.0 / ab); return; }
-  const double nr = hypot(aa, ab);
-  *c = aa / nr;
-  *s = (a * (1.0 / aa)) * conjg(b) * (1.0 / nr);
-}
+template <class S> struct real_t;
+template <> struct real_t<zd> { typedef double t; };
+template <> struct real_t<zf> { typedef float t; };
 
-struct EigSmem {
-  zd* T;   // m x m, column-major, ld = m
-  zd* Q;
-  int* piv;
-  zd* vec;  // scratch MMAX
-  double* dsc;
-  int* ish;
-};
-
-// Block-wide: LU with partial pivoting of A (m x m, ld m) in place; piv[k] = pivot row.
-__device__ bool lu_block(zd* A, int m, int* piv, double* dsc, int* ish) {
+// Block-wide LU with partial pivoting of A (m x m, leading dimension ld) in place;
+// piv[k] = pivot row of step k.  Returns false on an exactly zero pivot column.
+template <class S>
+__device__ bool lu_block(S* A, int m, int ld, int* piv, typename real_t<S>::t* dsc) {
+  typedef typename real_t<S>::t Rl;
   for (int k = 0; k < m; ++k) {
-    // pivot search (warp 0)
     if (threadIdx.x < 32) {
-      double best = -1.0;
+      Rl best = -1;
       int bi = k;
       for (int r = k + threadIdx.x; r < m; r += 32) {
-        const double v = cabs_(A[r + k * m]);
+        const Rl v = cabs_(A[r + k * ld]);
         if (v > best) { best = v; bi = r; }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const Rl ob = __shfl_down_sync(0xffffffffu, best, o);
         const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
@@ -236,191 +232,126 @@ __device__ bool lu_block(zd* A, int m, int* piv, double* dsc, int* ish) {
     }
     __syncthreads();
     const int p = piv[k];
-    if (dsc[0] == 0.0) return false;
+    if (dsc[0] == Rl(0)) return false;
     if (p != k)
       for (int c = threadIdx.x; c < m; c += blockDim.x) {
-        const zd t = A[k + c * m]; A[k + c * m] = A[p + c * m]; A[p + c * m] = t;
+        const S t = A[k + c * ld]; A[k + c * ld] = A[p + c * ld]; A[p + c * ld] = t;
       }
     __syncthreads();
-    const zd inv = zd(1.0) / A[k + k * m];
-    for (int r = k + 1 + threadIdx.x; r < m; r += blockDim.x) A[r + k * m] = A[r + k * m] * inv;
+    const S inv = S(Rl(1)) / A[k + k * ld];
+    for (int r = k + 1 + threadIdx.x; r < m; r += blockDim.x) A[r + k * ld] = A[r + k * ld] * inv;
     __syncthreads();
     const int rem = m - k - 1;
     for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
       const int r = k + 1 + e % rem, c = k + 1 + e / rem;
-      A[r + c * m] -= A[r + k * m] * A[k + c * m];
+      A[r + c * ld] -= A[r + k * ld] * A[k + c * ld];
     }
     __syncthreads();
   }
-  (void)ish;
   return true;
 }
 
-// Block-wide: B <- A^{-1} B for the LU of A (B: m x nb, ld m)
-__device__ void lu_solve_block(const zd* LU, int m, const int* piv, zd* B, int nb) {
+// Block-wide: columns of B (stride ldb) <- A^{-1} B for the LU of A (one thread per column)
+template <class S>
+__device__ void lu_solve_block(const S* LU, int m, int ld, const int* piv, S* B, int nb, int ldb) {
   for (int col = threadIdx.x; col < nb; col += blockDim.x) {
-    zd* b = B + col * m;
-    for (int k = 0; k < m; ++k) { const int p = piv[k]; if (p != k) { const zd t = b[k]; b[k] = b[p]; b[p] = t; } }
-    for (int r = 0; r < m; ++r) { zd s = b[r]; for (int c = 0; c < r; ++c) s -= LU[r + c * m] * b[c]; b[r] = s; }
+    S* b = B + col * ldb;
+    for (int k = 0; k < m; ++k) { const int p = piv[k]; if (p != k) { const S t = b[k]; b[k] = b[p]; b[p] = t; } }
+    for (int r = 0; r < m; ++r) { S s = b[r]; for (int c = 0; c < r; ++c) s -= LU[r + c * ld] * b[c]; b[r] = s; }
     for (int r = m - 1; r >= 0; --r) {
-      zd s = b[r];
-      for (int c = r + 1; c < m; ++c) s -= LU[r + c * m] * b[c];
-      b[r] = s / LU[r + r * m];
+      S s = b[r];
+      for (int c = r + 1; c < m; ++c) s -= LU[r + c * ld] * b[c];
+      b[r] = s / LU[r + r * ld];
     }
   }
   __syncthreads();
 }
 
-// Block-wide: columns of B (stride ldb) <- A^{-H} B for the LU of A = P^T Lw U
-__device__ void lu_solve_adj_block(const zd* LU, int m, const int* piv, zd* B, int nb, int ldb) {
-  for (int col = threadIdx.x; col < nb; col += blockDim.x) {
-    zd* b = B + col * ldb;
-    // A = P^T Lw U  =>  A^H = U^H Lw^H P ;  solve U^H y = b, Lw^H z = y, x = P^T z
-    for (int r = 0; r < m; ++r) {
-      zd s = b[r];
-      for (int c = 0; c < r; ++c) s -= conjg(LU[c + r * m]) * b[c];
-      b[r] = s / conjg(LU[r + r * m]);
-    }
-    for (int r = m - 1; r >= 0; --r) {
-      zd s = b[r];
-      for (int c = r + 1; c < m; ++c) s -= conjg(LU[c + r * m]) * b[c];
-      b[r] = s;
-    }
-    for (int k = m - 1; k >= 0; --k) { const int p = piv[k]; if (p != k) { const zd t = b[k]; b[k] = b[p]; b[p] = t; } }
+// One warp: y <- A^{-1} y (A = P^T Lw U stored as LU, pivots piv), column-oriented substitution
+__device__ void lu_solve_warp(const zd* LU, int m, int ld, const int* piv, zd* y) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int k = 0; k < m; ++k) { const int p = piv[k]; if (p != k) { const zd t = y[k]; y[k] = y[p]; y[p] = t; } }
+  __syncwarp();
+  for (int c = 0; c < m; ++c) {          // unit lower triangular
+    const zd yc = y[c];
+    __syncwarp();
+    for (int r = c + 1 + lane; r < m; r += 32) y[r] -= LU[r + c * ld] * yc;
+    __syncwarp();
   }
-  __syncthreads();
+  for (int c = m - 1; c >= 0; --c) {     // upper triangular
+    const zd yc = y[c] / LU[c + c * ld];
+    __syncwarp();
+    if (lane == 0) y[c] = yc;
+    for (int r = lane; r < c; r += 32) y[r] -= LU[r + c * ld] * yc;
+    __syncwarp();
+  }
 }
 
-// Block-wide Householder reduction of T (m x m) to upper Hessenberg, Q <- Q P_1 ... P_{m-2}
-__device__ void hessenberg_block(zd* T, zd* Q, int m, zd* v, double* dsc) {
+// One warp: y <- A^{-H} y.  A^H = U^H Lw^H P: solve U^H z = y, Lw^H w = z, y = P^T w.
+__device__ void lu_solve_adj_warp(const zd* LU, int m, int ld, const int* piv, zd* y) {
+  const int lane = threadIdx.x & 31;
+  for (int c = 0; c < m; ++c) {          // U^H lower triangular: column c of U^H = conj(U[c, :])
+    const zd yc = y[c] / conjg(LU[c + c * ld]);
+    __syncwarp();
+    if (lane == 0) y[c] = yc;
+    for (int r = c + 1 + lane; r < m; r += 32) y[r] -= conjg(LU[c + r * ld]) * yc;
+    __syncwarp();
+  }
+  for (int c = m - 1; c >= 0; --c) {     // Lw^H unit upper triangular: column c = conj(Lw[c, :])
+    const zd yc = y[c];
+    __syncwarp();
+    for (int r = lane; r < c; r += 32) y[r] -= conjg(LU[c + r * ld]) * yc;
+    __syncwarp();
+  }
+  if (lane == 0)
+    for (int k = m - 1; k >= 0; --k) { const int p = piv[k]; if (p != k) { const zd t = y[k]; y[k] = y[p]; y[p] = t; } }
+  __syncwarp();
+}
+
+// Block-wide Householder reduction of T (m x m, ld) to upper Hessenberg form (no vectors)
+template <class S>
+__device__ void hessenberg_block(S* T, int m, int ld, S* v, typename real_t<S>::t* dsc) {
+  typedef typename real_t<S>::t Rl;
   for (int j = 0; j < m - 2; ++j) {
     const int len = m - j - 1;
-    // norm of x = T[j+1.., j]
     if (threadIdx.x < 32) {
-      double s = 0.0;
-      for (int r = threadIdx.x; r < len; r += 32) s += abs2(T[j + 1 + r + j * m]);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (threadIdx.x == 0) dsc[0] = s;
+      Rl sacc = 0;
+      for (int r = threadIdx.x; r < len; r += 32) sacc += abs2(T[j + 1 + r + j * ld]);
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+      if (threadIdx.x == 0) dsc[0] = sacc;
     }
     __syncthreads();
-    const double nx2 = dsc[0];
-    const zd x0 = T[j + 1 + j * m];
-    const double tail = nx2 - abs2(x0);
-    if (tail <= 1e-300) { __syncthreads(); continue; }
-    const double nx = sqrt(nx2);
-    const double ax0 = cabs_(x0);
-    const zd ph = ax0 > 0.0 ? x0 * (1.0 / ax0) : zd(1.0);
-    const zd alpha = -(ph * nx);                 // x - alpha e1 avoids cancellation
-    for (int r = threadIdx.x; r < len; r += blockDim.x) v[r] = T[j + 1 + r + j * m];
+    const Rl nx2 = dsc[0];
+    const S x0 = T[j + 1 + j * ld];
+    const Rl tail = nx2 - abs2(x0);
+    if (!(tail > Rl(0)) || tail <= nx2 * Rl(1e-30)) { __syncthreads(); continue; }
+    const Rl nx = sqrt(nx2);
+    const Rl ax0 = cabs_(x0);
+    const S ph = ax0 > Rl(0) ? x0 * (Rl(1) / ax0) : S(Rl(1));
+    const S alpha = -(ph * nx);
+    for (int r = threadIdx.x; r < len; r += blockDim.x) v[r] = T[j + 1 + r + j * ld];
     __syncthreads();
     if (threadIdx.x == 0) v[0] = v[0] - alpha;
     __syncthreads();
-    const double vv = tail + abs2(x0 - alpha);
-    const double f = 2.0 / vv;
-    // left: T[j+1.., c] -= f v (v^H T[j+1.., c]) for c >= j
+    const Rl f = Rl(2) / (tail + abs2(x0 - alpha));
     for (int c = j + threadIdx.x; c < m; c += blockDim.x) {
-      zd w = zd();
-      for (int r = 0; r < len; ++r) w += cmul(v[r], T[j + 1 + r + c * m]);
+      S w = S(Rl(0));
+      for (int r = 0; r < len; ++r) w += cmul(v[r], T[j + 1 + r + c * ld]);
       w = w * f;
-      for (int r = 0; r < len; ++r) T[j + 1 + r + c * m] -= v[r] * w;
+      for (int r = 0; r < len; ++r) T[j + 1 + r + c * ld] -= v[r] * w;
     }
     __syncthreads();
-    // right: T[r, j+1..] -= f (T[r, j+1..] v) v^H for all rows; Q likewise
-    for (int r = threadIdx.x; r < 2 * m; r += blockDim.x) {
-      zd* M = r < m ? T : Q;
-      const int rr = r < m ? r : r - m;
-      zd u = zd();
-      for (int c = 0; c < len; ++c) u += M[rr + (j + 1 + c) * m] * v[c];
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+      S u = S(Rl(0));
+      for (int c = 0; c < len; ++c) u += T[r + (j + 1 + c) * ld] * v[c];
       u = u * f;
-      for (int c = 0; c < len; ++c) M[rr + (j + 1 + c) * m] -= u * conjg(v[c]);
+      for (int c = 0; c < len; ++c) T[r + (j + 1 + c) * ld] -= u * conjg(v[c]);
     }
     __syncthreads();
-    for (int r = j + 2 + threadIdx.x; r < m; r += blockDim.x) T[r + j * m] = zd();
+    for (int r = j + 2 + threadIdx.x; r < m; r += blockDim.x) T[r + j * ld] = S(Rl(0));
     __syncthreads();
   }
-}
-
-// Warp 0: shifted QR (single shift, Wilkinson, implicit via Givens) on the Hessenberg T
-// to upper triangular (Schur) form, accumulating Q.  Returns false if it does not converge.
-__device__ bool schur_warp(zd* T, zd* Q, int m, int* dbg) {
-  const int lane = threadIdx.x & 31;
-  const double eps = 2.220446049250313e-16;
-  int hi = m - 1, iter = 0, total = 0;
-  while (hi > 0) {
-    // find lo: deflate small subdiagonals
-    int lo = hi;
-    while (lo > 0) {
-      const double sub = cabs_(T[lo + (lo - 1) * m]);
-      const double dsum = cabs_(T[lo + lo * m]) + cabs_(T[lo - 1 + (lo - 1) * m]);
-      if (sub <= eps * (dsum > 0.0 ? dsum : 1.0)) { __syncwarp(); if (lane == 0) T[lo + (lo - 1) * m] = zd(); __syncwarp(); break; }
-      --lo;
-    }
-    if (lo == hi) { --hi; iter = 0; continue; }
-    if (!finite_of(T[hi + hi * m]) || !finite_of(T[hi + (hi - 1) * m])) {
-      if (lane == 0) { dbg[0] = 3; dbg[1] = lo; dbg[2] = hi; dbg[3] = iter; dbg[4] = total; }
-      return false;
-    }
-    if (++total > 60 * m) {
-      if (lane == 0) { dbg[0] = 2; dbg[1] = lo; dbg[2] = hi; dbg[3] = iter; dbg[4] = total; }
-      return false;
-    }
-    ++iter;
-    // Wilkinson shift from the trailing 2x2 of the window
-    const zd a = T[hi - 1 + (hi - 1) * m], b = T[hi - 1 + hi * m], c = T[hi + (hi - 1) * m], d = T[hi + hi * m];
-    zd mu;
-    if (iter % 11 == 10) {
-      mu = d + zd(cabs_(c) * 0.75);   // exceptional shift
-    } else {
-      const zd tr = a + d, det = a * d - b * c;
-      const zd half = tr * 0.5;
-      const zd disc = half * half - det;
-      // complex sqrt
-      const double rdisc = cabs_(disc);
-      // clamp both radicands: hypot carries up to 2 ulp of error, so |disc| + Re(disc) can
-      // round below zero when disc is (nearly) a negative real, as it is for the conjugate
-      // eigenvalue pairs of a real matrix
-      double sr = sqrt(fmax(0.0, 0.5 * (rdisc + disc.re))), si = sqrt(fmax(0.0, 0.5 * (rdisc - disc.re)));
-      if (disc.im < 0.0) si = -si;
-      const zd sq(sr, si);
-      const zd l1 = half + sq, l2 = half - sq;
-      mu = cabs_(l1 - d) < cabs_(l2 - d) ? l1 : l2;
-    }
-    // implicit single-shift sweep on [lo, hi]
-    zd x = T[lo + lo * m] - mu, y = T[lo + 1 + lo * m];
-    for (int k = lo; k < hi; ++k) {
-      double cs;
-      zd sn;
-      if (k == lo) givens(x, y, &cs, &sn);
-      else givens(T[k + (k - 1) * m], T[k + 1 + (k - 1) * m], &cs, &sn);
-      // every lane has read the entries that define the rotation (and, for k == lo, the
-      // shift) before any lane overwrites them below
-      __syncwarp();
-      const int c0 = k > lo ? k - 1 : lo;
-      // rows k, k+1, columns c0..m-1
-      for (int col = c0 + lane; col < m; col += 32) {
-        const zd p = T[k + col * m], q = T[k + 1 + col * m];
-        T[k + col * m] = cs * p + sn * q;
-        T[k + 1 + col * m] = cs * q - conjg(sn) * p;
-      }
-      __syncwarp();
-      // columns k, k+1, rows 0..min(k+2, hi)
-      const int r1 = k + 2 < hi ? k + 2 : hi;
-      for (int row = lane; row <= r1; row += 32) {
-        const zd p = T[row + k * m], q = T[row + (k + 1) * m];
-        T[row + k * m] = cs * p + conjg(sn) * q;
-        T[row + (k + 1) * m] = cs * q - sn * p;
-      }
-      for (int row = lane; row < m; row += 32) {
-        const zd p = Q[row + k * m], q = Q[row + (k + 1) * m];
-        Q[row + k * m] = cs * p + conjg(sn) * q;
-        Q[row + (k + 1) * m] = cs * q - sn * p;
-      }
-      __syncwarp();
-      if (k > lo && lane == 0) T[k + 1 + (k - 1) * m] = zd();
-      __syncwarp();
-    }
-  }
-  return true;
 }
 
 // Selection of eigenvalue indices (reading: k closest to the origin; on a real problem a
@@ -473,108 +404,346 @@ __device__ int select_units(const zd* lam, int m, int k, int real_path, int* sel
   return units;
 }
 
-// Full eigen pipeline in one block; writes Wphi / Wphit (m x ldw, row a = Phi column) with
-// the Phi scalings folded in, the selected eigenvalues, st->kk and st->eig_status.
-__global__ void __launch_bounds__(256) k_eig(RefreshInfo f, DevState* st, zd* work, zd* Wphi, zd* Wphit, int ldw,
-                                             double* lam_out, int has_R, int m_in, int raw) {
+// ------------------------------------------------------------------------------------
+// Eigen pipeline (three kernels).
+//   k_eig_a (one block): M = R^{-1} L (FP64 LU with partial pivoting), FP64 Householder
+//     reduction to Hessenberg form, eigenvalues by an FP32 implicit single-shift QR restricted
+//     to the active window, and the k + NCAND_EXTRA eigenvalues closest to 0 as candidates
+//     (shifts for the FP64 refinement).
+//   k_eig_b (one block per candidate, FP64): inverse iteration on the pencil itself,
+//     (L - sigma R) y+ = R y and (L - sigma R)^H yl+ = R^H yl (dense LU with partial pivoting),
+//     then the two-sided Rayleigh quotient yl^H L y / yl^H R y; when that quotient has moved
+//     away from the FP32 shift, one more factorisation at the quotient (a Rayleigh step).
+//   k_eig_c (one block): candidates that refined to the same eigenvalue are merged, final
+//     selection on the refined eigenvalues (real / complex decided in FP64), unit norm,
+//     conjugate pairs split into real and imaginary parts, Phi scalings.
+// The QR iteration is long and sequential; on this part FP64 runs at about 2 FMA per clock per
+// SM and FP32 at 64x that, so it runs in FP32 and the eigenpairs are refined in FP64.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ float cabsf_(zf a) { return hypotf(a.re, a.im); }
+
+__device__ __forceinline__ float cabs1f_(zf a) { return fabsf(a.re) + fabsf(a.im); }
+
+// Plane rotation [c, s; -conj(s), c] with c real that zeroes b against a.  The matrix is scaled
+// to entries of order one before the QR iteration, so the squares neither overflow nor lose
+// anything that matters; reciprocal square roots replace hypot and division.
+__device__ void givens_f(zf a, zf b, float* c, zf* s) {
+  const float ab2 = abs2(b);
+  if (ab2 == 0.f) { *c = 1.f; *s = zf(0.f, 0.f); return; }
+  const float aa2 = abs2(a);
+  if (aa2 == 0.f) { *c = 0.f; *s = conjg(b) * rsqrtf(ab2); return; }
+  const float ria = rsqrtf(aa2), rn = rsqrtf(aa2 + ab2);
+  *c = aa2 * ria * rn;
+  *s = (a * ria) * conjg(b) * rn;
+}
+
+// Warp 0: eigenvalues of the Hessenberg H (FP32, ld) by implicit single-shift QR with Wilkinson
+// shifts, updating only the active window.  Returns false (with diagnostics) on failure.
+__device__ bool qr_eigs_warp_f32(zf* T, int m, int ld, int* dbg) {
+  const int lane = threadIdx.x & 31;
+  const float eps = 1.1920929e-07f;
+  int hi = m - 1, iter = 0, total = 0;
+  while (hi > 0) {
+    int lo = hi;
+    while (lo > 0) {
+      const float sub = cabs1f_(T[lo + (lo - 1) * ld]);
+      const float dsum = cabs1f_(T[lo + lo * ld]) + cabs1f_(T[lo - 1 + (lo - 1) * ld]);
+      if (sub <= eps * (dsum > 0.f ? dsum : 1.f)) {
+        __syncwarp();
+        if (lane == 0) T[lo + (lo - 1) * ld] = zf(0.f, 0.f);
+        __syncwarp();
+        break;
+      }
+      --lo;
+    }
+    if (lo == hi) { --hi; iter = 0; continue; }
+    if (!finite_of(T[hi + hi * ld].re) || !finite_of(T[hi + (hi - 1) * ld].re) ||
+        !isfinite(T[hi + hi * ld].im) || !isfinite(T[hi + (hi - 1) * ld].im)) {
+      if (lane == 0) { dbg[0] = 3; dbg[1] = lo; dbg[2] = hi; dbg[3] = iter; dbg[4] = total; }
+      return false;
+    }
+    if (++total > 60 * m) {
+      if (lane == 0) { dbg[0] = 2; dbg[1] = lo; dbg[2] = hi; dbg[3] = iter; dbg[4] = total; }
+      return false;
+    }
+    ++iter;
+    const zf a = T[hi - 1 + (hi - 1) * ld], b = T[hi - 1 + hi * ld], c = T[hi + (hi - 1) * ld], d = T[hi + hi * ld];
+    zf mu;
+    if (iter % 11 == 10) {
+      mu = d + zf(cabsf_(c) * 0.75f, 0.f);   // exceptional shift
+    } else {
+      const zf tr = a + d, det = a * d - b * c;
+      const zf half = tr * 0.5f;
+      const zf disc = half * half - det;
+      const float rdisc = cabsf_(disc);
+      // radicands clamped: hypotf's rounding can put |disc| + Re(disc) below zero
+      float sr = sqrtf(fmaxf(0.f, 0.5f * (rdisc + disc.re))), si = sqrtf(fmaxf(0.f, 0.5f * (rdisc - disc.re)));
+      if (disc.im < 0.f) si = -si;
+      const zf sq(sr, si);
+      const zf l1 = half + sq, l2 = half - sq;
+      mu = cabsf_(l1 - d) < cabsf_(l2 - d) ? l1 : l2;
+    }
+    const zf x = T[lo + lo * ld] - mu, y = T[lo + 1 + lo * ld];
+    for (int k = lo; k < hi; ++k) {
+      float cs;
+      zf sn;
+      if (k == lo) givens_f(x, y, &cs, &sn);
+      else givens_f(T[k + (k - 1) * ld], T[k + 1 + (k - 1) * ld], &cs, &sn);
+      __syncwarp();   // all lanes have read the rotation's defining entries
+      const int c0 = k > lo ? k - 1 : lo;
+      for (int col = c0 + lane; col <= hi; col += 32) {
+        const zf p = T[k + col * ld], q = T[k + 1 + col * ld];
+        T[k + col * ld] = cs * p + sn * q;
+        T[k + 1 + col * ld] = cs * q - conjg(sn) * p;
+      }
+      __syncwarp();
+      const int r1 = k + 2 < hi ? k + 2 : hi;
+      for (int row = lo + lane; row <= r1; row += 32) {
+        const zf p = T[row + k * ld], q = T[row + (k + 1) * ld];
+        T[row + k * ld] = cs * p + conjg(sn) * q;
+        T[row + (k + 1) * ld] = cs * q - sn * p;
+      }
+      __syncwarp();
+      if (k > lo && lane == 0) T[k + 1 + (k - 1) * ld] = zf(0.f, 0.f);
+      __syncwarp();
+    }
+  }
+  return true;
+}
+
+struct EigInts {   // integer area of the dense work buffer
+  int* piv; int* sel; int* pair; int* units; int* cols; int* ncand;
+};
+__device__ __host__ inline EigInts eig_ints(zd* work) {
+  int* b = reinterpret_cast<int*>(work + W_INT);
+  EigInts e;
+  e.piv = b; e.sel = b + MMAX; e.pair = b + MMAX + KMAX; e.units = b + MMAX + 2 * KMAX; e.cols = e.units + 1;
+  e.ncand = e.units + 2;
+  return e;
+}
+
+__global__ void __launch_bounds__(256) k_eig_a(RefreshInfo f, DevState* st, zd* work, int has_R, int m) {
   extern __shared__ unsigned char smraw[];
-  const Layout Lay = make_layout(f);
-  const int m = m_in > 0 ? m_in : (f.case_id == 0 ? f.s : Lay.nPhi);
-  zd* T = reinterpret_cast<zd*>(smraw);
-  zd* Q = T + m * m;
-  zd* v = Q + m * m;
+  const int ld = m | 1;   // odd leading dimension: conflict-free row access
+  zd* A = reinterpret_cast<zd*>(smraw);
+  zd* B = A + m * ld;
+  zd* v = B + m * ld;
   double* dsc = reinterpret_cast<double*>(v + MMAX);
   int* piv = reinterpret_cast<int*>(dsc + 4);
-  __shared__ int s_sel[KMAX], s_pair[KMAX], s_units, s_cols, s_ok;
-  zd* Lm = work + W_L;
-  zd* Rm = work + W_R;
-  zd* LU = work + W_LU;
-  zd* Y = work + W_Y;
-  zd* YL = work + W_YL;
+  zf* H = reinterpret_cast<zf*>(A);   // FP32 copy of the Hessenberg form, over R's LU
+  __shared__ int s_ok;
+  __shared__ double s_red[8];
+  const zd* Lm = work + W_L;
+  const zd* Rm = work + W_R;
+  const EigInts ei = eig_ints(work);
   if (threadIdx.x == 0) s_ok = 1;
-  // M = R^{-1} L   (T <- R, LU; Q <- L, solve)
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int r = e % m, c = e / m;
-    Q[e] = Lm[r + c * MMAX];
-    if (has_R) T[e] = Rm[r + c * MMAX];
+    B[r + c * ld] = Lm[r + c * MMAX];
+    if (has_R) A[r + c * ld] = Rm[r + c * MMAX];
   }
   __syncthreads();
   if (has_R) {
-    if (!lu_block(T, m, piv, dsc, nullptr)) { if (threadIdx.x == 0) s_ok = 0; }
+    if (!lu_block(A, m, ld, piv, dsc)) { if (threadIdx.x == 0) s_ok = 0; }
     __syncthreads();
-    if (!s_ok) { if (threadIdx.x == 0) { st->eig_status = 1; st->kk = 0; } return; }
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) LU[e] = T[e];
-    __syncthreads();
-    lu_solve_block(T, m, piv, Q, m);
+    if (!s_ok) { if (threadIdx.x == 0) { st->eig_status = 1; st->kk = 0; *ei.ncand = 0; } return; }
+    lu_solve_block(A, m, ld, piv, B, m, ld);   // B <- R^{-1} L
   }
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) { T[e] = Q[e]; Q[e] = (e % m == e / m) ? zd(1.0) : zd(); }
+  // The reduction to Hessenberg form stays in FP64: the harmonic Ritz pencils of these cycles are
+  // so ill-conditioned (R carries Lanczos and recycle vectors of very different norms) that an
+  // FP32 reduction moves their small eigenvalues by O(1); FP32 QR on the FP64 Hessenberg form
+  // still gives shifts to about 1e-4, which the FP64 refinement needs.
+  hessenberg_block(B, m, ld, v, dsc);
+  // FP32 copy scaled to entries of order one (the eigenvalues scale with it)
+  double amax = 0.0;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const zd h = B[(e % m) + (e / m) * ld];
+    amax = fmax(amax, fabs(h.re) + fabs(h.im));
+  }
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = amax;
   __syncthreads();
-  hessenberg_block(T, Q, m, v, dsc);
+  amax = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) amax = fmax(amax, s_red[w]);
+  if (!(amax > 0.0) || !isfinite(amax)) {
+    if (threadIdx.x == 0) { st->eig_status = 1; st->kk = 0; *ei.ncand = 0; }
+    return;
+  }
+  const double inv = 1.0 / amax;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int r = e % m, c = e / m;
+    const zd h = B[r + c * ld];
+    H[r + c * ld] = zf((float)(h.re * inv), (float)(h.im * inv));
+  }
+  __syncthreads();
   if (threadIdx.x < 32) {
-    const bool ok = schur_warp(T, Q, m, st->dbg);
+    const bool ok = qr_eigs_warp_f32(H, m, ld, st->dbg);
     if (threadIdx.x == 0 && !ok) s_ok = 0;
   }
   __syncthreads();
-  if (!s_ok) { if (threadIdx.x == 0) { st->eig_status = 2; st->kk = 0; } return; }
-  // eigenvalues and selection
+  if (!s_ok) { if (threadIdx.x == 0) { st->eig_status = 2; st->kk = 0; *ei.ncand = 0; } return; }
   if (threadIdx.x == 0) {
-    zd lam[MMAX];
-    for (int i = 0; i < m; ++i) lam[i] = T[i + i * m];
-    int cols = 0;
-    s_units = select_units(lam, m, f.k, f.real_path, s_sel, s_pair, &cols);
-    s_cols = cols;
+    // candidates: the k + NCAND_EXTRA finite FP32 eigenvalues closest to the origin; real /
+    // complex classification and the final selection wait for the FP64 refinement
+    int order[MMAX];
+    int cnt = 0;
+    for (int i = 0; i < m; ++i) {
+      const zf h = H[i + i * ld];
+      if (isfinite(h.re) && isfinite(h.im)) order[cnt++] = i;
+    }
+    for (int a = 1; a < cnt; ++a) {
+      const int vv = order[a];
+      const float av = cabs_(H[vv + vv * ld]);
+      int b = a - 1;
+      while (b >= 0 && cabs_(H[order[b] + order[b] * ld]) > av) { order[b + 1] = order[b]; --b; }
+      order[b + 1] = vv;
+    }
+    const int nc = min(cnt, f.k + NCAND_EXTRA);
+    for (int c = 0; c < nc; ++c) {
+      const zf h = H[order[c] + order[c] * ld];
+      work[W_LAM + c] = zd((double)h.re * amax, (double)h.im * amax);
+    }
+    *ei.ncand = nc;
+    st->eig_status = 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_eig_b(zd* work, int m, int has_R) {
+  extern __shared__ unsigned char smraw[];
+  const EigInts ei = eig_ints(work);
+  const int cand = blockIdx.x;
+  if (cand >= *ei.ncand) return;
+  const int ld = m | 1;
+  zd* A = reinterpret_cast<zd*>(smraw);   // L - sigma R, then its LU
+  zd* yr = A + m * ld;
+  zd* yl = yr + MMAX;
+  zd* tr = yl + MMAX;
+  zd* tl = tr + MMAX;
+  double* dsc = reinterpret_cast<double*>(tl + MMAX);
+  int* piv = reinterpret_cast<int*>(dsc + 4);
+  __shared__ int s_ok;
+  __shared__ zd s_lam;
+  const zd* Lm = work + W_L;
+  const zd* Rm = work + W_R;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto Rat = [&](int r, int c) -> zd { return has_R ? Rm[r + c * MMAX] : (r == c ? zd(1.0) : zd()); };
+  zd sigma = work[W_LAM + cand];
+  for (int e = threadIdx.x; e < m; e += blockDim.x) {
+    const double t = 1.0 + 0.5 * sin(1.7 * e + 0.3);   // fixed start: no zero entries, no structure
+    yr[e] = zd(t, 0.0);
+    yl[e] = zd(t, 0.0);
+  }
+  zd lam = sigma;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int r = e % m, c = e / m;
+      A[r + c * ld] = Lm[r + c * MMAX] - sigma * Rat(r, c);
+    }
+    if (threadIdx.x == 0) s_ok = 1;
+    __syncthreads();
+    if (!lu_block(A, m, ld, piv, dsc)) { if (threadIdx.x == 0) s_ok = 0; }
+    __syncthreads();
+    if (!s_ok) {
+      // sigma is an eigenvalue to working precision: nudge the zero pivots instead
+      if (threadIdx.x == 0) {
+        double an = 0.0;
+        for (int e = 0; e < m * m; ++e) an = fmax(an, cabs_(Lm[(e % m) + (e / m) * MMAX]));
+        for (int k = 0; k < m; ++k)
+          if (cabs_(A[k + k * ld]) == 0.0) A[k + k * ld] = zd(1e-15 * (an > 0 ? an : 1.0));
+      }
+      __syncthreads();
+    }
+    const int steps = pass == 0 ? 4 : 2;
+    for (int it = 0; it < steps; ++it) {
+      // right-hand sides R y (warp 0) and R^H yl (warp 1)
+      if (warp == 0)
+        for (int r = lane; r < m; r += 32) { zd acc = zd(); for (int c = 0; c < m; ++c) acc += Rat(r, c) * yr[c]; tr[r] = acc; }
+      if (warp == 1)
+        for (int r = lane; r < m; r += 32) { zd acc = zd(); for (int c = 0; c < m; ++c) acc += cmul(Rat(c, r), yl[c]); tl[r] = acc; }
+      __syncthreads();
+      if (warp == 0) lu_solve_warp(A, m, ld, piv, tr);
+      if (warp == 1) lu_solve_adj_warp(A, m, ld, piv, tl);
+      __syncthreads();
+      if (warp < 2) {   // normalise (largest entry 1 in modulus)
+        zd* t = warp == 0 ? tr : tl;
+        zd* y = warp == 0 ? yr : yl;
+        double big = 0.0;
+        for (int i = lane; i < m; i += 32) big = fmax(big, cabs_(t[i]));
+        for (int o = 16; o > 0; o >>= 1) big = fmax(big, __shfl_xor_sync(0xffffffffu, big, o));
+        const double sc = big > 0.0 ? 1.0 / big : 1.0;
+        for (int i = lane; i < m; i += 32) y[i] = t[i] * sc;
+      }
+      __syncthreads();
+    }
+    // two-sided Rayleigh quotient of the pencil: (yl^H L y) / (yl^H R y)
+    if (warp == 0) {
+      zd num = zd(), den = zd();
+      for (int r = lane; r < m; r += 32) {
+        zd ly = zd(), ry = zd();
+        for (int c = 0; c < m; ++c) { ly += Lm[r + c * MMAX] * yr[c]; ry += Rat(r, c) * yr[c]; }
+        num += cmul(yl[r], ly);
+        den += cmul(yl[r], ry);
+      }
+      num = warp_sum(num);
+      den = warp_sum(den);
+      if (lane == 0) s_lam = (cabs_(den) > 0.0) ? num / den : sigma;
+    }
+    __syncthreads();
+    lam = s_lam;
+    const bool finite = isfinite(lam.re) && isfinite(lam.im);
+    // the FP32 shift was close enough: the quotient did not move
+    if (!finite || cabs_(lam - sigma) <= 1e-6 * cabs_(lam)) break;
+    sigma = lam;
+  }
+  zd* Y = work + W_Y + cand * MMAX;
+  zd* YL = work + W_YL + cand * MMAX;
+  for (int e = threadIdx.x; e < m; e += blockDim.x) { Y[e] = yr[e]; YL[e] = yl[e]; }
+  if (threadIdx.x == 0) work[W_LAM2 + cand] = lam;
+}
+
+__global__ void __launch_bounds__(256) k_eig_c(RefreshInfo f, DevState* st, zd* work, zd* Wphi, zd* Wphit, int ldw,
+                                               double* lam_out, int m, int raw) {
+  const Layout Lay = make_layout(f);
+  const EigInts ei = eig_ints(work);
+  __shared__ int s_units;
+  if (threadIdx.x == 0) {
+    int units = 0, cols = 0;
+    if (st->eig_status == 0 && *ei.ncand > 0) {
+      zd lam[KMAX + NCAND_EXTRA];
+      for (int c = 0; c < *ei.ncand; ++c) {
+        // a candidate that refined to the eigenvalue of an earlier one is dropped
+        lam[c] = work[W_LAM2 + c];
+        for (int q = 0; q < c; ++q)
+          if (cabs_(lam[c] - work[W_LAM2 + q]) <= 1e-8 * cabs_(lam[c])) { lam[c] = zd(nan(""), 0.0); break; }
+      }
+      units = select_units(lam, *ei.ncand, f.k, f.real_path, ei.sel, ei.pair, &cols);
+    }
+    *ei.units = units;
+    *ei.cols = cols;
+    st->kk = cols;
+    s_units = units;
   }
   __syncthreads();
   const int units = s_units;
-  // eigenvectors of the triangular T: right y (back substitution), left yl (forward)
-  double tn = 0.0;
-  for (int e = 0; e < m; ++e) tn = fmax(tn, cabs_(T[e + e * m]));
-  const double small = 1e-14 * (tn > 0.0 ? tn : 1.0);
-  for (int u = threadIdx.x; u < 2 * units; u += blockDim.x) {
-    const int unit = u % units;
-    const bool left = u >= units;
-    const int i = s_sel[unit];
-    const zd lam = T[i + i * m];
-    zd* y = (left ? YL : Y) + unit * MMAX;
-    for (int r = 0; r < m; ++r) y[r] = zd();
-    y[i] = zd(1.0);
-    if (!left) {
-      for (int r = i - 1; r >= 0; --r) {
-        zd s = zd();
-        for (int c = r + 1; c <= i; ++c) s += T[r + c * m] * y[c];
-        zd d = T[r + r * m] - lam;
-        if (cabs_(d) < small) d = zd(small);
-        y[r] = -(s / d);
-      }
-    } else {
-      // y^H T = lam y^H  <=>  (T - lam I)^H y = 0, y_i = 1, y_r = 0 for r < i
-      for (int l = i + 1; l < m; ++l) {
-        zd s = zd();
-        for (int p = i; p < l; ++p) s += conjg(T[p + l * m]) * y[p];
-        zd d = conjg(lam) - conjg(T[l + l * m]);
-        if (cabs_(d) < small) d = zd(small);
-        y[l] = s / d;
-      }
+  if (st->eig_status != 0 || units <= 0) {
+    for (int e = threadIdx.x; e < m * 2; e += blockDim.x) {
+      zd* out = e >= m ? Wphit : Wphi;
+      for (int c = 0; c < ldw; ++c) out[(e % m) * ldw + c] = zd();
     }
+    return;
+  }
+  zd* Lv = work + W_GH;           // scratch: selected left vectors (stride MMAX)
+  zd* Rv = Lv + MMAX * KMAX;      // selected right vectors
+  for (int e = threadIdx.x; e < m * units; e += blockDim.x) {
+    const int r = e % m, u = e / m;
+    Rv[r + u * MMAX] = work[W_Y + ei.sel[u] * MMAX + r];
+    Lv[r + u * MMAX] = work[W_YL + ei.sel[u] * MMAX + r];
   }
   __syncthreads();
-  // back-transform: w = Q y -> Rm columns, u = Q yl -> Lm columns (L, R already consumed)
-  for (int e = threadIdx.x; e < m * units * 2; e += blockDim.x) {
-    const int r = e % m, u = (e / m) % units;
-    const bool left = e >= m * units;
-    const zd* y = (left ? YL : Y) + u * MMAX;
-    zd s = zd();
-    for (int c = 0; c < m; ++c) s += Q[r + c * m] * y[c];
-    if (left) Lm[r + u * MMAX] = s; else Rm[r + u * MMAX] = s;
-  }
-  __syncthreads();
-  // left vectors of the pencil: x = R^{-H} u
-  if (has_R) lu_solve_adj_block(LU, m, piv, Lm, units, MMAX);
-  // unit norm, largest component real and positive
-  if (threadIdx.x < 2 * units) {
+  if (threadIdx.x < 2 * units) {   // unit norm, largest component real and positive
     const int u = threadIdx.x % units;
     const bool left = threadIdx.x >= units;
-    zd* w = (left ? Lm : Rm) + u * MMAX;
+    zd* w = (left ? Lv : Rv) + u * MMAX;
     double nrm = 0.0, big = -1.0;
     int bi = 0;
     for (int r = 0; r < m; ++r) { const double a2 = abs2(w[r]); nrm += a2; if (a2 > big) { big = a2; bi = r; } }
@@ -586,15 +755,15 @@ __global__ void __launch_bounds__(256) k_eig(RefreshInfo f, DevState* st, zd* wo
   if (threadIdx.x == 0 && lam_out) {
     int col = 0;
     for (int u = 0; u < units; ++u) {
-      const zd lam = T[s_sel[u] + s_sel[u] * m];
+      const zd lam = work[W_LAM2 + ei.sel[u]];
       lam_out[2 * col] = lam.re; lam_out[2 * col + 1] = lam.im;
-      if (s_pair[u]) { lam_out[2 * col + 2] = lam.re; lam_out[2 * col + 3] = -lam.im; }
-      col += s_pair[u] ? 2 : 1;
+      if (ei.pair[u]) { lam_out[2 * col + 2] = lam.re; lam_out[2 * col + 3] = -lam.im; }
+      col += ei.pair[u] ? 2 : 1;
     }
   }
-  // write W (right) and Wt (left), row r = Phi column r, with the Phi scaling folded in
-  // (v_m = r_{m-1}/||r_{m-1}||, vt_m = rt_{m-1} ||r_{m-1}|| / conj(rho_{m-1})); a conjugate
-  // pair of a real problem contributes its real and imaginary parts.
+  // W (right) and Wt (left), row r = Phi column r, Phi scaling folded in (v_m = r_{m-1} /
+  // ||r_{m-1}||, vt_m = rt_{m-1} ||r_{m-1}|| / conj(rho_{m-1})); a conjugate pair of a real
+  // problem contributes its real and imaginary parts
   for (int e = threadIdx.x; e < m * 2; e += blockDim.x) {
     const int r = e % m;
     const bool left = e >= m;
@@ -607,10 +776,10 @@ __global__ void __launch_bounds__(256) k_eig(RefreshInfo f, DevState* st, zd* wo
     }
     int col = 0;
     for (int u = 0; u < units; ++u) {
-      const zd wv = (left ? Lm : Rm)[r + u * MMAX];
+      const zd wv = (left ? Lv : Rv)[r + u * MMAX];
       if (f.real_path) {
         out[r * ldw + col] = zd(sc.re * wv.re, 0.0);
-        if (s_pair[u]) { out[r * ldw + col + 1] = zd(sc.re * wv.im, 0.0); col += 2; } else col += 1;
+        if (ei.pair[u]) { out[r * ldw + col + 1] = zd(sc.re * wv.im, 0.0); col += 2; } else col += 1;
       } else {
         out[r * ldw + col] = sc * wv;
         col += 1;
@@ -618,7 +787,22 @@ __global__ void __launch_bounds__(256) k_eig(RefreshInfo f, DevState* st, zd* wo
     }
     for (int c = col; c < ldw; ++c) out[r * ldw + c] = zd();
   }
-  if (threadIdx.x == 0) { st->kk = s_cols; st->eig_status = 0; }
+}
+
+static void launch_eig3(const RefreshInfo& info, DevState* st, zd* work, zd* Wphi, zd* Wphit, int ldw,
+                        double* lam_out, int has_R, int m, int raw, cudaStream_t s) {
+  const int ld = m | 1;
+  const size_t smem_a = (size_t)(2 * m * ld + MMAX) * sizeof(zd) + 4 * sizeof(double) + MMAX * sizeof(int);
+  const size_t smem_b = (size_t)(m * ld + 4 * MMAX) * sizeof(zd) + 4 * sizeof(double) + MMAX * sizeof(int);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_eig_a, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * MMAX * (MMAX + 1) * sizeof(zd) + 8192);
+    cudaFuncSetAttribute(k_eig_b, cudaFuncAttributeMaxDynamicSharedMemorySize, MMAX * (MMAX + 1) * sizeof(zd) + 8192);
+    attr_set = true;
+  }
+  k_eig_a<<<1, 256, smem_a, s>>>(info, st, work, has_R, m);
+  k_eig_b<<<KMAX + NCAND_EXTRA, 256, smem_b, s>>>(work, m, has_R);
+  k_eig_c<<<1, 256, 0, s>>>(info, st, work, Wphi, Wphit, ldw, lam_out, m, raw);
 }
 
 template <class T>
@@ -637,13 +821,7 @@ void launch_dense_refresh(const RefreshInfo& info, DevState* st, const typename 
     k_lr<A><<<64, 256, 0, s>>>(info, st, G, work);
     m = (info.case_id == 2 ? info.kc : info.kp) + info.s;
   }
-  const size_t smem = (size_t)(2 * m * m + MMAX) * sizeof(zd) + 4 * sizeof(double) + MMAX * sizeof(int);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * MMAX * MMAX * sizeof(zd) + 8192);
-    attr_set = true;
-  }
-  k_eig<<<1, 256, smem, s>>>(info, st, work, Wphi, Wphit, ldw, lam_out, has_R, m, 0);
+  launch_eig3(info, st, work, Wphi, Wphit, ldw, lam_out, has_R, m, 0, s);
 }
 
 // Component entry: L (and R) already in work (W_L, W_R, ld MMAX); st is a scratch state that
@@ -658,9 +836,7 @@ void launch_dense_eig_host(int real_path, int m, const zd* L, const zd* R, int h
   info.k = k;
   info.real_path = real_path;
   DevState* st = reinterpret_cast<DevState*>(work + W_END);
-  const size_t smem = (size_t)(2 * m * m + MMAX) * sizeof(zd) + 4 * sizeof(double) + MMAX * sizeof(int);
-  cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * MMAX * MMAX * sizeof(zd) + 8192);
-  k_eig<<<1, 256, smem, s>>>(info, st, work, W, Wt, KMAX, lam, has_R, m, 1);
+  launch_eig3(info, st, work, W, Wt, KMAX, lam, has_R, m, 1, s);
 }
 
 // ------------------------------------------------------------------------------------

@@ -86,14 +86,59 @@ template <> __device__ __forceinline__ bool finite_acc<zd>(zd v) { return isfini
 
 // ------------------------------------------------------------------------------------
 // phase 1: dual SpMV with on-the-fly p update, projections
+//
+// The projections Ct^H z and C^H zt run over the contiguous 32 x LD slab of the row-major
+// bases that belongs to a warp's 32 rows: element e = lane + 32 t of the slab is row e / LD,
+// column e % LD, so loads are fully coalesced and every lane does useful work.  Because LD is a
+// multiple of 4, lane `lane` only ever meets the P = LD / gcd(LD, 32) <= 7 columns
+// (lane + 32 u) % LD, u < P, and keeps one accumulator per such column (slot u = t mod P).
+// The block then folds the slots back to columns in a fixed order.
 // ------------------------------------------------------------------------------------
-template <class V, class T, int KT>
+constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
+
+template <int LD> struct Slab {
+  static constexpr int G = cgcd(LD, 32);
+  static constexpr int P = LD / G;
+};
+
+// Fold one side's per-lane slot accumulators red[warp][lane][u] (A type, shared memory) into
+// per-block column sums out[c], c < LD; fixed order (deterministic).
+template <class A, int LD>
+__device__ void fold_slots(const A* red, A* wpart, int nwarps, A* out) {
+  constexpr int P = Slab<LD>::P;
+  // stage 1: item (c, w) sums over the lanes of warp w that hold column c
+  for (int it = threadIdx.x; it < LD * nwarps; it += blockDim.x) {
+    const int w = it % nwarps, c = it / nwarps;
+    A sacc = A(0.0);
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      int l0 = (c - 32 * u) % LD;
+      if (l0 < 0) l0 += LD;
+      for (int l = l0; l < 32; l += LD) sacc += red[(w * 32 + l) * P + u];
+    }
+    wpart[c * nwarps + w] = sacc;
+  }
+  __syncthreads();
+  // stage 2: column c sums over warps
+  for (int c = threadIdx.x; c < LD; c += blockDim.x) {
+    A sacc = A(0.0);
+    for (int w = 0; w < nwarps; ++w) sacc += wpart[c * nwarps + w];
+    out[c] = sacc;
+  }
+  __syncthreads();
+}
+
+template <class V, class T, int LD>
 __global__ void __launch_bounds__(NTHREADS) k_phase1(OpArgs<V> op, VecArgs<T> v, DevState* st,
                                                      typename traits<T>::acc* part) {
   typedef typename traits<T>::acc A;
-  constexpr int KA = KT > 0 ? KT : 1;
-  __shared__ A red[(NTHREADS / 32) * 2 * KA];
-  __shared__ A tot[2 * KA];
+  constexpr int NW = NTHREADS / 32;
+  constexpr int LDA = LD > 0 ? LD : 4;
+  constexpr int P = Slab<LDA>::P;
+  __shared__ T zs[NW][32], zts[NW][32];
+  __shared__ A red[LD > 0 ? NW * 32 * P : 1];       // one side at a time
+  __shared__ A wpart[LD > 0 ? LDA * NW : 1];
+  __shared__ A tot[2 * LDA];
   if (st->done) return;
   const int i = st->iter + 1;
   const T beta = from_zd<T>(st->beta), cbeta = conjg(beta);
@@ -104,58 +149,78 @@ __global__ void __launch_bounds__(NTHREADS) k_phase1(OpArgs<V> op, VecArgs<T> v,
   const T* __restrict__ pto = v.pt[(i - 1) & 1];
   T* __restrict__ pn = v.p[i & 1];
   T* __restrict__ ptn = v.pt[i & 1];
-  const int k = KT > 0 ? st->kc : 0;
   const T sh = shift_of<T>::get(op.sh_re, op.sh_im), shc = conjg(sh);
-  T a1[KA], a2[KA];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T a1[P], a2[P];
 #pragma unroll
-  for (int c = 0; c < KA; ++c) { a1[c] = T(0); a2[c] = T(0); }
+  for (int u = 0; u < P; ++u) { a1[u] = T(0); a2[u] = T(0); }
   const int stride = gridDim.x * blockDim.x;
-  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += stride) {
+  for (int base = blockIdx.x * blockDim.x + warp * 32; base < op.n; base += stride) {
+    const int row = base + lane;
     T z = T(0), zt = T(0);
-    const int e0 = op.rp[row], e1 = op.rp[row + 1];
-    if (op.shared) {
-      for (int e = e0; e < e1; ++e) {
-        const int j = op.ci[e];
-        z += vmul(op.va[e], r[j] + beta * po[j]);
-        zt += vmul(op.tva[e], rt[j] + cbeta * pto[j]);
+    if (row < op.n) {
+      const int e0 = op.rp[row], e1 = op.rp[row + 1];
+      if (op.shared) {
+        for (int e = e0; e < e1; ++e) {
+          const int j = op.ci[e];
+          z += vmul(op.va[e], r[j] + beta * po[j]);
+          zt += vmul(op.tva[e], rt[j] + cbeta * pto[j]);
+        }
+      } else {
+        for (int e = e0; e < e1; ++e) {
+          const int j = op.ci[e];
+          z += vmul(op.va[e], r[j] + beta * po[j]);
+        }
+        const int f0 = op.trp[row], f1 = op.trp[row + 1];
+        for (int e = f0; e < f1; ++e) {
+          const int j = op.tci[e];
+          zt += vmul(op.tva[e], rt[j] + cbeta * pto[j]);
+        }
       }
-    } else {
-      for (int e = e0; e < e1; ++e) {
-        const int j = op.ci[e];
-        z += vmul(op.va[e], r[j] + beta * po[j]);
-      }
-      const int f0 = op.trp[row], f1 = op.trp[row + 1];
-      for (int e = f0; e < f1; ++e) {
-        const int j = op.tci[e];
-        zt += vmul(op.tva[e], rt[j] + cbeta * pto[j]);
-      }
+      const T prow = r[row] + beta * po[row];
+      const T ptrow = rt[row] + cbeta * pto[row];
+      pn[row] = prow;
+      ptn[row] = ptrow;
+      if (op.has_shift) { z = sh * prow - z; zt = shc * ptrow - zt; }
+      v.z[row] = z;
+      v.zt[row] = zt;
     }
-    const T prow = r[row] + beta * po[row];
-    const T ptrow = rt[row] + cbeta * pto[row];
-    pn[row] = prow;
-    ptn[row] = ptrow;
-    if (op.has_shift) { z = sh * prow - z; zt = shc * ptrow - zt; }
-    v.z[row] = z;
-    v.zt[row] = zt;
-    if (KT > 0) {
-      const T* __restrict__ crow = v.C + (int64_t)row * v.ldk;
-      const T* __restrict__ ctrow = v.Ct + (int64_t)row * v.ldk;
+    if (LD > 0) {
+      zs[warp][lane] = z;
+      zts[warp][lane] = zt;
+      __syncwarp();
+      const int nvalid = op.n - base < 32 ? op.n - base : 32;
+      const T* __restrict__ ctb = v.Ct + (int64_t)base * LDA;
+      const T* __restrict__ cb = v.C + (int64_t)base * LDA;
 #pragma unroll
-      for (int c = 0; c < KA; ++c)
-        if (c < k) { a1[c] += cmul(ctrow[c], z); a2[c] += cmul(crow[c], zt); }
+      for (int t = 0; t < LDA; ++t) {
+        const int e = lane + 32 * t;
+        const int rr = e / LDA;
+        if (rr < nvalid) {
+          a1[t % P] += cmul(ctb[e], zs[warp][rr]);
+          a2[t % P] += cmul(cb[e], zts[warp][rr]);
+        }
+      }
+      __syncwarp();
     }
   }
-  if (KT == 0) return;
-  A vals[2 * KA];
+  if (LD == 0) return;
 #pragma unroll
-  for (int c = 0; c < KA; ++c) { vals[c] = cvt<A>(a1[c]); vals[KA + c] = cvt<A>(a2[c]); }
-  write_partials(vals, 2 * KA, red, part);
+  for (int u = 0; u < P; ++u) red[(warp * 32 + lane) * P + u] = cvt<A>(a1[u]);
+  __syncthreads();
+  fold_slots<A, LDA>(red, wpart, NW, tot);          // Ct^H z  -> tot[0 .. LD)
+#pragma unroll
+  for (int u = 0; u < P; ++u) red[(warp * 32 + lane) * P + u] = cvt<A>(a2[u]);
+  __syncthreads();
+  fold_slots<A, LDA>(red, wpart, NW, tot + LDA);    // C^H zt  -> tot[LD .. 2 LD)
+  if (threadIdx.x < 2 * LDA) part[(int64_t)blockIdx.x * (2 * LDA) + threadIdx.x] = tot[threadIdx.x];
   if (!arrive_last(&st->cnt[0])) return;
-  reduce_cols(part, gridDim.x, 2 * KA, tot);
+  reduce_cols(part, gridDim.x, 2 * LDA, tot);
+  const int k = st->kc;
   if (threadIdx.x < k) {
     const double d = st->Dc[threadIdx.x];
     st->zeta[threadIdx.x] = to_zd(tot[threadIdx.x] * (1.0 / d));
-    st->zetat[threadIdx.x] = to_zd(tot[KA + threadIdx.x] * (1.0 / d));
+    st->zetat[threadIdx.x] = to_zd(tot[LDA + threadIdx.x] * (1.0 / d));
   }
 }
 
@@ -169,15 +234,15 @@ __global__ void __launch_bounds__(NTHREADS) k_phase2(OpArgs<V> op, VecArgs<T> v,
   constexpr int KA = KT > 0 ? KT : 1;
   __shared__ A red[(NTHREADS / 32) * 3];
   __shared__ A tot[3];
+  __shared__ T ze[KA], zet[KA];   // zeta, zetat broadcast from shared memory (few registers)
   if (st->done) return;
   const int i = st->iter + 1;
   const int k = KT > 0 ? st->kc : 0;
-  T ze[KA], zet[KA];
-#pragma unroll
-  for (int c = 0; c < KA; ++c) {
+  for (int c = threadIdx.x; c < KA; c += blockDim.x) {
     ze[c] = c < k ? from_zd<T>(st->zeta[c]) : T(0);
     zet[c] = c < k ? from_zd<T>(st->zetat[c]) : T(0);
   }
+  __syncthreads();
   const T* __restrict__ pt = v.pt[i & 1];
   A pq = A(0.0), nq = A(0.0), npt = A(0.0);
   const int stride = gridDim.x * blockDim.x;
@@ -618,8 +683,20 @@ template <class V, class T>
 void launch_phase1(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
                    cudaStream_t s) {
   typedef typename traits<T>::acc A;
-#define RB_CALL(K) k_phase1<V, T, K><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part)
-  RB_KT_DISPATCH(kt, RB_CALL)
+  // kt == 0: no recycle space (no projection); otherwise dispatch on the bases' row stride
+  const int ld = kt == 0 ? 0 : v.ldk;
+#define RB_CALL(L) k_phase1<V, T, L><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part)
+  switch (ld) {
+    case 0: RB_CALL(0); break;
+    case 4: RB_CALL(4); break;
+    case 8: RB_CALL(8); break;
+    case 12: RB_CALL(12); break;
+    case 16: RB_CALL(16); break;
+    case 20: RB_CALL(20); break;
+    case 24: RB_CALL(24); break;
+    case 28: RB_CALL(28); break;
+    default: RB_CALL(32); break;
+  }
 #undef RB_CALL
 }
 template <class V, class T>
@@ -655,6 +732,12 @@ void launch_finish(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void*
   RB_KT_DISPATCH(kt, RB_CALL)
 #undef RB_CALL
   k_fin_b<V, T><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part);
+}
+template <class T>
+void launch_finish_a(const VecArgs<T>& v, DevState* st, int kt, int grid, cudaStream_t s) {
+#define RB_CALL(K) k_fin_a<T, K><<<grid, NTHREADS, 0, s>>>((int)v.n, v, st)
+  RB_KT_DISPATCH(kt, RB_CALL)
+#undef RB_CALL
 }
 template <class T>
 void launch_philox(T* out, int64_t n, uint64_t seed, cudaStream_t s) {
@@ -725,6 +808,10 @@ RB_INST_VT(cplx<double>, cplx<double>)
 RB_INST_VT(float, cplx<float>)
 RB_INST_VT(cplx<float>, cplx<float>)
 
+template void launch_finish_a<double>(const VecArgs<double>&, DevState*, int, int, cudaStream_t);
+template void launch_finish_a<float>(const VecArgs<float>&, DevState*, int, int, cudaStream_t);
+template void launch_finish_a<cplx<double>>(const VecArgs<cplx<double>>&, DevState*, int, int, cudaStream_t);
+template void launch_finish_a<cplx<float>>(const VecArgs<cplx<float>>&, DevState*, int, int, cudaStream_t);
 template void launch_philox<double>(double*, int64_t, uint64_t, cudaStream_t);
 template void launch_philox<float>(float*, int64_t, uint64_t, cudaStream_t);
 template void launch_philox<cplx<double>>(cplx<double>*, int64_t, uint64_t, cudaStream_t);

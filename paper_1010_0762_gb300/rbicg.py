@@ -29,7 +29,7 @@ class Params(C.Structure):
     _fields_ = [("k", C.c_int), ("s", C.c_int), ("max_itn", C.c_int), ("tol", C.c_double),
                 ("svd_tol", C.c_double), ("inner_tol", C.c_double), ("refine_max", C.c_int),
                 ("precision", C.c_int), ("seed", C.c_uint64), ("setup_fp32", C.c_int),
-                ("recycle", C.c_int), ("inner_svd_tol", C.c_double)]
+                ("recycle", C.c_int), ("inner_svd_tol", C.c_double), ("guard", C.c_double)]
 
 
 class CSRStruct(C.Structure):
@@ -41,7 +41,7 @@ class CSRStruct(C.Structure):
 class Result(C.Structure):
     _fields_ = [("iters", C.c_int), ("cycles", C.c_int), ("recycle_dim", C.c_int), ("refine_steps", C.c_int),
                 ("relres", C.c_double), ("relres_dual", C.c_double), ("true_relres", C.c_double),
-                ("true_relres_dual", C.c_double), ("status", C.c_int)]
+                ("true_relres_dual", C.c_double), ("status", C.c_int), ("fallback", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
