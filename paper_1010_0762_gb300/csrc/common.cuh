@@ -107,6 +107,10 @@ __device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_dow
 __device__ __forceinline__ cplx<double> shfl_down(cplx<double> v, int o) {
   return {__shfl_down_sync(0xffffffffu, v.re, o), __shfl_down_sync(0xffffffffu, v.im, o)};
 }
+__device__ __forceinline__ float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ cplx<float> shfl_down(cplx<float> v, int o) {
+  return {__shfl_down_sync(0xffffffffu, v.re, o), __shfl_down_sync(0xffffffffu, v.im, o)};
+}
 template <class A>
 __device__ __forceinline__ A warp_sum(A v) {
 #pragma unroll

@@ -156,6 +156,13 @@ struct Solver : SolverBase {
   int64_t n;
   int ldk, R, grid, gram_grid;
   cudaStream_t s;
+  // The cycle refresh (Sections 4.1-4.3) reads only the finished cycle's ring columns and
+  // scalar histories and writes only the next system's U_j, C_j: it runs on its own stream,
+  // concurrently with the next cycle's iterations.  The ring holds two cycles for that.
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_cycle = nullptr, ev_ref = nullptr;
+  bool ref_pending = false;
+  void* gpart = nullptr;        // Gram partials of the refresh (part belongs to the iteration)
   int64_t* launches;
   // operator (values in V; A^H values owned here)
   OpArgs<V> op{};
@@ -193,7 +200,14 @@ struct Solver : SolverBase {
   Solver(const rbicg_params& p_, int64_t n_, cudaStream_t s_, int64_t* launches_, Profiler* prof_)
       : prm(p_), n(n_), s(s_), launches(launches_), prof(prof_) {
     ldk = std::max(1, ((prm.k + 3) / 4) * 4);
-    R = prm.s + 2;
+    // ring of residuals r_m at slot m % R: a refresh after iteration j s reads r_{(j-1)s-1} ..
+    // r_{js} while cycle j+1 writes r_{js+1} .. r_{(j+1)s}
+    R = prm.recycle ? 2 * (prm.s + 2) : prm.s + 2;
+    int lo_prio = 0, hi_prio = 0;
+    RB_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+    RB_CUDA(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi_prio));
+    RB_CUDA(cudaEventCreateWithFlags(&ev_cycle, cudaEventDisableTiming));
+    RB_CUDA(cudaEventCreateWithFlags(&ev_ref, cudaEventDisableTiming));
     const int sms = num_sms();
     grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + NTHREADS - 1) / NTHREADS, (int64_t)sms * 8));
     gram_grid = 2 * sms;
@@ -216,6 +230,7 @@ struct Solver : SolverBase {
     const size_t part_elems =
         std::max<size_t>((size_t)grid * (2 * KMAX + 2), (size_t)gram_grid * 64 * 64);
     part = dmalloc<A>(part_elems);
+    gpart = dmalloc<A>((size_t)gram_grid * 64 * 64);
     G = dmalloc<A>((size_t)GRAM_MAXCOLS * GRAM_MAXCOLS);
     work = dmalloc<zd>(dense_work_elems_fwd());
     Wphi = dmalloc<zd>(MMAX * KMAX); Wphit = dmalloc<zd>(MMAX * KMAX);
@@ -228,16 +243,20 @@ struct Solver : SolverBase {
 
   ~Solver() override {
     cudaStreamSynchronize(s);
+    if (s2) cudaStreamSynchronize(s2);
     T* bufs[] = {ring, ringt, p[0], p[1], pt[0], pt[1], z, zt, U, Ut, C, Ct,
                  Uc[0], Uc[1], Utc[0], Utc[1], Cc[0], Cc[1], Ctc[0], Ctc[1]};
     for (T* b : bufs) cudaFree(b);
-    cudaFree(st); cudaFree(part); cudaFree(G); cudaFree(work); cudaFree(Wphi); cudaFree(Wphit);
+    cudaFree(st); cudaFree(part); cudaFree(gpart); cudaFree(G); cudaFree(work); cudaFree(Wphi); cudaFree(Wphit);
     cudaFree(Nmat); cudaFree(Mmat); cudaFree(sig); cudaFree(iflag);
     if (x_save) cudaFree(x_save);
     if (xt_save) cudaFree(xt_save);
     if (gz) cudaFree(gz);
     free_op();
     if (hv) cudaFreeHost(hv);
+    if (ev_cycle) cudaEventDestroy(ev_cycle);
+    if (ev_ref) cudaEventDestroy(ev_ref);
+    if (s2) cudaStreamDestroy(s2);
   }
 
   void free_op() {
@@ -251,9 +270,17 @@ struct Solver : SolverBase {
 
   void count(int k) { *launches += k; }
 
-  // Fetch the host view of the device state (one sync).
+  // Make the iteration stream wait for the refresh in flight (if any).
+  void join_refresh() {
+    if (!ref_pending) return;
+    RB_CUDA(cudaStreamWaitEvent(s, ev_ref, 0));
+    ref_pending = false;
+  }
+
+  // Fetch the host view of the device state (one sync, after the refresh in flight).
   void fetch() {
     RB_CUDA(cudaGetLastError());   // a failed launch must not leave the host loop waiting
+    join_refresh();
     RB_CUDA(cudaMemcpyAsync(hv, st, sizeof(HostView), cudaMemcpyDeviceToHost, s));
     RB_CUDA(cudaStreamSynchronize(s));
     prof->harvest();
@@ -331,7 +358,7 @@ struct Solver : SolverBase {
     append_block(X, Ct, prm.k); append_block(X, C, prm.k);
     append_block(Y, C, prm.k); append_block(Y, Ct, prm.k);
     launch_gram<T>(X, Y, n, 0, part, gram_grid, G, s);
-    launch_dense_svd(!traits<T>::cx, kdev, prm.k, reinterpret_cast<const zd*>(as_zd_gram()), nullptr, nullptr,
+    launch_dense_svd(!traits<T>::cx, kdev, prm.k, reinterpret_cast<const zd*>(as_zd_gram(s)), nullptr, nullptr,
                      prm.svd_tol, Nmat, Mmat, sig, &st->kc, st->Dc, iflag + 2, s);
     launch_rotate<T>(U, ldk, Nmat, kdev, &st->kc, prm.k, n, 0, s);
     launch_rotate<T>(C, ldk, Nmat, kdev, &st->kc, prm.k, n, 0, s);
@@ -345,10 +372,10 @@ struct Solver : SolverBase {
 
   // The Gram output is A (double for real problems); the dense SVD reads complex entries.
   zd* gz = nullptr;
-  const zd* as_zd_gram() {
+  const zd* as_zd_gram(cudaStream_t st_) {
     if (traits<T>::cx) return reinterpret_cast<const zd*>(G);
     if (!gz) gz = dmalloc<zd>((size_t)GRAM_MAXCOLS * GRAM_MAXCOLS);
-    launch_real_to_zd(reinterpret_cast<const double*>(G), gz, (int64_t)GRAM_MAXCOLS * GRAM_MAXCOLS, s);
+    launch_real_to_zd(reinterpret_cast<const double*>(G), gz, (int64_t)GRAM_MAXCOLS * GRAM_MAXCOLS, st_);
     count(1);
     return gz;
   }
@@ -357,6 +384,9 @@ struct Solver : SolverBase {
   // Runs after iteration j*s.  kp = columns of U_{j-1}.  Returns nothing; results are read
   // at the next sync (st->pcyc, st->eig_status).
   void refresh(int j, int kp, const T* /*unused*/) {
+    RB_CUDA(cudaEventRecord(ev_cycle, s));
+    RB_CUDA(cudaStreamWaitEvent(s2, ev_cycle, 0));
+    cudaStream_t q = s2;
     const bool first = kc == 0;
     RefreshInfo f{};
     f.case_id = first ? (j == 1 ? 0 : 1) : (j == 1 ? 2 : 3);
@@ -383,33 +413,35 @@ struct Solver : SolverBase {
       append_block(Pht, Utb, kb);
       append_ring(Ph, ring, (j - 1) * ss, j * ss - 1);
       append_ring(Pht, ringt, (j - 1) * ss, j * ss - 1);
-      const int pg = prof->begin(3, s);
-      launch_gram<T>(X, Y, n, prm.setup_fp32, part, gram_grid, G, s);
-      prof->end(pg, 2, s);
+      const int pg = prof->begin(3, q);
+      launch_gram<T>(X, Y, n, prm.setup_fp32, gpart, gram_grid, G, q);
+      prof->end(pg, 2, q);
       count(2);
     }
-    const int pd = prof->begin(4, s);
-    launch_dense_refresh<T>(f, st, G, work, Wphi, Wphit, KMAX, nullptr, s);
-    prof->end(pd, f.case_id == 0 ? 2 : 4, s);
+    const int pd = prof->begin(4, q);
+    launch_dense_refresh<T>(f, st, G, work, Wphi, Wphit, KMAX, nullptr, q);
+    prof->end(pd, f.case_id == 0 ? 2 : 4, q);
     count(f.case_id == 0 ? 2 : 4);
-    const int pb = prof->begin(5, s);
+    const int pb = prof->begin(5, q);
     int* kk = &st->kk;
-    launch_combine<T>(Ph, Wphi, KMAX, kk, prm.k, Uc[jc], ldk, n, prm.setup_fp32, s);
-    launch_combine<T>(Pht, Wphit, KMAX, kk, prm.k, Utc[jc], ldk, n, prm.setup_fp32, s);
-    launch_spmm<V, T>(op, 0, Uc[jc], ldk, kk, prm.k, Cc[jc], prm.setup_fp32, s);
-    launch_spmm<V, T>(op, 1, Utc[jc], ldk, kk, prm.k, Ctc[jc], prm.setup_fp32, s);
+    launch_combine<T>(Ph, Wphi, KMAX, kk, prm.k, Uc[jc], ldk, n, prm.setup_fp32, q);
+    launch_combine<T>(Pht, Wphit, KMAX, kk, prm.k, Utc[jc], ldk, n, prm.setup_fp32, q);
+    launch_spmm<V, T>(op, 0, Uc[jc], ldk, kk, prm.k, Cc[jc], prm.setup_fp32, q);
+    launch_spmm<V, T>(op, 1, Utc[jc], ldk, kk, prm.k, Ctc[jc], prm.setup_fp32, q);
     ColList<T> X2{}, Y2{};
     append_block(X2, Ctc[jc], prm.k); append_block(X2, Cc[jc], prm.k);
     append_block(Y2, Cc[jc], prm.k); append_block(Y2, Ctc[jc], prm.k);
-    launch_gram<T>(X2, Y2, n, prm.setup_fp32, part, gram_grid, G, s);
-    launch_dense_svd(!traits<T>::cx, kk, prm.k, as_zd_gram(), nullptr, nullptr, prm.svd_tol, Nmat, Mmat, sig,
-                     &st->pcyc, nullptr, iflag + 3, s);
-    launch_rotate<T>(Uc[jc], ldk, Nmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, s);
-    launch_rotate<T>(Cc[jc], ldk, Nmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, s);
-    launch_rotate<T>(Utc[jc], ldk, Mmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, s);
-    launch_rotate<T>(Ctc[jc], ldk, Mmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, s);
-    prof->end(pb, 11, s);
+    launch_gram<T>(X2, Y2, n, prm.setup_fp32, gpart, gram_grid, G, q);
+    launch_dense_svd(!traits<T>::cx, kk, prm.k, as_zd_gram(q), nullptr, nullptr, prm.svd_tol, Nmat, Mmat, sig,
+                     &st->pcyc, nullptr, iflag + 3, q);
+    launch_rotate<T>(Uc[jc], ldk, Nmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, q);
+    launch_rotate<T>(Cc[jc], ldk, Nmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, q);
+    launch_rotate<T>(Utc[jc], ldk, Mmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, q);
+    launch_rotate<T>(Ctc[jc], ldk, Mmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, q);
+    prof->end(pb, 11, q);
     count(11);
+    RB_CUDA(cudaEventRecord(ev_ref, q));
+    ref_pending = true;
   }
 
   // ------------------------------------------------------------------ Algorithm 2
@@ -487,6 +519,7 @@ struct Solver : SolverBase {
       const bool bad_end = done == DONE_BREAK_RHO || done == DONE_BREAK_PQ || done == DONE_NONFINITE;
       const bool stalled = !done && iter >= guard_limit;
       if (guard_limit != 0x7fffffff && (stalled || bad_end)) {
+        join_refresh();   // the restart rewrites ring slots and histories a refresh may read
         if (done == DONE_NONFINITE) {
           // the iterate may hold non-finite values: restart from the saved initial guess
           RB_CUDA(cudaMemcpyAsync(x, x_save, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));

@@ -13,9 +13,13 @@
 //    scaling (Section 4.3, eq. (equationSVD)); truncation at svd_tol; rotation coefficients.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
 
 namespace rb {
+
+namespace cg = cooperative_groups;
 
 constexpr int PSIMAX = 2 * KMAX + SMAX + 2;   // rows of H (columns of Psi)
 
@@ -113,10 +117,14 @@ __device__ int phi_ycol(const Layout& L, int b) {
 }
 
 // work layout (zd): Hd [PSIMAX x MMAX], Htd [PSIMAX x MMAX], GH [PSIMAX x MMAX],
-// Lm [MMAX x MMAX], Rm [MMAX x MMAX] (column-major), then eig scratch.
+// Lm [MMAX x MMAX], Rm [MMAX x MMAX] (column-major), then the eigen pipeline's data:
+// H (Hessenberg form of R^{-1} L), QV / QF (Householder vectors and factors), RI (R^{-1}),
+// Y / YL (candidate eigenvectors), LAM / LAM2 (FP32 shifts, refined eigenvalues), integers.
 constexpr int64_t W_HD = 0, W_HTD = W_HD + PSIMAX * MMAX, W_GH = W_HTD + PSIMAX * MMAX,
                   W_L = W_GH + PSIMAX * MMAX, W_R = W_L + MMAX * MMAX,
-                  W_Y = W_R + MMAX * MMAX, W_YL = W_Y + MMAX * (KMAX + 8), W_LAM = W_YL + MMAX * (KMAX + 8),
+                  W_H = W_R + MMAX * MMAX, W_QV = W_H + MMAX * MMAX, W_QF = W_QV + MMAX * MMAX,
+                  W_RI = W_QF + MMAX,
+                  W_Y = W_RI + MMAX * MMAX, W_YL = W_Y + MMAX * (KMAX + 8), W_LAM = W_YL + MMAX * (KMAX + 8),
                   W_LAM2 = W_LAM + KMAX + 8, W_INT = W_LAM2 + KMAX + 8,
                   W_END = W_INT + (MMAX + 2 * KMAX + 8 + 3) / 4 + 1;
 static_assert(PSIMAX * MMAX >= 2 * MMAX * KMAX, "k_eig_c keeps the selected vectors in the GH area");
@@ -205,154 +213,10 @@ __global__ void k_t1(RefreshInfo f, const DevState* st, zd* work) {
 __device__ __forceinline__ double cabs_(zd a) { return hypot(a.re, a.im); }
 typedef cplx<float> zf;
 __device__ __forceinline__ float cabs_(zf a) { return hypotf(a.re, a.im); }
-
-template <class S> struct real_t;
-template <> struct real_t<zd> { typedef double t; };
-template <> struct real_t<zf> { typedef float t; };
-
-// Block-wide LU with partial pivoting of A (m x m, leading dimension ld) in place;
-// piv[k] = pivot row of step k.  Returns false on an exactly zero pivot column.
-template <class S>
-__device__ bool lu_block(S* A, int m, int ld, int* piv, typename real_t<S>::t* dsc) {
-  typedef typename real_t<S>::t Rl;
-  for (int k = 0; k < m; ++k) {
-    if (threadIdx.x < 32) {
-      Rl best = -1;
-      int bi = k;
-      for (int r = k + threadIdx.x; r < m; r += 32) {
-        const Rl v = cabs_(A[r + k * ld]);
-        if (v > best) { best = v; bi = r; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const Rl ob = __shfl_down_sync(0xffffffffu, best, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (threadIdx.x == 0) { piv[k] = bi; dsc[0] = best; }
-    }
-    __syncthreads();
-    const int p = piv[k];
-    if (dsc[0] == Rl(0)) return false;
-    if (p != k)
-      for (int c = threadIdx.x; c < m; c += blockDim.x) {
-        const S t = A[k + c * ld]; A[k + c * ld] = A[p + c * ld]; A[p + c * ld] = t;
-      }
-    __syncthreads();
-    const S inv = S(Rl(1)) / A[k + k * ld];
-    for (int r = k + 1 + threadIdx.x; r < m; r += blockDim.x) A[r + k * ld] = A[r + k * ld] * inv;
-    __syncthreads();
-    const int rem = m - k - 1;
-    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-      const int r = k + 1 + e % rem, c = k + 1 + e / rem;
-      A[r + c * ld] -= A[r + k * ld] * A[k + c * ld];
-    }
-    __syncthreads();
-  }
-  return true;
-}
-
-// Block-wide: columns of B (stride ldb) <- A^{-1} B for the LU of A (one thread per column)
-template <class S>
-__device__ void lu_solve_block(const S* LU, int m, int ld, const int* piv, S* B, int nb, int ldb) {
-  for (int col = threadIdx.x; col < nb; col += blockDim.x) {
-    S* b = B + col * ldb;
-    for (int k = 0; k < m; ++k) { const int p = piv[k]; if (p != k) { const S t = b[k]; b[k] = b[p]; b[p] = t; } }
-    for (int r = 0; r < m; ++r) { S s = b[r]; for (int c = 0; c < r; ++c) s -= LU[r + c * ld] * b[c]; b[r] = s; }
-    for (int r = m - 1; r >= 0; --r) {
-      S s = b[r];
-      for (int c = r + 1; c < m; ++c) s -= LU[r + c * ld] * b[c];
-      b[r] = s / LU[r + r * ld];
-    }
-  }
-  __syncthreads();
-}
-
-// One warp: y <- A^{-1} y (A = P^T Lw U stored as LU, pivots piv), column-oriented substitution
-__device__ void lu_solve_warp(const zd* LU, int m, int ld, const int* piv, zd* y) {
-  const int lane = threadIdx.x & 31;
-  if (lane == 0)
-    for (int k = 0; k < m; ++k) { const int p = piv[k]; if (p != k) { const zd t = y[k]; y[k] = y[p]; y[p] = t; } }
-  __syncwarp();
-  for (int c = 0; c < m; ++c) {          // unit lower triangular
-    const zd yc = y[c];
-    __syncwarp();
-    for (int r = c + 1 + lane; r < m; r += 32) y[r] -= LU[r + c * ld] * yc;
-    __syncwarp();
-  }
-  for (int c = m - 1; c >= 0; --c) {     // upper triangular
-    const zd yc = y[c] / LU[c + c * ld];
-    __syncwarp();
-    if (lane == 0) y[c] = yc;
-    for (int r = lane; r < c; r += 32) y[r] -= LU[r + c * ld] * yc;
-    __syncwarp();
-  }
-}
-
-// One warp: y <- A^{-H} y.  A^H = U^H Lw^H P: solve U^H z = y, Lw^H w = z, y = P^T w.
-__device__ void lu_solve_adj_warp(const zd* LU, int m, int ld, const int* piv, zd* y) {
-  const int lane = threadIdx.x & 31;
-  for (int c = 0; c < m; ++c) {          // U^H lower triangular: column c of U^H = conj(U[c, :])
-    const zd yc = y[c] / conjg(LU[c + c * ld]);
-    __syncwarp();
-    if (lane == 0) y[c] = yc;
-    for (int r = c + 1 + lane; r < m; r += 32) y[r] -= conjg(LU[c + r * ld]) * yc;
-    __syncwarp();
-  }
-  for (int c = m - 1; c >= 0; --c) {     // Lw^H unit upper triangular: column c = conj(Lw[c, :])
-    const zd yc = y[c];
-    __syncwarp();
-    for (int r = lane; r < c; r += 32) y[r] -= conjg(LU[c + r * ld]) * yc;
-    __syncwarp();
-  }
-  if (lane == 0)
-    for (int k = m - 1; k >= 0; --k) { const int p = piv[k]; if (p != k) { const zd t = y[k]; y[k] = y[p]; y[p] = t; } }
-  __syncwarp();
-}
-
-// Block-wide Householder reduction of T (m x m, ld) to upper Hessenberg form (no vectors)
-template <class S>
-__device__ void hessenberg_block(S* T, int m, int ld, S* v, typename real_t<S>::t* dsc) {
-  typedef typename real_t<S>::t Rl;
-  for (int j = 0; j < m - 2; ++j) {
-    const int len = m - j - 1;
-    if (threadIdx.x < 32) {
-      Rl sacc = 0;
-      for (int r = threadIdx.x; r < len; r += 32) sacc += abs2(T[j + 1 + r + j * ld]);
-      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
-      if (threadIdx.x == 0) dsc[0] = sacc;
-    }
-    __syncthreads();
-    const Rl nx2 = dsc[0];
-    const S x0 = T[j + 1 + j * ld];
-    const Rl tail = nx2 - abs2(x0);
-    if (!(tail > Rl(0)) || tail <= nx2 * Rl(1e-30)) { __syncthreads(); continue; }
-    const Rl nx = sqrt(nx2);
-    const Rl ax0 = cabs_(x0);
-    const S ph = ax0 > Rl(0) ? x0 * (Rl(1) / ax0) : S(Rl(1));
-    const S alpha = -(ph * nx);
-    for (int r = threadIdx.x; r < len; r += blockDim.x) v[r] = T[j + 1 + r + j * ld];
-    __syncthreads();
-    if (threadIdx.x == 0) v[0] = v[0] - alpha;
-    __syncthreads();
-    const Rl f = Rl(2) / (tail + abs2(x0 - alpha));
-    for (int c = j + threadIdx.x; c < m; c += blockDim.x) {
-      S w = S(Rl(0));
-      for (int r = 0; r < len; ++r) w += cmul(v[r], T[j + 1 + r + c * ld]);
-      w = w * f;
-      for (int r = 0; r < len; ++r) T[j + 1 + r + c * ld] -= v[r] * w;
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < m; r += blockDim.x) {
-      S u = S(Rl(0));
-      for (int c = 0; c < len; ++c) u += T[r + (j + 1 + c) * ld] * v[c];
-      u = u * f;
-      for (int c = 0; c < len; ++c) T[r + (j + 1 + c) * ld] -= u * conjg(v[c]);
-    }
-    __syncthreads();
-    for (int r = j + 2 + threadIdx.x; r < m; r += blockDim.x) T[r + j * ld] = S(Rl(0));
-    __syncthreads();
-  }
-}
+// |re| + |im|: the pivot and scale measure of complex LU (no square root; within a factor
+// sqrt(2) of the modulus).  FP64 hypot costs dozens of FP64 instructions on this part.
+__device__ __forceinline__ double cabs1_(zd a) { return fabs(a.re) + fabs(a.im); }
+__device__ __forceinline__ float cabs1_(zf a) { return fabsf(a.re) + fabsf(a.im); }
 
 // Selection of eigenvalue indices (reading: k closest to the origin; on a real problem a
 // conjugate pair is one unit of two columns, k-1 columns if it straddles the cut).
@@ -363,12 +227,14 @@ __device__ int select_units(const zd* lam, int m, int k, int real_path, int* sel
   int cnt = 0;
   for (int i = 0; i < m; ++i)
     if (isfinite(lam[i].re) && isfinite(lam[i].im)) order[cnt++] = i;
-  // insertion sort by (|lam|, index)
+  // insertion sort by (|lam|, index); |lam|^2 orders the same way without square roots
+  double mag[MMAX];
+  for (int i = 0; i < m; ++i) mag[i] = abs2(lam[i]);
   for (int a = 1; a < cnt; ++a) {
     const int v = order[a];
-    const double av = cabs_(lam[v]);
+    const double av = mag[v];
     int b = a - 1;
-    while (b >= 0 && (cabs_(lam[order[b]]) > av || (cabs_(lam[order[b]]) == av && order[b] > v))) { order[b + 1] = order[b]; --b; }
+    while (b >= 0 && (mag[order[b]] > av || (mag[order[b]] == av && order[b] > v))) { order[b + 1] = order[b]; --b; }
     order[b + 1] = v;
   }
   bool used[MMAX];
@@ -377,7 +243,7 @@ __device__ int select_units(const zd* lam, int m, int k, int real_path, int* sel
   for (int t = 0; t < cnt; ++t) {
     const int i = order[t];
     if (used[i]) continue;
-    const double al = cabs_(lam[i]);
+    const double al = sqrt(mag[i]);
     const bool isreal = !real_path || fabs(lam[i].im) <= 1e-10 * (al > 0.0 ? al : 1.0);
     if (!real_path || isreal) {
       if (cols + 1 > k) break;
@@ -389,7 +255,7 @@ __device__ int select_units(const zd* lam, int m, int k, int real_path, int* sel
     double best = 1e300;
     for (int q = 0; q < m; ++q) {
       if (used[q] || q == i) continue;
-      const double dd = cabs_(lam[q] - conjg(lam[i]));
+      const double dd = abs2(lam[q] - conjg(lam[i]));
       if (dd < best) { best = dd; pj = q; }
     }
     if (cols + 2 > k) break;
@@ -405,20 +271,25 @@ __device__ int select_units(const zd* lam, int m, int k, int real_path, int* sel
 }
 
 // ------------------------------------------------------------------------------------
-// Eigen pipeline (three kernels).
-//   k_eig_a (one block): M = R^{-1} L (FP64 LU with partial pivoting), FP64 Householder
-//     reduction to Hessenberg form, eigenvalues by an FP32 implicit single-shift QR restricted
-//     to the active window, and the k + NCAND_EXTRA eigenvalues closest to 0 as candidates
-//     (shifts for the FP64 refinement).
-//   k_eig_b (one block per candidate, FP64): inverse iteration on the pencil itself,
-//     (L - sigma R) y+ = R y and (L - sigma R)^H yl+ = R^H yl (dense LU with partial pivoting),
-//     then the two-sided Rayleigh quotient yl^H L y / yl^H R y; when that quotient has moved
-//     away from the FP32 shift, one more factorisation at the quotient (a Rayleigh step).
+// Eigen pipeline of eq. (finalGenEigValue), three kernels.
+//   k_eig_cl (one cluster of ECL CTAs, FP64, columns of [R | L | I] dealt round-robin to the
+//     CTAs): Gauss-Jordan elimination with partial pivoting, [R | L | I] -> [I | M | R^{-1}],
+//     M = R^{-1} L; Householder reduction of M to Hessenberg form H = Q^H M Q (Householder
+//     vectors kept); then CTA 0 runs an FP32 implicit single-shift QR on the scaled H for the
+//     eigenvalues and nominates the k + NCAND_EXTRA closest to 0 as candidates.
+//   k_eig_h (one block per candidate, FP64): inverse iteration on H for the right and left
+//     eigenvectors z, zl of H (O(m^2) per step: H - sigma I is upper Hessenberg, so its LU
+//     with partial pivoting only exchanges neighbouring rows), one Rayleigh-quotient update of
+//     the shift; then y = Q z, yl = R^{-H} Q zl are the pencil's right and left eigenvectors and
+//     yl^H L y / yl^H R y its eigenvalue.
 //   k_eig_c (one block): candidates that refined to the same eigenvalue are merged, final
 //     selection on the refined eigenvalues (real / complex decided in FP64), unit norm,
 //     conjugate pairs split into real and imaginary parts, Phi scalings.
-// The QR iteration is long and sequential; on this part FP64 runs at about 2 FMA per clock per
-// SM and FP32 at 64x that, so it runs in FP32 and the eigenpairs are refined in FP64.
+// GB300 executes FP64 at about 1.75 FMA per clock per SM, and the pencils of these cycles are so
+// ill-conditioned (R carries Lanczos and recycle vectors of very different norms) that the
+// reduction must stay in FP64: it is spread over a cluster of SMs (distributed shared memory
+// for the per-step broadcasts and reductions).  The QR iteration is long and sequential and
+// runs in FP32 (64x the FP64 rate); its eigenvalues are only shifts for the FP64 refinement.
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ float cabsf_(zf a) { return hypotf(a.re, a.im); }
 
@@ -522,80 +393,244 @@ __device__ __host__ inline EigInts eig_ints(zd* work) {
   return e;
 }
 
-__global__ void __launch_bounds__(256) k_eig_a(RefreshInfo f, DevState* st, zd* work, int has_R, int m) {
-  extern __shared__ unsigned char smraw[];
-  const int ld = m | 1;   // odd leading dimension: conflict-free row access
-  zd* A = reinterpret_cast<zd*>(smraw);
-  zd* B = A + m * ld;
-  zd* v = B + m * ld;
-  double* dsc = reinterpret_cast<double*>(v + MMAX);
-  int* piv = reinterpret_cast<int*>(dsc + 4);
-  zf* H = reinterpret_cast<zf*>(A);   // FP32 copy of the Hessenberg form, over R's LU
-  __shared__ int s_ok;
+constexpr int ECL = 8;                                   // CTAs of the eigen cluster (portable size)
+constexpr int ECL_COLS = (3 * MMAX + ECL - 1) / ECL;     // local columns of [R | L | I] per CTA
+
+struct EclBcast {   // one elimination / reflection step, written by the CTA owning its column
+  zd col[MMAX];     // Gauss-Jordan: pivot column after the row exchange; Householder: v
+  zd f;             // Householder: 2 / ||v||^2
+  int piv, flag;    // Gauss-Jordan: pivot row, 1 = zero pivot; Householder: 1 = no reflection
+};
+
+__global__ void __cluster_dims__(ECL, 1, 1) __launch_bounds__(256)
+k_eig_cl(RefreshInfo f, DevState* st, zd* work, int has_R, int m) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  zd* cols = reinterpret_cast<zd*>(smraw);   // local column lc at cols + lc * MMAX
+  __shared__ EclBcast bc[2];
+  __shared__ zd up[2][MMAX];   // this CTA's part of T v (right Householder update)
+  __shared__ zd lv[MMAX];      // local copy of the broadcast column
+  __shared__ zd uvec[MMAX];
+  __shared__ zd tv[ECL_COLS];
   __shared__ double s_red[8];
+  __shared__ int s_piv, s_skip;
+  __shared__ zd s_inva, s_f;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   const zd* Lm = work + W_L;
   const zd* Rm = work + W_R;
   const EigInts ei = eig_ints(work);
-  if (threadIdx.x == 0) s_ok = 1;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int r = e % m, c = e / m;
-    B[r + c * ld] = Lm[r + c * MMAX];
-    if (has_R) A[r + c * ld] = Rm[r + c * MMAX];
+  // global columns: has_R: [0, m) R, [m, 2m) L -> M, [2m, 3m) I -> R^{-1}; else [0, m) L = M.
+  // Local column lc of CTA `rank` is global column rank + lc ECL.
+  const int ncol = has_R ? 3 * m : m;
+  const int mcol0 = has_R ? m : 0;
+  const int nloc = ncol > rank ? (ncol - rank + ECL - 1) / ECL : 0;
+  for (int e = tid; e < nloc * m; e += blockDim.x) {
+    const int lc = e / m, r = e % m, g = rank + lc * ECL;
+    zd v;
+    if (!has_R) v = Lm[r + g * MMAX];
+    else if (g < m) v = Rm[r + g * MMAX];
+    else if (g < 2 * m) v = Lm[r + (g - m) * MMAX];
+    else v = (r == g - 2 * m) ? zd(1.0) : zd();
+    cols[lc * MMAX + r] = v;
   }
+  if (tid == 0) s_skip = 1;
+  bool failed = false;   // per thread, always equal in all threads: every thread reads the flags
   __syncthreads();
-  if (has_R) {
-    if (!lu_block(A, m, ld, piv, dsc)) { if (threadIdx.x == 0) s_ok = 0; }
-    __syncthreads();
-    if (!s_ok) { if (threadIdx.x == 0) { st->eig_status = 1; st->kk = 0; *ei.ncand = 0; } return; }
-    lu_solve_block(A, m, ld, piv, B, m, ld);   // B <- R^{-1} L
+  // Every CTA runs the same sequence of cluster barriers whatever the data (a failed pivot only
+  // switches the arithmetic off), so no CTA can wait at a barrier that another never reaches.
+  // ---- Gauss-Jordan with partial pivoting: one cluster barrier per column
+  for (int k = 0; has_R && k < m; ++k) {
+    const int owner = k % ECL;
+    if (rank == owner && warp == 0 && !failed) {
+      const zd* c = cols + (k / ECL) * MMAX;
+      double best = -1.0;
+      int bi = k;
+      for (int r = k + lane; r < m; r += 32) {
+        const double v = cabs1_(c[r]);
+        if (v > best) { best = v; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      bi = __shfl_sync(0xffffffffu, bi, 0);
+      best = __shfl_sync(0xffffffffu, best, 0);
+      EclBcast& B = bc[k & 1];
+      for (int r = lane; r < m; r += 32) B.col[r] = c[r == k ? bi : (r == bi ? k : r)];
+      if (lane == 0) { B.piv = bi; B.flag = (best > 0.0 && isfinite(best)) ? 0 : 1; }
+    }
+    cl.sync();
+    if (!failed) {
+      const EclBcast* rb = cl.map_shared_rank(&bc[k & 1], owner);
+      for (int r = tid; r < m; r += blockDim.x) lv[r] = rb->col[r];
+      if (tid == 0) s_piv = rb->piv;
+      if (rb->flag) failed = true;
+      __syncthreads();
+      if (!failed) {
+        const int p = s_piv;
+        if (tid == 0) s_inva = zd(1.0) / lv[k];
+        __syncthreads();
+        const zd inva = s_inva;
+        for (int lc = tid; lc < nloc; lc += blockDim.x) {   // row exchange, pivot row scaled
+          zd* c = cols + lc * MMAX;
+          if (rank + lc * ECL == k) { tv[lc] = zd(); continue; }
+          if (p != k) { const zd t = c[k]; c[k] = c[p]; c[p] = t; }
+          const zd t = c[k] * inva;
+          c[k] = t;
+          tv[lc] = t;
+        }
+        __syncthreads();
+        for (int e = tid; e < nloc * m; e += blockDim.x) {   // elimination in every other row
+          const int lc = e / m, r = e % m;
+          zd* c = cols + lc * MMAX;
+          if (rank + lc * ECL == k) c[r] = r == k ? zd(1.0) : zd();
+          else if (r != k) c[r] -= lv[r] * tv[lc];
+        }
+        __syncthreads();
+      }
+    }
   }
-  // The reduction to Hessenberg form stays in FP64: the harmonic Ritz pencils of these cycles are
-  // so ill-conditioned (R carries Lanczos and recycle vectors of very different norms) that an
-  // FP32 reduction moves their small eigenvalues by O(1); FP32 QR on the FP64 Hessenberg form
-  // still gives shifts to about 1e-4, which the FP64 refinement needs.
-  hessenberg_block(B, m, ld, v, dsc);
-  // FP32 copy scaled to entries of order one (the eigenvalues scale with it)
+  cl.sync();   // the last elimination broadcast is read before the reflections reuse bc
+  // ---- Householder reduction of M to Hessenberg form: two cluster barriers per column
+  zd* QV = work + W_QV;
+  zd* QF = work + W_QF;
+  for (int j = 0; j + 2 < m; ++j) {
+    const int gj = mcol0 + j, owner = gj % ECL, len = m - j - 1;
+    if (rank == owner && warp == 0 && !failed) {
+      zd* c = cols + (gj / ECL) * MMAX;
+      EclBcast& B = bc[j & 1];
+      double nx2 = 0.0;
+      for (int i = lane; i < len; i += 32) nx2 += abs2(c[j + 1 + i]);
+      nx2 = __shfl_sync(0xffffffffu, warp_sum(nx2), 0);
+      const zd x0 = c[j + 1];
+      const double tail = nx2 - abs2(x0);
+      const bool skip = !(tail > 0.0) || tail <= nx2 * 1e-30;
+      if (!skip) {
+        const double nx = sqrt(nx2), ax0 = cabs_(x0);
+        const zd ph = ax0 > 0.0 ? x0 * (1.0 / ax0) : zd(1.0);
+        const zd alpha = -(ph * nx);
+        const zd fct = zd(2.0 / (tail + abs2(x0 - alpha)));
+        for (int i = lane; i < len; i += 32) {
+          const zd vi = i == 0 ? x0 - alpha : c[j + 1 + i];
+          B.col[i] = vi;
+          QV[i + j * MMAX] = vi;
+        }
+        __syncwarp();
+        for (int i = lane; i < len; i += 32) c[j + 1 + i] = i == 0 ? alpha : zd();   // P x = alpha e_1
+        if (lane == 0) { B.f = fct; QF[j] = fct; }
+      } else if (lane == 0) {
+        B.f = zd();
+        QF[j] = zd();
+      }
+      if (lane == 0) B.flag = skip ? 1 : 0;
+    }
+    cl.sync();
+    if (!failed) {
+      const EclBcast* rb = cl.map_shared_rank(&bc[j & 1], owner);
+      for (int i = tid; i < len; i += blockDim.x) lv[i] = rb->col[i];
+      if (tid == 0) { s_skip = rb->flag; s_f = rb->f; }
+      __syncthreads();
+      if (!s_skip) {
+        const zd fct = s_f;
+        // left: T[j+1:, c] -= f v (v^H T[j+1:, c]) for this CTA's columns c > j (warp per column)
+        for (int lc = warp; lc < nloc; lc += nwarp) {
+          const int cc = rank + lc * ECL - mcol0;
+          if (cc <= j || cc >= m) continue;
+          zd* c = cols + lc * MMAX;
+          zd w = zd();
+          for (int i = lane; i < len; i += 32) w += cmul(lv[i], c[j + 1 + i]);
+          w = warp_sum(w);
+          w = zd(__shfl_sync(0xffffffffu, w.re, 0), __shfl_sync(0xffffffffu, w.im, 0)) * fct;
+          for (int i = lane; i < len; i += 32) c[j + 1 + i] -= lv[i] * w;
+        }
+        __syncthreads();
+        // right, this CTA's part of u = T[:, j+1:] v
+        for (int r = tid; r < m; r += blockDim.x) {
+          zd acc = zd();
+          for (int lc = 0; lc < nloc; ++lc) {
+            const int cc = rank + lc * ECL - mcol0;
+            if (cc > j && cc < m) acc += cols[lc * MMAX + r] * lv[cc - j - 1];
+          }
+          up[j & 1][r] = acc;
+        }
+      }
+    }
+    cl.sync();
+    if (!failed && !s_skip) {
+      for (int r = tid; r < m; r += blockDim.x) {
+        zd acc = zd();
+        for (int q = 0; q < ECL; ++q) acc += cl.map_shared_rank(&up[j & 1][0], q)[r];
+        uvec[r] = acc * s_f;
+      }
+      __syncthreads();
+      for (int e = tid; e < nloc * m; e += blockDim.x) {   // T[:, c] -= u conj(v_c)
+        const int lc = e / m, r = e % m;
+        const int cc = rank + lc * ECL - mcol0;
+        if (cc > j && cc < m) cols[lc * MMAX + r] -= uvec[r] * conjg(lv[cc - j - 1]);
+      }
+      __syncthreads();
+    }
+  }
+  // ---- H and R^{-1} to the work buffer, then CTA 0 alone
+  for (int e = tid; e < nloc * m; e += blockDim.x) {
+    const int lc = e / m, r = e % m, g = rank + lc * ECL;
+    if (g >= mcol0 && g < mcol0 + m) work[W_H + r + (g - mcol0) * MMAX] = cols[lc * MMAX + r];
+    else if (has_R && g >= 2 * m) work[W_RI + r + (g - 2 * m) * MMAX] = cols[lc * MMAX + r];
+  }
+  __threadfence();
+  cl.sync();   // every CTA's writes are visible; no shared memory of another CTA is read after this
+  if (rank != 0) return;
+  if (failed) {
+    if (tid == 0) { st->eig_status = 1; st->kk = 0; *ei.ncand = 0; }
+    return;
+  }
+  const zd* Hg = work + W_H;
+  const int ld = m | 1;
+  zf* H = reinterpret_cast<zf*>(smraw);   // FP32 copy scaled to entries of order one
   double amax = 0.0;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const zd h = B[(e % m) + (e / m) * ld];
-    amax = fmax(amax, fabs(h.re) + fabs(h.im));
-  }
+  for (int e = tid; e < m * m; e += blockDim.x) amax = fmax(amax, cabs1_(Hg[(e % m) + (e / m) * MMAX]));
   for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = amax;
+  if (lane == 0) s_red[warp] = amax;
   __syncthreads();
   amax = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) amax = fmax(amax, s_red[w]);
+  for (int w = 0; w < nwarp; ++w) amax = fmax(amax, s_red[w]);
   if (!(amax > 0.0) || !isfinite(amax)) {
-    if (threadIdx.x == 0) { st->eig_status = 1; st->kk = 0; *ei.ncand = 0; }
+    if (tid == 0) { st->eig_status = 1; st->kk = 0; *ei.ncand = 0; }
     return;
   }
   const double inv = 1.0 / amax;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+  for (int e = tid; e < m * m; e += blockDim.x) {
     const int r = e % m, c = e / m;
-    const zd h = B[r + c * ld];
+    const zd h = Hg[r + c * MMAX];
     H[r + c * ld] = zf((float)(h.re * inv), (float)(h.im * inv));
   }
+  __shared__ int s_ok;
+  if (tid == 0) s_ok = 1;
   __syncthreads();
-  if (threadIdx.x < 32) {
+  if (tid < 32) {
     const bool ok = qr_eigs_warp_f32(H, m, ld, st->dbg);
-    if (threadIdx.x == 0 && !ok) s_ok = 0;
+    if (tid == 0 && !ok) s_ok = 0;
   }
   __syncthreads();
-  if (!s_ok) { if (threadIdx.x == 0) { st->eig_status = 2; st->kk = 0; *ei.ncand = 0; } return; }
-  if (threadIdx.x == 0) {
+  if (!s_ok) { if (tid == 0) { st->eig_status = 2; st->kk = 0; *ei.ncand = 0; } return; }
+  if (tid == 0) {
     // candidates: the k + NCAND_EXTRA finite FP32 eigenvalues closest to the origin; real /
     // complex classification and the final selection wait for the FP64 refinement
     int order[MMAX];
+    float mag[MMAX];
     int cnt = 0;
     for (int i = 0; i < m; ++i) {
       const zf h = H[i + i * ld];
+      mag[i] = abs2(h);
       if (isfinite(h.re) && isfinite(h.im)) order[cnt++] = i;
     }
     for (int a = 1; a < cnt; ++a) {
       const int vv = order[a];
-      const float av = cabs_(H[vv + vv * ld]);
+      const float av = mag[vv];
       int b = a - 1;
-      while (b >= 0 && cabs_(H[order[b] + order[b] * ld]) > av) { order[b + 1] = order[b]; --b; }
+      while (b >= 0 && mag[order[b]] > av) { order[b + 1] = order[b]; --b; }
       order[b + 1] = vv;
     }
     const int nc = min(cnt, f.k + NCAND_EXTRA);
@@ -608,97 +643,203 @@ __global__ void __launch_bounds__(256) k_eig_a(RefreshInfo f, DevState* st, zd* 
   }
 }
 
-__global__ void __launch_bounds__(256) k_eig_b(zd* work, int m, int has_R) {
-  extern __shared__ unsigned char smraw[];
+// One warp: LU with partial pivoting of the upper Hessenberg A = H - sigma I (ld MMAX) in place.
+// Step k exchanges rows k and k+1 when that gives the larger pivot (sw[k]) and stores the
+// multiplier at A[k+1, k]; dinv[k] receives 1 / U[k, k] (a zero pivot is replaced by a tiny one:
+// sigma is then an eigenvalue to working precision, which inverse iteration tolerates).
+__device__ void hess_lu_warp(zd* A, int m, int* sw, zd* dinv, double tiny) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k + 1 < m; ++k) {
+    const bool swp = cabs1_(A[k + 1 + k * MMAX]) > cabs1_(A[k + k * MMAX]);
+    if (swp)
+      for (int c = k + lane; c < m; c += 32) {
+        const zd t = A[k + c * MMAX]; A[k + c * MMAX] = A[k + 1 + c * MMAX]; A[k + 1 + c * MMAX] = t;
+      }
+    __syncwarp();
+    zd piv = A[k + k * MMAX];
+    if (cabs1_(piv) == 0.0) piv = zd(tiny);
+    const zd l = A[k + 1 + k * MMAX] / piv;
+    __syncwarp();
+    for (int c = k + 1 + lane; c < m; c += 32) A[k + 1 + c * MMAX] -= l * A[k + c * MMAX];
+    if (lane == 0) { A[k + k * MMAX] = piv; A[k + 1 + k * MMAX] = l; sw[k] = swp; }
+    __syncwarp();
+  }
+  if (lane == 0 && cabs1_(A[(m - 1) + (m - 1) * MMAX]) == 0.0) A[(m - 1) + (m - 1) * MMAX] = zd(tiny);
+  __syncwarp();
+  for (int k = lane; k < m; k += 32) dinv[k] = zd(1.0) / A[k + k * MMAX];
+  __syncwarp();
+}
+
+// One warp: y <- A^{-1} y for the factorisation of hess_lu_warp.
+__device__ void hess_solve_warp(const zd* A, int m, const int* sw, const zd* dinv, zd* y) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int k = 0; k + 1 < m; ++k) {
+      if (sw[k]) { const zd t = y[k]; y[k] = y[k + 1]; y[k + 1] = t; }
+      y[k + 1] -= A[k + 1 + k * MMAX] * y[k];
+    }
+  __syncwarp();
+  for (int c = m - 1; c >= 0; --c) {   // U x = y, column oriented
+    const zd yc = y[c] * dinv[c];
+    __syncwarp();
+    if (lane == 0) y[c] = yc;
+    for (int r = lane; r < c; r += 32) y[r] -= A[r + c * MMAX] * yc;
+    __syncwarp();
+  }
+}
+
+// One warp: y <- A^{-H} y.  A = P_0 E_0^{-1} ... P_{m-2} E_{m-2}^{-1} U, so A^H w = y is
+// U^H w' = y followed by w = P_0 E_0^H ... P_{m-2} E_{m-2}^H w'.
+__device__ void hess_solve_adj_warp(const zd* A, int m, const int* sw, const zd* dinv, zd* y) {
+  const int lane = threadIdx.x & 31;
+  for (int c = 0; c < m; ++c) {   // U^H lower triangular: column c holds conj(U[c, r]), r > c
+    const zd yc = y[c] * conjg(dinv[c]);
+    __syncwarp();
+    if (lane == 0) y[c] = yc;
+    for (int r = c + 1 + lane; r < m; r += 32) y[r] -= conjg(A[c + r * MMAX]) * yc;
+    __syncwarp();
+  }
+  if (lane == 0)
+    for (int k = m - 2; k >= 0; --k) {
+      y[k] -= conjg(A[k + 1 + k * MMAX]) * y[k + 1];
+      if (sw[k]) { const zd t = y[k]; y[k] = y[k + 1]; y[k + 1] = t; }
+    }
+  __syncwarp();
+}
+
+// One warp: y <- Q y, Q = P_0 P_1 ... P_{m-3} (P_j = I - f_j v_j v_j^H on rows j+1..m-1).
+__device__ void apply_q_warp(const zd* QV, const zd* QF, int m, zd* y) {
+  const int lane = threadIdx.x & 31;
+  for (int j = m - 3; j >= 0; --j) {
+    const zd fj = QF[j];
+    if (fj.re == 0.0 && fj.im == 0.0) continue;
+    const int len = m - j - 1;
+    zd w = zd();
+    for (int i = lane; i < len; i += 32) w += cmul(QV[i + j * MMAX], y[j + 1 + i]);
+    w = warp_sum(w);
+    w = zd(__shfl_sync(0xffffffffu, w.re, 0), __shfl_sync(0xffffffffu, w.im, 0)) * fj;
+    for (int i = lane; i < len; i += 32) y[j + 1 + i] -= QV[i + j * MMAX] * w;
+    __syncwarp();
+  }
+}
+
+// One warp: largest |re| + |im| scaled to 1 (t -> y)
+__device__ void normalise_warp(const zd* t, zd* y, int m) {
+  const int lane = threadIdx.x & 31;
+  double big = 0.0;
+  for (int i = lane; i < m; i += 32) big = fmax(big, cabs1_(t[i]));
+  for (int o = 16; o > 0; o >>= 1) big = fmax(big, __shfl_xor_sync(0xffffffffu, big, o));
+  const double sc = big > 0.0 ? 1.0 / big : 1.0;
+  for (int i = lane; i < m; i += 32) y[i] = t[i] * sc;
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(64) k_eig_h(zd* work, int m, int has_R) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   const EigInts ei = eig_ints(work);
   const int cand = blockIdx.x;
   if (cand >= *ei.ncand) return;
-  const int ld = m | 1;
-  zd* A = reinterpret_cast<zd*>(smraw);   // L - sigma R, then its LU
-  zd* yr = A + m * ld;
-  zd* yl = yr + MMAX;
-  zd* tr = yl + MMAX;
-  zd* tl = tr + MMAX;
-  double* dsc = reinterpret_cast<double*>(tl + MMAX);
-  int* piv = reinterpret_cast<int*>(dsc + 4);
-  __shared__ int s_ok;
-  __shared__ zd s_lam;
-  const zd* Lm = work + W_L;
-  const zd* Rm = work + W_R;
+  zd* A = reinterpret_cast<zd*>(smraw);   // H - sigma I and its LU (ld MMAX)
+  zd* z = A + MMAX * m;
+  zd* zl = z + MMAX;
+  zd* t = zl + MMAX;
+  zd* tl = t + MMAX;
+  zd* dinv = tl + MMAX;
+  __shared__ int sw[MMAX];
+  __shared__ zd s_num, s_den;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  auto Rat = [&](int r, int c) -> zd { return has_R ? Rm[r + c * MMAX] : (r == c ? zd(1.0) : zd()); };
+  const zd* Hg = work + W_H;
+  double hn = 0.0;   // scale of H for the zero-pivot replacement
+  for (int e = lane; e < m * m; e += 32) hn = fmax(hn, cabs1_(Hg[(e % m) + (e / m) * MMAX]));
+  for (int o = 16; o > 0; o >>= 1) hn = fmax(hn, __shfl_xor_sync(0xffffffffu, hn, o));
+  const double tiny = 1e-15 * (hn > 0.0 ? hn : 1.0);
   zd sigma = work[W_LAM + cand];
   for (int e = threadIdx.x; e < m; e += blockDim.x) {
-    const double t = 1.0 + 0.5 * sin(1.7 * e + 0.3);   // fixed start: no zero entries, no structure
-    yr[e] = zd(t, 0.0);
-    yl[e] = zd(t, 0.0);
+    const double v = 1.0 + 0.5 * sin(1.7 * e + 0.3);   // fixed start: no zero entries, no structure
+    z[e] = zd(v, 0.0);
+    zl[e] = zd(v, 0.0);
   }
-  zd lam = sigma;
   for (int pass = 0; pass < 2; ++pass) {
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       const int r = e % m, c = e / m;
-      A[r + c * ld] = Lm[r + c * MMAX] - sigma * Rat(r, c);
+      A[r + c * MMAX] = r == c ? Hg[r + c * MMAX] - sigma : Hg[r + c * MMAX];
     }
-    if (threadIdx.x == 0) s_ok = 1;
     __syncthreads();
-    if (!lu_block(A, m, ld, piv, dsc)) { if (threadIdx.x == 0) s_ok = 0; }
+    if (warp == 0) hess_lu_warp(A, m, sw, dinv, tiny);
     __syncthreads();
-    if (!s_ok) {
-      // sigma is an eigenvalue to working precision: nudge the zero pivots instead
-      if (threadIdx.x == 0) {
-        double an = 0.0;
-        for (int e = 0; e < m * m; ++e) an = fmax(an, cabs_(Lm[(e % m) + (e / m) * MMAX]));
-        for (int k = 0; k < m; ++k)
-          if (cabs_(A[k + k * ld]) == 0.0) A[k + k * ld] = zd(1e-15 * (an > 0 ? an : 1.0));
-      }
-      __syncthreads();
-    }
-    const int steps = pass == 0 ? 4 : 2;
+    const int steps = pass == 0 ? 3 : 2;
     for (int it = 0; it < steps; ++it) {
-      // right-hand sides R y (warp 0) and R^H yl (warp 1)
-      if (warp == 0)
-        for (int r = lane; r < m; r += 32) { zd acc = zd(); for (int c = 0; c < m; ++c) acc += Rat(r, c) * yr[c]; tr[r] = acc; }
-      if (warp == 1)
-        for (int r = lane; r < m; r += 32) { zd acc = zd(); for (int c = 0; c < m; ++c) acc += cmul(Rat(c, r), yl[c]); tl[r] = acc; }
-      __syncthreads();
-      if (warp == 0) lu_solve_warp(A, m, ld, piv, tr);
-      if (warp == 1) lu_solve_adj_warp(A, m, ld, piv, tl);
-      __syncthreads();
-      if (warp < 2) {   // normalise (largest entry 1 in modulus)
-        zd* t = warp == 0 ? tr : tl;
-        zd* y = warp == 0 ? yr : yl;
-        double big = 0.0;
-        for (int i = lane; i < m; i += 32) big = fmax(big, cabs_(t[i]));
-        for (int o = 16; o > 0; o >>= 1) big = fmax(big, __shfl_xor_sync(0xffffffffu, big, o));
-        const double sc = big > 0.0 ? 1.0 / big : 1.0;
-        for (int i = lane; i < m; i += 32) y[i] = t[i] * sc;
+      if (warp == 0) {
+        for (int i = lane; i < m; i += 32) t[i] = z[i];
+        __syncwarp();
+        hess_solve_warp(A, m, sw, dinv, t);
+        normalise_warp(t, z, m);
+      } else {
+        for (int i = lane; i < m; i += 32) tl[i] = zl[i];
+        __syncwarp();
+        hess_solve_adj_warp(A, m, sw, dinv, tl);
+        normalise_warp(tl, zl, m);
       }
-      __syncthreads();
     }
-    // two-sided Rayleigh quotient of the pencil: (yl^H L y) / (yl^H R y)
+    __syncthreads();
+    // Rayleigh quotient of H: zl^H H z / zl^H z
     if (warp == 0) {
       zd num = zd(), den = zd();
       for (int r = lane; r < m; r += 32) {
-        zd ly = zd(), ry = zd();
-        for (int c = 0; c < m; ++c) { ly += Lm[r + c * MMAX] * yr[c]; ry += Rat(r, c) * yr[c]; }
-        num += cmul(yl[r], ly);
-        den += cmul(yl[r], ry);
+        zd hz = zd();
+        for (int c = (r > 0 ? r - 1 : 0); c < m; ++c) hz += Hg[r + c * MMAX] * z[c];
+        num += cmul(zl[r], hz);
+        den += cmul(zl[r], z[r]);
       }
       num = warp_sum(num);
       den = warp_sum(den);
-      if (lane == 0) s_lam = (cabs_(den) > 0.0) ? num / den : sigma;
+      if (lane == 0) { s_num = num; s_den = den; }
     }
     __syncthreads();
-    lam = s_lam;
-    const bool finite = isfinite(lam.re) && isfinite(lam.im);
-    // the FP32 shift was close enough: the quotient did not move
-    if (!finite || cabs_(lam - sigma) <= 1e-6 * cabs_(lam)) break;
+    const zd lam = cabs1_(s_den) > 0.0 ? s_num / s_den : sigma;
+    if (!(isfinite(lam.re) && isfinite(lam.im)) || cabs1_(lam - sigma) <= 1e-10 * cabs1_(lam)) break;
     sigma = lam;
+    __syncthreads();
   }
+  __syncthreads();
+  // pencil vectors: y = Q z (warp 0); yl = R^{-H} Q zl (warp 1)
+  if (warp == 0) {
+    apply_q_warp(work + W_QV, work + W_QF, m, z);
+  } else {
+    apply_q_warp(work + W_QV, work + W_QF, m, zl);
+    if (has_R) {
+      const zd* RI = work + W_RI;
+      for (int r = lane; r < m; r += 32) {
+        zd acc = zd();
+        for (int c = 0; c < m; ++c) acc += cmul(RI[c + r * MMAX], zl[c]);
+        tl[r] = acc;
+      }
+      __syncwarp();
+      for (int r = lane; r < m; r += 32) zl[r] = tl[r];
+    }
+  }
+  __syncthreads();
   zd* Y = work + W_Y + cand * MMAX;
   zd* YL = work + W_YL + cand * MMAX;
-  for (int e = threadIdx.x; e < m; e += blockDim.x) { Y[e] = yr[e]; YL[e] = yl[e]; }
-  if (threadIdx.x == 0) work[W_LAM2 + cand] = lam;
+  for (int e = threadIdx.x; e < m; e += blockDim.x) { Y[e] = z[e]; YL[e] = zl[e]; }
+  // eigenvalue from the pencil itself: yl^H L y / yl^H R y
+  if (warp == 0) {
+    const zd* Lm = work + W_L;
+    const zd* Rm = work + W_R;
+    zd num = zd(), den = zd();
+    for (int r = lane; r < m; r += 32) {
+      zd ly = zd(), ry = zd();
+      for (int c = 0; c < m; ++c) {
+        ly += Lm[r + c * MMAX] * z[c];
+        ry += (has_R ? Rm[r + c * MMAX] : (r == c ? zd(1.0) : zd())) * z[c];
+      }
+      num += cmul(zl[r], ly);
+      den += cmul(zl[r], ry);
+    }
+    num = warp_sum(num);
+    den = warp_sum(den);
+    if (lane == 0) work[W_LAM2 + cand] = cabs1_(den) > 0.0 ? num / den : sigma;
+  }
 }
 
 __global__ void __launch_bounds__(256) k_eig_c(RefreshInfo f, DevState* st, zd* work, zd* Wphi, zd* Wphit, int ldw,
@@ -714,7 +855,7 @@ __global__ void __launch_bounds__(256) k_eig_c(RefreshInfo f, DevState* st, zd* 
         // a candidate that refined to the eigenvalue of an earlier one is dropped
         lam[c] = work[W_LAM2 + c];
         for (int q = 0; q < c; ++q)
-          if (cabs_(lam[c] - work[W_LAM2 + q]) <= 1e-8 * cabs_(lam[c])) { lam[c] = zd(nan(""), 0.0); break; }
+          if (cabs1_(lam[c] - work[W_LAM2 + q]) <= 1e-8 * cabs1_(lam[c])) { lam[c] = zd(nan(""), 0.0); break; }
       }
       units = select_units(lam, *ei.ncand, f.k, f.real_path, ei.sel, ei.pair, &cols);
     }
@@ -791,17 +932,16 @@ __global__ void __launch_bounds__(256) k_eig_c(RefreshInfo f, DevState* st, zd* 
 
 static void launch_eig3(const RefreshInfo& info, DevState* st, zd* work, zd* Wphi, zd* Wphit, int ldw,
                         double* lam_out, int has_R, int m, int raw, cudaStream_t s) {
-  const int ld = m | 1;
-  const size_t smem_a = (size_t)(2 * m * ld + MMAX) * sizeof(zd) + 4 * sizeof(double) + MMAX * sizeof(int);
-  const size_t smem_b = (size_t)(m * ld + 4 * MMAX) * sizeof(zd) + 4 * sizeof(double) + MMAX * sizeof(int);
+  const size_t smem_cl = std::max<size_t>((size_t)ECL_COLS * MMAX * sizeof(zd), (size_t)MMAX * (MMAX + 1) * sizeof(zf));
+  const size_t smem_h = (size_t)(MMAX * m + 5 * MMAX) * sizeof(zd);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_eig_a, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * MMAX * (MMAX + 1) * sizeof(zd) + 8192);
-    cudaFuncSetAttribute(k_eig_b, cudaFuncAttributeMaxDynamicSharedMemorySize, MMAX * (MMAX + 1) * sizeof(zd) + 8192);
+    cudaFuncSetAttribute(k_eig_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl);
+    cudaFuncSetAttribute(k_eig_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((MMAX * MMAX + 5 * MMAX) * sizeof(zd)));
     attr_set = true;
   }
-  k_eig_a<<<1, 256, smem_a, s>>>(info, st, work, has_R, m);
-  k_eig_b<<<KMAX + NCAND_EXTRA, 256, smem_b, s>>>(work, m, has_R);
+  k_eig_cl<<<ECL, 256, smem_cl, s>>>(info, st, work, has_R, m);
+  k_eig_h<<<KMAX + NCAND_EXTRA, 64, smem_h, s>>>(work, m, has_R);
   k_eig_c<<<1, 256, 0, s>>>(info, st, work, Wphi, Wphit, ldw, lam_out, m, raw);
 }
 
@@ -844,11 +984,96 @@ void launch_dense_eig_host(int real_path, int m, const zd* L, const zd* R, int h
 // holding Ct^H C (top-left), Ct^H Ct (top-right), C^H C (bottom-left).  k = *k_dev columns.
 // Output: Nmat = D^{-1} N_p, Mmat = Dt^{-1} M_p (kmax x KMAX row-major), sigma, *p_dev.
 // ------------------------------------------------------------------------------------
+// Rotation of one-sided Jacobi for the column pair (a, b) with squared norms app, aqq and
+// inner product apq = a^H b (|apq|^2 = g2 > 0): cosine cs, sine sn and phase e, so that
+// [a, b] <- [cs a - sn conj(e) b, sn e a + cs b] makes the two columns orthogonal.
+// FP32 version: everything in FP32.
+__device__ __forceinline__ bool jacobi_rot(float app, float aqq, zf apq, float g2, float* cs, float* sn, zf* e) {
+  const float rg = rsqrtf(g2);
+  const float zeta = (aqq - app) * 0.5f * rg, az = fabsf(zeta);
+  const float t = az > 1e18f ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(1.f + zeta * zeta));
+  if (t == 0.f) return false;
+  *cs = rsqrtf(1.f + t * t);
+  *sn = *cs * t;
+  *e = apq * rg;
+  return true;
+}
+// FP64 version: the angle in FP32 (an inexact angle only leaves a little of a^H b for the next
+// sweep), cosine, sine and phase in FP64 so that the rotation is unitary to FP64 rounding.
+__device__ __forceinline__ bool jacobi_rot(double app, double aqq, zd apq, double g2, double* cs, double* sn, zd* e) {
+  const double zq = (aqq - app) / (2.0 * sqrt(g2));
+  const float zeta = (float)zq, az = fabsf(zeta);
+  const float tf = az > 1e18f ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(1.f + zeta * zeta));
+  if (tf == 0.f) return false;
+  const double t = (double)tf;
+  *cs = rsqrt(1.0 + t * t);
+  *sn = *cs * t;
+  *e = apq * rsqrt(g2);
+  return true;
+}
+
+// Block-wide one-sided Jacobi sweeps on the k x k column-major A (V accumulates the right
+// rotations), round-robin (circle) pair ordering, warp w handles pairs w, w + 8, ...  A pair is
+// converged when |a^H b|^2 <= tol2 |a|^2 |b|^2.  Returns the sweeps run.
+template <class C, class Rl>
+__device__ int jacobi_sweeps(C* A, C* V, int k, int max_sweeps, Rl tol2, int* s_rot) {
+  const int kk = (k + 1) & ~1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) *s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < kk - 1; ++round) {
+      for (int pr = warp; pr < kk / 2; pr += nw) {
+        // circle method: position 0 fixed, positions 1..kk-1 rotate by `round`
+        int a = pr == 0 ? 0 : 1 + (pr - 1 + round) % (kk - 1);
+        const int pb = kk - 1 - pr;
+        int b = 1 + (pb - 1 + round) % (kk - 1);
+        if (a > b) { const int t = a; a = b; b = t; }
+        if (b >= k || a == b) continue;
+        Rl app = 0, aqq = 0;
+        C apq = C(Rl(0));
+        for (int r = lane; r < k; r += 32) {
+          const C x = A[r + a * k], y = A[r + b * k];
+          app += abs2(x); aqq += abs2(y); apq += cmul(x, y);
+        }
+        app = warp_sum(app); aqq = warp_sum(aqq); apq = warp_sum(apq);
+        app = __shfl_sync(0xffffffffu, app, 0); aqq = __shfl_sync(0xffffffffu, aqq, 0);
+        apq = C(__shfl_sync(0xffffffffu, apq.re, 0), __shfl_sync(0xffffffffu, apq.im, 0));
+        const Rl g2 = abs2(apq);
+        if (g2 <= tol2 * (app * aqq) || g2 == Rl(0)) continue;
+        Rl cs, sn;
+        C e;
+        if (!jacobi_rot(app, aqq, apq, g2, &cs, &sn, &e)) continue;
+        if (lane == 0) *s_rot = 1;
+        __syncwarp();   // all lanes' reads of columns a, b precede the writes
+        for (int r = lane; r < k; r += 32) {
+          const C x = A[r + a * k], y = A[r + b * k];
+          A[r + a * k] = cs * x - sn * (conjg(e) * y);
+          A[r + b * k] = sn * (e * x) + cs * y;
+          const C vx = V[r + a * k], vy = V[r + b * k];
+          V[r + a * k] = cs * vx - sn * (conjg(e) * vy);
+          V[r + b * k] = sn * (e * vx) + cs * vy;
+        }
+      }
+      __syncthreads();
+    }
+    if (!*s_rot) break;
+    __syncthreads();
+  }
+  __syncthreads();
+  return sweep;
+}
+
 __global__ void __launch_bounds__(256) k_svd(int real_path, const int* k_dev, int kmax, const zd* S2, double svd_tol,
                                              zd* Nmat, zd* Mmat, double* sigma, int* p_dev, double* Dc_dev,
                                              int* status) {
-  __shared__ zd A[KMAX * KMAX];   // column-major k x k: A = S_norm, rotated to M Sigma
-  __shared__ zd V[KMAX * KMAX];   // accumulated right rotations (N)
+  extern __shared__ unsigned char smraw[];
+  zd* A = reinterpret_cast<zd*>(smraw);   // column-major k x k: A = S_norm, rotated to M Sigma
+  zd* V = A + KMAX * KMAX;                // accumulated right rotations (N)
+  zd* A0 = V + KMAX * KMAX;               // S_norm (kept for the FP64 restart)
+  zf* Af = reinterpret_cast<zf*>(A0 + KMAX * KMAX);
+  zf* Vf = Af + KMAX * KMAX;
   __shared__ double dn[KMAX], dtn[KMAX], sg[KMAX];
   __shared__ int ord[KMAX], s_rot, s_p;
   const int k = min(*k_dev, kmax);
@@ -867,56 +1092,47 @@ __global__ void __launch_bounds__(256) k_svd(int real_path, const int* k_dev, in
     const double sr = dtn[r] > 0.0 ? 1.0 / dtn[r] : 0.0, scc = dn[c] > 0.0 ? 1.0 / dn[c] : 0.0;
     zd a = S2[r * ld2 + c] * (sr * scc);
     if (real_path) a.im = 0.0;
-    A[r + c * k] = a;
-    V[r + c * k] = r == c ? zd(1.0) : zd();
+    A0[r + c * k] = a;
+    Af[r + c * k] = zf((float)a.re, (float)a.im);   // entries <= 1 after the unit-norm scaling
+    Vf[r + c * k] = r == c ? zf(1.f) : zf(0.f);
   }
   __syncthreads();
-  // one-sided Jacobi, round-robin pairs (kk even), warp w handles pair w
-  const int kk = (k + 1) & ~1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    if (threadIdx.x == 0) s_rot = 0;
-    __syncthreads();
-    for (int round = 0; round < kk - 1; ++round) {
-      for (int pr = warp; pr < kk / 2; pr += nw) {
-        // circle method: position 0 fixed, positions 1..kk-1 rotate by `round`
-        int a = pr == 0 ? 0 : 1 + (pr - 1 + round) % (kk - 1);
-        const int pb = kk - 1 - pr;
-        int b = 1 + (pb - 1 + round) % (kk - 1);
-        if (a > b) { const int t = a; a = b; b = t; }
-        if (b >= k || a == b) continue;
-        double app = 0.0, aqq = 0.0;
-        zd apq = zd();
-        for (int r = lane; r < k; r += 32) {
-          const zd x = A[r + a * k], y = A[r + b * k];
-          app += abs2(x); aqq += abs2(y); apq += cmul(x, y);
-        }
-        app = warp_sum(app); aqq = warp_sum(aqq); apq = warp_sum(apq);
-        app = __shfl_sync(0xffffffffu, app, 0); aqq = __shfl_sync(0xffffffffu, aqq, 0);
-        apq = zd(__shfl_sync(0xffffffffu, apq.re, 0), __shfl_sync(0xffffffffu, apq.im, 0));
-        const double g = cabs_(apq);
-        if (g <= 1e-15 * sqrt(app * aqq) || g == 0.0) continue;
-        if (lane == 0) s_rot = 1;
-        // rotate columns a, b so that they become orthogonal
-        const double zeta = (aqq - app) / (2.0 * g);
-        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-        const zd e = apq * (1.0 / g);   // phase of a^H b
-        __syncwarp();                    // all lanes' reads of columns a, b precede the writes
-        for (int r = lane; r < k; r += 32) {
-          const zd x = A[r + a * k], y = A[r + b * k];
-          A[r + a * k] = cs * x - sn * (conjg(e) * y);
-          A[r + b * k] = sn * (e * x) + cs * y;
-          const zd vx = V[r + a * k], vy = V[r + b * k];
-          V[r + a * k] = cs * vx - sn * (conjg(e) * vy);
-          V[r + b * k] = sn * (e * vx) + cs * vy;
-        }
-      }
-      __syncthreads();
+  // FP32 sweeps to about FP32 orthogonality, then A <- A0 Vf and V <- Vf in FP64 and FP64
+  // sweeps from there (one or two: the convergence of cyclic Jacobi is quadratic).
+  jacobi_sweeps<zf, float>(Af, Vf, k, 30, (8e-8f * k) * (8e-8f * k), &s_rot);
+  // Vf is unitary only to FP32 rounding: two Newton-Schulz steps in FP64, V <- V (3 I - V^H V) / 2,
+  // make it unitary to FP64 rounding (the error squares at each step); G = V^H V goes in A.
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x)
+    V[e] = zd((double)Vf[e].re, (double)Vf[e].im);
+  __syncthreads();
+  for (int ns = 0; ns < 2; ++ns) {
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+      const int r = e % k, c = e / k;
+      zd acc = zd();
+      for (int q = 0; q < k; ++q) acc += cmul(V[q + r * k], V[q + c * k]);
+      A[r + c * k] = acc;
     }
-    if (!s_rot) break;
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {   // A0's spare copy: Af/Vf area
+      const int r = e % k, c = e / k;
+      zd acc = zd();
+      for (int q = 0; q < k; ++q) acc += V[r + q * k] * ((q == c ? zd(3.0) : zd()) - A[q + c * k]);
+      reinterpret_cast<zd*>(Af)[r + c * k] = acc * 0.5;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) V[e] = reinterpret_cast<zd*>(Af)[e];
     __syncthreads();
   }
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {   // A = A0 V
+    const int r = e % k, c = e / k;
+    zd acc = zd();
+    for (int q = 0; q < k; ++q) acc += A0[r + q * k] * V[q + c * k];
+    A[r + c * k] = acc;
+  }
+  __syncthreads();
+  // converged pair: |a^H b| at the rounding floor of a k-term FP64 inner product (about
+  // k eps ||a|| ||b||); a threshold below it never lets the sweeps stop
+  jacobi_sweeps<zd, double>(A, V, k, 10, (4e-16 * k) * (4e-16 * k), &s_rot);
   // singular values, order
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
     double s = 0.0;
@@ -963,7 +1179,13 @@ void launch_dense_svd(int real_path, const int* k_dev, int kmax, const zd* S, co
                       double svd_tol, zd* Nmat, zd* Mmat, double* sigma, int* p_dev, double* Dc_dev, int* status_dev,
                       cudaStream_t s) {
   (void)nC; (void)nCt;
-  k_svd<<<1, 256, 0, s>>>(real_path, k_dev, kmax, S, svd_tol, Nmat, Mmat, sigma, p_dev, Dc_dev, status_dev);
+  const size_t smem = 3 * KMAX * KMAX * sizeof(zd) + 2 * KMAX * KMAX * sizeof(zf);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  k_svd<<<1, 256, smem, s>>>(real_path, k_dev, kmax, S, svd_tol, Nmat, Mmat, sigma, p_dev, Dc_dev, status_dev);
 }
 
 template void launch_dense_refresh<double>(const RefreshInfo&, DevState*, const double*, zd*, zd*, zd*, int, double*,
