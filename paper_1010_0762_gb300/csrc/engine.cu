@@ -161,6 +161,8 @@ struct Solver : SolverBase {
   // concurrently with the next cycle's iterations.  The ring holds two cycles for that.
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_cycle = nullptr, ev_ref = nullptr;
+  cudaStream_t gs = nullptr;                        // graph capture / launch stream
+  cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr;
   bool ref_pending = false;
   void* gpart = nullptr;        // Gram partials of the refresh (part belongs to the iteration)
   int64_t* launches;
@@ -208,6 +210,9 @@ struct Solver : SolverBase {
     RB_CUDA(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi_prio));
     RB_CUDA(cudaEventCreateWithFlags(&ev_cycle, cudaEventDisableTiming));
     RB_CUDA(cudaEventCreateWithFlags(&ev_ref, cudaEventDisableTiming));
+    RB_CUDA(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+    RB_CUDA(cudaEventCreateWithFlags(&ev_g0, cudaEventDisableTiming));
+    RB_CUDA(cudaEventCreateWithFlags(&ev_g1, cudaEventDisableTiming));
     const int sms = num_sms();
     grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + NTHREADS - 1) / NTHREADS, (int64_t)sms * 8));
     gram_grid = 2 * sms;
@@ -244,6 +249,8 @@ struct Solver : SolverBase {
   ~Solver() override {
     cudaStreamSynchronize(s);
     if (s2) cudaStreamSynchronize(s2);
+    if (gs) cudaStreamSynchronize(gs);
+    drop_graph();
     T* bufs[] = {ring, ringt, p[0], p[1], pt[0], pt[1], z, zt, U, Ut, C, Ct,
                  Uc[0], Uc[1], Utc[0], Utc[1], Cc[0], Cc[1], Ctc[0], Ctc[1]};
     for (T* b : bufs) cudaFree(b);
@@ -257,6 +264,9 @@ struct Solver : SolverBase {
     if (ev_cycle) cudaEventDestroy(ev_cycle);
     if (ev_ref) cudaEventDestroy(ev_ref);
     if (s2) cudaStreamDestroy(s2);
+    if (ev_g0) cudaEventDestroy(ev_g0);
+    if (ev_g1) cudaEventDestroy(ev_g1);
+    if (gs) cudaStreamDestroy(gs);
   }
 
   void free_op() {
@@ -279,11 +289,15 @@ struct Solver : SolverBase {
 
   // Fetch the host view of the device state (one sync, after the refresh in flight).
   void fetch() {
+    fetch_async();
+    RB_CUDA(cudaStreamSynchronize(s));
+    prof->harvest();
+  }
+  // the copy of fetch() without the sync (a batch syncs once for all its requests)
+  void fetch_async() {
     RB_CUDA(cudaGetLastError());   // a failed launch must not leave the host loop waiting
     join_refresh();
     RB_CUDA(cudaMemcpyAsync(hv, st, sizeof(HostView), cudaMemcpyDeviceToHost, s));
-    RB_CUDA(cudaStreamSynchronize(s));
-    prof->harvest();
   }
 
   template <class F>
@@ -450,128 +464,208 @@ struct Solver : SolverBase {
     double relres = 0, relres_dual = 0, true_relres = 0, true_relres_dual = 0;
   };
 
-  PairOut solve(const T* b, const T* bt, T* x, T* xt, double tol, int max_itn, uint64_t seed) {
-    const int kU_in = prm.recycle ? kU : 0;
+  // ---- one pair solve as a resumable state machine: begin(), then per cycle launch_cycle()
+  // (single) or a batched launch, fetch() and after_cycle(), then end().  solve() and the
+  // batched runner share every decision.
+  struct Run {
+    const T *b = nullptr, *bt = nullptr;
+    T *x = nullptr, *xt = nullptr;
+    double tol = 0;
+    int max_itn = 0;
+    uint64_t seed = 0;
+    int kU_in = 0, kt = 0;
+    VecArgs<T> v{};
+    PairOut out;
+    bool recycle = false, broken = false;
+    int j = 0, kp = 0, last_refresh = 0, good_refresh = 0, good_p = 0;
+    int done = 0, iter = 0, iter_before = 0, best_at = 0, guard_limit = 0x7fffffff;
+    double best_r = 0;
+  } run;
+
+  // CUDA graph of one cycle (todo iterations x 3 phases), captured on first use and replayed
+  // while its launch parameters stay the same
+  cudaGraphExec_t cyc_exec = nullptr;
+  int cyc_todo = -1, cyc_kt = -1;
+  VecArgs<T> cyc_v{};
+  OpArgs<V> cyc_op{};
+  bool use_graphs = true;
+
+  void drop_graph() {
+    if (cyc_exec) cudaGraphExecDestroy(cyc_exec);
+    cyc_exec = nullptr;
+    cyc_todo = -1;
+  }
+
+  void begin(const T* b, const T* bt, T* x, T* xt, double tol, int max_itn, uint64_t seed) {
+    Run& R_ = run;
+    R_ = Run{};
+    R_.b = b; R_.bt = bt; R_.x = x; R_.xt = xt; R_.tol = tol; R_.max_itn = max_itn; R_.seed = seed;
+    R_.kU_in = prm.recycle ? kU : 0;
     if (pending_start) system_start();
-    int kt = kt_for(kc);
+    R_.kt = kt_for(kc);
     set_field(&DevState::tol, tol);
     set_field(&DevState::max_itn, max_itn);
     set_field(&DevState::done, 0);
     set_field(&DevState::eig_status, 0);
     set_field(&DevState::pcyc, 0);
-    VecArgs<T> v = vec(b, bt, x, xt, C, Ct, U, Ut);
+    R_.v = vec(b, bt, x, xt, C, Ct, U, Ut);
     const int pi = prof->begin(7, s);
-    launch_init<V, T>(op, v, st, part, kt, grid, 0, s);
+    launch_init<V, T>(op, R_.v, st, part, R_.kt, grid, 0, s);
     prof->end(pi, 2, s);
     count(2);
     fetch();
     if (hv->restart) {
       // Algorithm 2 step 3: xt_{-1} <- random (Philox4x32-10), recompute the dual start
       launch_philox<T>(xt, n, seed, s);
-      launch_init<V, T>(op, v, st, part, kt, grid, 1, s);
+      launch_init<V, T>(op, R_.v, st, part, R_.kt, grid, 1, s);
       count(3);
       fetch();
     }
-    PairOut out;
-    const bool recycle = prm.recycle != 0;
-    int j = 0, kp = 0, last_refresh = 0, good_refresh = 0, good_p = 0;
-    bool broken = false;
-    int done = hv->done;
-    int iter = 0, iter_before = 0;
-    double best_r = hv->rnorm;
-    int best_at = 0;
+    R_.recycle = prm.recycle != 0;
+    R_.done = hv->done;
+    R_.best_r = hv->rnorm;
     // stagnation guard (not in the paper): see rbicg_params.guard
-    int guard_limit = (kc > 0 && prm.guard > 0.0 && last_plain_iters > 0)
-                          ? (int)std::min<double>(2e9, prm.guard * last_plain_iters) : 0x7fffffff;
-    if (guard_limit != 0x7fffffff) {
+    R_.guard_limit = (kc > 0 && prm.guard > 0.0 && last_plain_iters > 0)
+                         ? (int)std::min<double>(2e9, prm.guard * last_plain_iters) : 0x7fffffff;
+    if (R_.guard_limit != 0x7fffffff) {
       if (!x_save) { x_save = dmalloc<T>(n); xt_save = dmalloc<T>(n); }
       RB_CUDA(cudaMemcpyAsync(x_save, x, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
       RB_CUDA(cudaMemcpyAsync(xt_save, xt, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
     }
-    while (!done) {
-      const int todo = std::min(prm.s, max_itn - iter_before - iter);
-      for (int t = 0; t < todo; ++t) {
-        int pp = prof->begin(0, s);
-        launch_phase1<V, T>(op, v, st, part, kt, grid, s);
-        prof->end(pp, 1, s);
-        pp = prof->begin(1, s);
-        launch_phase2<V, T>(op, v, st, part, kt, grid, s);
-        prof->end(pp, 1, s);
-        pp = prof->begin(2, s);
-        launch_phase3<V, T>(op, v, st, part, grid, s);
-        prof->end(pp, 1, s);
-      }
-      count(3 * todo);
-      fetch();
-      // status of the refresh launched after the previous cycle
-      if (last_refresh > 0 && !broken) {
-        if (hv->eig_status != 0) broken = true;
-        else { good_refresh = last_refresh; good_p = hv->pcyc; kp = hv->pcyc; }
-      }
-      if (!hv->done && hv->iter <= iter)
-        throw Err{RBICG_ERR_CUDA, "iteration made no progress (device state not advancing)"};
-      iter = hv->iter;
-      done = hv->done;
-      if (!done && iter_before + iter >= max_itn) done = DONE_MAXIT;
-      if (!done && diverge > 0.0 && hv->rnorm > diverge * (hv->bnorm > 0 ? hv->bnorm : 1.0)) done = DONE_MAXIT;
-      if (hv->rnorm < best_r) { best_r = hv->rnorm; best_at = iter_before + iter; }
-      if (!done && stall_window > 0 && iter_before + iter - best_at > stall_window) done = DONE_MAXIT;
-      const bool bad_end = done == DONE_BREAK_RHO || done == DONE_BREAK_PQ || done == DONE_NONFINITE;
-      const bool stalled = !done && iter >= guard_limit;
-      if (guard_limit != 0x7fffffff && (stalled || bad_end)) {
-        join_refresh();   // the restart rewrites ring slots and histories a refresh may read
-        if (done == DONE_NONFINITE) {
-          // the iterate may hold non-finite values: restart from the saved initial guess
-          RB_CUDA(cudaMemcpyAsync(x, x_save, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
-          RB_CUDA(cudaMemcpyAsync(xt, xt_save, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
-        }
+  }
 
-        // step 7 on the current iterate, then restart from it without the recycle space
-        if (done != DONE_NONFINITE) {
-          launch_finish_a<T>(v, st, kt, grid, s);
-          count(1);
-        }
-        iter_before += iter;
-        kc = 0;
-        set_field(&DevState::kc, 0);
-        out.fallback = 1;
-        guard_limit = 0x7fffffff;
-        const int pi2 = prof->begin(7, s);
-        launch_init<V, T>(op, v, st, part, 0, grid, 0, s);
-        prof->end(pi2, 2, s);
-        count(2);
-        fetch();
-        if (hv->restart) {
-          launch_philox<T>(xt, n, seed, s);
-          launch_init<V, T>(op, v, st, part, 0, grid, 1, s);
-          count(3);
-          fetch();
-        }
-        kt = 0;
-        j = 0; kp = 0; last_refresh = 0; good_refresh = 0; good_p = 0; broken = false;
-        iter = 0;
-        done = hv->done;
-        continue;
-      }
-      if (recycle && !broken && iter == (j + 1) * prm.s) {
-        ++j;
-        refresh(j, kp, nullptr);
-        last_refresh = j;
-      }
+  // iterations of the next cycle
+  int cycle_len() const { return std::min(prm.s, run.max_itn - run.iter_before - run.iter); }
+
+  void launch_phases(int todo) {
+    for (int t = 0; t < todo; ++t) {
+      int pp = prof->begin(0, s);
+      launch_phase1<V, T>(op, run.v, st, part, run.kt, grid, s);
+      prof->end(pp, 1, s);
+      pp = prof->begin(1, s);
+      launch_phase2<V, T>(op, run.v, st, part, run.kt, grid, s);
+      prof->end(pp, 1, s);
+      pp = prof->begin(2, s);
+      launch_phase3<V, T>(op, run.v, st, part, grid, s);
+      prof->end(pp, 1, s);
     }
+  }
+
+  // The graph is captured on, and launched into, the private stream gs (the caller's stream may
+  // be the legacy default stream, which cannot be captured), ordered after and before the work
+  // of s by two events.  If capture or instantiation fails, the cycle runs as plain launches.
+  void launch_cycle(int todo) {
+    count(3 * todo);
+    if (!use_graphs || prof->on || todo <= 0) { launch_phases(todo); return; }
+    if (!cyc_exec || cyc_todo != todo || cyc_kt != run.kt || memcmp(&cyc_v, &run.v, sizeof(cyc_v)) != 0 ||
+        memcmp(&cyc_op, &op, sizeof(cyc_op)) != 0) {
+      drop_graph();
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        use_graphs = false;
+        launch_phases(todo);
+        return;
+      }
+      const cudaStream_t keep = s;
+      s = gs;
+      launch_phases(todo);
+      s = keep;
+      const cudaError_t ec = cudaStreamEndCapture(gs, &g);
+      const cudaError_t ei = ec == cudaSuccess ? cudaGraphInstantiate(&cyc_exec, g, 0) : ec;
+      if (g) cudaGraphDestroy(g);
+      if (ei != cudaSuccess) {
+        cudaGetLastError();
+        cyc_exec = nullptr;
+        use_graphs = false;
+        launch_phases(todo);
+        return;
+      }
+      cyc_todo = todo; cyc_kt = run.kt; cyc_v = run.v; cyc_op = op;
+    }
+    RB_CUDA(cudaEventRecord(ev_g0, s));
+    RB_CUDA(cudaStreamWaitEvent(gs, ev_g0, 0));
+    RB_CUDA(cudaGraphLaunch(cyc_exec, gs));
+    RB_CUDA(cudaEventRecord(ev_g1, gs));
+    RB_CUDA(cudaStreamWaitEvent(s, ev_g1, 0));
+  }
+
+  // after a cycle and fetch(): statuses, stopping rules, guard, next refresh
+  void after_cycle() {
+    Run& R_ = run;
+    // status of the refresh launched after the previous cycle
+    if (R_.last_refresh > 0 && !R_.broken) {
+      if (hv->eig_status != 0) R_.broken = true;
+      else { R_.good_refresh = R_.last_refresh; R_.good_p = hv->pcyc; R_.kp = hv->pcyc; }
+    }
+    if (!hv->done && hv->iter <= R_.iter)
+      throw Err{RBICG_ERR_CUDA, "iteration made no progress (device state not advancing)"};
+    R_.iter = hv->iter;
+    R_.done = hv->done;
+    const int total = R_.iter_before + R_.iter;
+    if (!R_.done && total >= R_.max_itn) R_.done = DONE_MAXIT;
+    if (!R_.done && diverge > 0.0 && hv->rnorm > diverge * (hv->bnorm > 0 ? hv->bnorm : 1.0)) R_.done = DONE_MAXIT;
+    if (hv->rnorm < R_.best_r) { R_.best_r = hv->rnorm; R_.best_at = total; }
+    if (!R_.done && stall_window > 0 && total - R_.best_at > stall_window) R_.done = DONE_MAXIT;
+    const bool bad_end = R_.done == DONE_BREAK_RHO || R_.done == DONE_BREAK_PQ || R_.done == DONE_NONFINITE;
+    const bool stalled = !R_.done && R_.iter >= R_.guard_limit;
+    if (R_.guard_limit != 0x7fffffff && (stalled || bad_end)) {
+      join_refresh();   // the restart rewrites ring slots and histories a refresh may read
+      if (R_.done == DONE_NONFINITE) {
+        // the iterate may hold non-finite values: restart from the saved initial guess
+        RB_CUDA(cudaMemcpyAsync(R_.x, x_save, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+        RB_CUDA(cudaMemcpyAsync(R_.xt, xt_save, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+      } else {
+        // step 7 on the current iterate, then restart from it without the recycle space
+        launch_finish_a<T>(R_.v, st, R_.kt, grid, s);
+        count(1);
+      }
+      R_.iter_before += R_.iter;
+      kc = 0;
+      set_field(&DevState::kc, 0);
+      set_field(&DevState::max_itn, std::max(1, R_.max_itn - R_.iter_before));
+      R_.out.fallback = 1;
+      R_.guard_limit = 0x7fffffff;
+      const int pi2 = prof->begin(7, s);
+      launch_init<V, T>(op, R_.v, st, part, 0, grid, 0, s);
+      prof->end(pi2, 2, s);
+      count(2);
+      fetch();
+      if (hv->restart) {
+        launch_philox<T>(R_.xt, n, R_.seed, s);
+        launch_init<V, T>(op, R_.v, st, part, 0, grid, 1, s);
+        count(3);
+        fetch();
+      }
+      R_.kt = 0;
+      R_.j = 0; R_.kp = 0; R_.last_refresh = 0; R_.good_refresh = 0; R_.good_p = 0; R_.broken = false;
+      R_.iter = 0;
+      R_.done = hv->done;
+      return;
+    }
+    if (R_.recycle && !R_.broken && R_.iter == (R_.j + 1) * prm.s) {
+      ++R_.j;
+      refresh(R_.j, R_.kp, nullptr);
+      R_.last_refresh = R_.j;
+    }
+  }
+
+  PairOut end() {
+    Run& R_ = run;
+    PairOut out = R_.out;
     const int pf = prof->begin(7, s);
-    launch_finish<V, T>(op, v, st, part, kt, grid, s);
+    launch_finish<V, T>(op, R_.v, st, part, R_.kt, grid, s);
     prof->end(pf, 2, s);
     count(2);
     fetch();
-    if (last_refresh > good_refresh && !broken) {
-      if (hv->eig_status != 0) broken = true;
-      else { good_refresh = last_refresh; good_p = hv->pcyc; }
+    if (R_.last_refresh > R_.good_refresh && !R_.broken) {
+      if (hv->eig_status != 0) R_.broken = true;
+      else { R_.good_refresh = R_.last_refresh; R_.good_p = hv->pcyc; }
     }
-    out.iters = iter_before + hv->iter;
-    out.cycles = good_refresh;
+    out.iters = R_.iter_before + hv->iter;
+    out.cycles = R_.good_refresh;
     out.recycle_dim = out.fallback ? 0 : kc;
-    if (out.fallback || kU_in == 0) last_plain_iters = hv->iter;
+    if (out.fallback || R_.kU_in == 0) last_plain_iters = hv->iter;
     const double nb = hv->bnorm > 0 ? hv->bnorm : 1.0, nbt = hv->btnorm > 0 ? hv->btnorm : 1.0;
     out.relres = hv->rnorm / nb;
     out.relres_dual = hv->rtnorm / nbt;
@@ -585,17 +679,17 @@ struct Solver : SolverBase {
       default: out.status = RBICG_NOT_CONVERGED; break;
     }
     if (hv->iter == 0 && hv->done == DONE_CONVERGED) out.status = RBICG_OK;
-    // recycle space for the next system (Section 4: the final U_j; Section 6.2: keep the
-    // previous space if no cycle completed)
     if (debug_on())
       fprintf(stderr, "[rbicg] solve n=%lld T=%zu kc=%d iters=%d done=%d relres=%.3e/%.3e true=%.3e/%.3e cycles=%d p=%d\n",
               (long long)n, sizeof(T), kc, hv->iter, hv->done, out.relres, out.relres_dual, out.true_relres,
-              out.true_relres_dual, good_refresh, good_p);
-    if (recycle) {
-      if (good_refresh > 0) {
-        const int jc = good_refresh & 1;
+              out.true_relres_dual, R_.good_refresh, R_.good_p);
+    // recycle space for the next system (Section 4: the final U_j; Section 6.2: keep the
+    // previous space if no cycle completed)
+    if (R_.recycle) {
+      if (R_.good_refresh > 0) {
+        const int jc = R_.good_refresh & 1;
         std::swap(U, Uc[jc]); std::swap(Ut, Utc[jc]); std::swap(C, Cc[jc]); std::swap(Ct, Ctc[jc]);
-        kU = good_p;
+        kU = R_.good_p;
       } else if (kc > 0) {
         kU = kc;
       } else {
@@ -603,8 +697,18 @@ struct Solver : SolverBase {
       }
     }
     pending_start = 1;   // the next solve re-derives C, Ct for the (possibly new) operator
-    if (kU_in > 0 && kc == 0 && out.status == RBICG_OK) out.status = RBICG_RECYCLE_EMPTY;
+    if (R_.kU_in > 0 && kc == 0 && out.status == RBICG_OK) out.status = RBICG_RECYCLE_EMPTY;
     return out;
+  }
+
+  PairOut solve(const T* b, const T* bt, T* x, T* xt, double tol, int max_itn, uint64_t seed) {
+    begin(b, bt, x, xt, tol, max_itn, seed);
+    while (!run.done) {
+      launch_cycle(cycle_len());
+      fetch();
+      after_cycle();
+    }
+    return end();
   }
 
   void launch_real_to_zd(const double* a, zd* b, int64_t m, cudaStream_t st_) { launch_convert_rz(a, b, m, st_); }
@@ -666,6 +770,8 @@ struct Impl {
   virtual void reset() = 0;
   virtual void export_recycle(void* U, void* Ut, int* p) = 0;
   virtual void import_recycle(const void* U, const void* Ut, int p) = 0;
+  // FP64 handles: the solver that a batch drives directly, and the kind of its (V, T)
+  virtual void* batch_solver(int* kind) = 0;
 };
 
 template <class V, class T>
@@ -827,6 +933,12 @@ struct ImplT : Impl {
   }
 
   bool fp64_only = false;   // FP32_REFINED handle that fell back to FP64 (until rbicg_reset)
+
+  void* batch_solver(int* kind) override {
+    if (lo) return nullptr;   // FP32-refined handles are solved one by one
+    *kind = traits<T>::cx ? (traits<V>::cx ? 2 : 1) : 0;
+    return hi.get();
+  }
 
   rbicg_result solve_fp64(const T* b, const T* bt, T* x, T* xt, int iters_before, int steps_before) {
     rbicg_result res{};
@@ -1050,17 +1162,167 @@ extern "C" rbicg_status rbicg_solve_pair(rbicg_handle h, const rbicg_csr* A, con
   })
 }
 
+template <class P>
+static rbicg_result to_result(const P& o) {
+  rbicg_result r{};
+  r.iters = o.iters; r.cycles = o.cycles; r.recycle_dim = o.recycle_dim; r.refine_steps = 0;
+  r.relres = o.relres; r.relres_dual = o.relres_dual;
+  r.true_relres = o.true_relres; r.true_relres_dual = o.true_relres_dual;
+  r.status = o.status; r.fallback = o.fallback;
+  return r;
+}
+
+// A batch of FP64 pairs driven together: every iteration phase is ONE launch over all active
+// requests (request r owns its usual grid's blocks, so its arithmetic and reduction order are
+// exactly those of a solo solve); each request keeps its own stopping test, guard and cycle
+// refreshes (on its own refresh stream); finished requests leave the batch at cycle boundaries.
+template <class V, class T>
+static void run_batch(const std::vector<Solver<V, T>*>& sv, const std::vector<rbicg_handle>& hs,
+                      const void* const* bs, const void* const* bts, void* const* xs, void* const* xts,
+                      rbicg_result* res, cudaStream_t s0) {
+  const int nb = (int)sv.size();
+  std::vector<cudaStream_t> saved(nb);
+  for (int r = 0; r < nb; ++r) {
+    saved[r] = sv[r]->s;
+    sv[r]->s = s0;
+  }
+  struct Restore {
+    const std::vector<Solver<V, T>*>& sv;
+    std::vector<cudaStream_t>& saved;
+    ~Restore() {
+      for (size_t r = 0; r < sv.size(); ++r) sv[r]->s = saved[r];
+    }
+  } restore{sv, saved};
+  BatchArgs<V, T>* dba = dmalloc<BatchArgs<V, T>>(1);
+  std::unique_ptr<BatchArgs<V, T>> hb(new BatchArgs<V, T>());
+  struct Free {
+    void* p;
+    ~Free() { cudaFree(p); }
+  } free_dba{dba};
+  for (int r = 0; r < nb; ++r) {
+    const rbicg_params& q = hs[r]->prm;
+    sv[r]->begin(reinterpret_cast<const T*>(bs[r]), reinterpret_cast<const T*>(bts[r]), reinterpret_cast<T*>(xs[r]),
+                 reinterpret_cast<T*>(xts[r]), q.tol, q.max_itn, q.seed);
+  }
+  std::vector<int> active;
+  for (int r = 0; r < nb; ++r)
+    if (!sv[r]->run.done) active.push_back(r);
+  while (!active.empty()) {
+    int kt = 0, todo = 0, blocks = 0;
+    hb->nreq = (int)active.size();
+    hb->start[0] = 0;
+    for (size_t i = 0; i < active.size(); ++i) {
+      Solver<V, T>* q = sv[active[i]];
+      hb->op[i] = q->op;
+      hb->v[i] = q->run.v;
+      hb->st[i] = q->st;
+      hb->part[i] = q->part;
+      blocks += q->grid;
+      hb->start[i + 1] = blocks;
+      kt = std::max(kt, q->run.kt);
+      todo = std::max(todo, q->cycle_len());
+    }
+    const int ld = kt == 0 ? 0 : sv[active[0]]->ldk;
+    RB_CUDA(cudaMemcpyAsync(dba, hb.get(), sizeof(BatchArgs<V, T>), cudaMemcpyHostToDevice, s0));
+    for (int t = 0; t < todo; ++t) {
+      launch_phase1_batch<V, T>(dba, blocks, ld, s0);
+      launch_phase2_batch<V, T>(dba, blocks, kt, s0);
+      launch_phase3_batch<V, T>(dba, blocks, s0);
+    }
+    sv[active[0]]->count(3 * todo);
+    for (int r : active) sv[r]->fetch_async();
+    RB_CUDA(cudaStreamSynchronize(s0));
+    for (int r : active) sv[r]->prof->harvest();
+    std::vector<int> next;
+    for (int r : active) {
+      sv[r]->after_cycle();
+      if (!sv[r]->run.done) next.push_back(r);
+    }
+    active.swap(next);
+  }
+  for (int r = 0; r < nb; ++r) {
+    const rbicg_result o = to_result(sv[r]->end());
+    if (res) res[r] = o;
+  }
+}
+
 extern "C" rbicg_status rbicg_solve_batch(rbicg_handle* hs, const rbicg_csr* const* As, const void* const* bs,
                                           const void* const* bts, void* const* xs, void* const* xts, int count,
                                           rbicg_result* res) {
-  if (!hs || count < 0) return fail(nullptr, RBICG_ERR_ARG, "bad batch arguments");
+  if (!hs || count < 0 || count > BMAX || (count > 0 && (!bs || !bts || !xs || !xts)))
+    return fail(nullptr, RBICG_ERR_ARG, "bad batch arguments (count must be 0..32, arrays non-null)");
+  if (count == 0) return RBICG_OK;
+  // operators first (as rbicg_solve_pair would), then decide whether the batch can run together
+  for (int i = 0; i < count; ++i) {
+    rbicg_handle h = hs[i];
+    if (!h) return fail(nullptr, RBICG_ERR_ARG, "handle is NULL");
+    if (!bs[i] || !bts[i] || !xs[i] || !xts[i]) return fail(h, RBICG_ERR_ARG, "null vector pointer");
+    for (int q = 0; q < i; ++q)
+      if (hs[q] == h) return fail(h, RBICG_ERR_ARG, "a handle appears twice in the batch");
+    const rbicg_csr* A = As ? As[i] : nullptr;
+    RB_GUARD(h, {
+      if (A) {
+        const std::string m = check_csr(h, A);
+        if (!m.empty()) return fail(h, RBICG_ERR_ARG, m);
+        OpKey k;
+        k.rp = A->row_ptr; k.ci = A->col_idx; k.va = A->val; k.n = A->n; k.nnz = A->nnz; k.has_shift = A->has_shift;
+        k.val_complex = A->val_complex; k.sr = A->shift_re; k.si = A->shift_im;
+        if (!h->impl || !(k == h->key)) do_update(h, A);
+      }
+      if (!h->impl) return fail(h, RBICG_ERR_ARG, "no operator set (pass A or call rbicg_update_recycle)");
+    })
+  }
+  int kind0 = -1;
+  bool together = true;
+  std::vector<void*> solvers(count);
+  for (int i = 0; i < count; ++i) {
+    int kind = -1;
+    solvers[i] = hs[i]->impl->batch_solver(&kind);
+    if (!solvers[i] || (i > 0 && (kind != kind0 || hs[i]->prm.k != hs[0]->prm.k))) together = false;
+    if (i == 0) kind0 = kind;
+  }
+  if (!together) {
+    // mixed kinds, recycle dimensions or FP32-refined handles: one after another
+    rbicg_status worst = RBICG_OK;
+    for (int i = 0; i < count; ++i) {
+      rbicg_result r{};
+      const rbicg_status st = rbicg_solve_pair(hs[i], nullptr, bs[i], bts[i], xs[i], xts[i], &r);
+      if (res) res[i] = r;
+      if (st < 0) return st;
+      if (st > worst) worst = st;
+    }
+    return worst;
+  }
+  std::vector<rbicg_handle> hv(hs, hs + count);
+  std::vector<rbicg_result> out(count);
+  RB_GUARD(hs[0], {
+    switch (kind0) {
+      case 0: {
+        std::vector<Solver<double, double>*> sv(count);
+        for (int i = 0; i < count; ++i) sv[i] = static_cast<Solver<double, double>*>(solvers[i]);
+        run_batch<double, double>(sv, hv, bs, bts, xs, xts, out.data(), hs[0]->s);
+        break;
+      }
+      case 1: {
+        std::vector<Solver<double, cplx<double>>*> sv(count);
+        for (int i = 0; i < count; ++i) sv[i] = static_cast<Solver<double, cplx<double>>*>(solvers[i]);
+        run_batch<double, cplx<double>>(sv, hv, bs, bts, xs, xts, out.data(), hs[0]->s);
+        break;
+      }
+      default: {
+        std::vector<Solver<cplx<double>, cplx<double>>*> sv(count);
+        for (int i = 0; i < count; ++i) sv[i] = static_cast<Solver<cplx<double>, cplx<double>>*>(solvers[i]);
+        run_batch<cplx<double>, cplx<double>>(sv, hv, bs, bts, xs, xts, out.data(), hs[0]->s);
+        break;
+      }
+    }
+  })
   rbicg_status worst = RBICG_OK;
   for (int i = 0; i < count; ++i) {
-    rbicg_result r{};
-    const rbicg_status st = rbicg_solve_pair(hs[i], As ? As[i] : nullptr, bs[i], bts[i], xs[i], xts[i], &r);
-    if (res) res[i] = r;
-    if (st < 0) return st;
-    if (st > worst) worst = st;
+    if (res) res[i] = out[i];
+    if (out[i].status < 0) return fail(hs[i], (rbicg_status)out[i].status, "non-finite value in the iteration");
+    if (out[i].status > worst) worst = (rbicg_status)out[i].status;
+    hs[i]->err.clear();
   }
   return worst;
 }

@@ -80,6 +80,19 @@ struct VecArgs {
   const T* C; const T* Ct; const T* U; const T* Ut; int ldk;   // n x ldk row-major bases
 };
 
+// Per-request arguments of a batched iteration launch: request r owns the blocks
+// [start[r], start[r + 1]) of the grid.  Lives in device memory.
+constexpr int BMAX = 32;
+template <class V, class T>
+struct BatchArgs {
+  OpArgs<V> op[BMAX];
+  VecArgs<T> v[BMAX];
+  DevState* st[BMAX];
+  void* part[BMAX];
+  int start[BMAX + 1];
+  int nreq;
+};
+
 // Column source of a tall-skinny product: column c of a row-major block (stride ld) or a
 // plain vector (stride 1), scaled on the dense side.
 template <class T>
@@ -91,6 +104,12 @@ template <class T>
 struct ColList { int m; ColSrc<T> c[GRAM_MAXCOLS]; };
 
 // ---- launchers (kernels_iter.cu) ----
+template <class V, class T>
+void launch_phase1_batch(const BatchArgs<V, T>* ba, int blocks, int ld, cudaStream_t s);
+template <class V, class T>
+void launch_phase2_batch(const BatchArgs<V, T>* ba, int blocks, int kt, cudaStream_t s);
+template <class V, class T>
+void launch_phase3_batch(const BatchArgs<V, T>* ba, int blocks, cudaStream_t s);
 template <class V, class T>
 void launch_phase1(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
                    cudaStream_t s);

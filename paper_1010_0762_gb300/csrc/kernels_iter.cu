@@ -26,15 +26,22 @@ __device__ __forceinline__ zd ld_cg(const zd* p) {
   return zd(__ldcg(q), __ldcg(q + 1));
 }
 
+// A block's place in its solve: block `id` of `n`.  A single solve uses (blockIdx.x, gridDim.x);
+// a batched launch deals consecutive block ranges to its requests, so every request sees the
+// same blocks, partial sums and reduction order as when it runs alone.
+struct Blk {
+  int id, n;
+};
+
 // Returns true in every thread of the block that arrives last at `cnt` (after all other
 // blocks' partial writes are visible); the last block resets the counter.
-__device__ __forceinline__ bool arrive_last(unsigned int* cnt) {
+__device__ __forceinline__ bool arrive_last(unsigned int* cnt, int nblk) {
   __shared__ int s_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int t = atomicAdd(cnt, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == (unsigned int)nblk - 1);
     if (s_last) *cnt = 0u;
   }
   __syncthreads();
@@ -58,9 +65,9 @@ __device__ void reduce_cols(const A* part, int G, int cnt, A* out) {
 
 // Block-sum `cnt` accumulators (register arrays) and write them as this block's row of part.
 template <class A>
-__device__ void write_partials(A* vals, int cnt, A* smem, A* part) {
+__device__ void write_partials(A* vals, int cnt, A* smem, A* part, int bid) {
   block_sum_vec(vals, cnt, smem);
-  if (threadIdx.x < cnt) part[(int64_t)blockIdx.x * cnt + threadIdx.x] = smem[threadIdx.x];
+  if (threadIdx.x < cnt) part[(int64_t)bid * cnt + threadIdx.x] = smem[threadIdx.x];
 }
 
 template <class T> struct shift_of {
@@ -129,8 +136,8 @@ __device__ void fold_slots(const A* red, A* wpart, int nwarps, A* out) {
 }
 
 template <class V, class T, int LD>
-__global__ void __launch_bounds__(NTHREADS) k_phase1(OpArgs<V> op, VecArgs<T> v, DevState* st,
-                                                     typename traits<T>::acc* part) {
+__device__ __forceinline__ void phase1_body(const OpArgs<V> op, const VecArgs<T> v, DevState* st,
+                                            typename traits<T>::acc* part, Blk g) {
   typedef typename traits<T>::acc A;
   constexpr int NW = NTHREADS / 32;
   constexpr int LDA = LD > 0 ? LD : 4;
@@ -145,17 +152,18 @@ __global__ void __launch_bounds__(NTHREADS) k_phase1(OpArgs<V> op, VecArgs<T> v,
   const int64_t so = (int64_t)((i - 1) % v.R) * v.ld;
   const T* __restrict__ r = v.ring + so;
   const T* __restrict__ rt = v.ringt + so;
-  const T* __restrict__ po = v.p[(i - 1) & 1];
-  const T* __restrict__ pto = v.pt[(i - 1) & 1];
-  T* __restrict__ pn = v.p[i & 1];
-  T* __restrict__ ptn = v.pt[i & 1];
+  // (selects instead of indexing: the argument structs then stay in registers)
+  const T* __restrict__ po = (i & 1) ? v.p[0] : v.p[1];
+  const T* __restrict__ pto = (i & 1) ? v.pt[0] : v.pt[1];
+  T* __restrict__ pn = (i & 1) ? v.p[1] : v.p[0];
+  T* __restrict__ ptn = (i & 1) ? v.pt[1] : v.pt[0];
   const T sh = shift_of<T>::get(op.sh_re, op.sh_im), shc = conjg(sh);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T a1[P], a2[P];
 #pragma unroll
   for (int u = 0; u < P; ++u) { a1[u] = T(0); a2[u] = T(0); }
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x + warp * 32; base < op.n; base += stride) {
+  const int stride = g.n * blockDim.x;
+  for (int base = g.id * blockDim.x + warp * 32; base < op.n; base += stride) {
     const int row = base + lane;
     T z = T(0), zt = T(0);
     if (row < op.n) {
@@ -213,9 +221,9 @@ __global__ void __launch_bounds__(NTHREADS) k_phase1(OpArgs<V> op, VecArgs<T> v,
   for (int u = 0; u < P; ++u) red[(warp * 32 + lane) * P + u] = cvt<A>(a2[u]);
   __syncthreads();
   fold_slots<A, LDA>(red, wpart, NW, tot + LDA);    // C^H zt  -> tot[LD .. 2 LD)
-  if (threadIdx.x < 2 * LDA) part[(int64_t)blockIdx.x * (2 * LDA) + threadIdx.x] = tot[threadIdx.x];
-  if (!arrive_last(&st->cnt[0])) return;
-  reduce_cols(part, gridDim.x, 2 * LDA, tot);
+  if (threadIdx.x < 2 * LDA) part[(int64_t)g.id * (2 * LDA) + threadIdx.x] = tot[threadIdx.x];
+  if (!arrive_last(&st->cnt[0], g.n)) return;
+  reduce_cols(part, g.n, 2 * LDA, tot);
   const int k = st->kc;
   if (threadIdx.x < k) {
     const double d = st->Dc[threadIdx.x];
@@ -228,8 +236,8 @@ __global__ void __launch_bounds__(NTHREADS) k_phase1(OpArgs<V> op, VecArgs<T> v,
 // phase 2: q = z - C zeta, qt = zt - Ct zetat, (pt, q) -> alpha
 // ------------------------------------------------------------------------------------
 template <class V, class T, int KT>
-__global__ void __launch_bounds__(NTHREADS) k_phase2(OpArgs<V> op, VecArgs<T> v, DevState* st,
-                                                     typename traits<T>::acc* part) {
+__device__ __forceinline__ void phase2_body(const OpArgs<V> op, const VecArgs<T> v, DevState* st,
+                                            typename traits<T>::acc* part, Blk g) {
   typedef typename traits<T>::acc A;
   constexpr int KA = KT > 0 ? KT : 1;
   __shared__ A red[(NTHREADS / 32) * 3];
@@ -243,10 +251,10 @@ __global__ void __launch_bounds__(NTHREADS) k_phase2(OpArgs<V> op, VecArgs<T> v,
     zet[c] = c < k ? from_zd<T>(st->zetat[c]) : T(0);
   }
   __syncthreads();
-  const T* __restrict__ pt = v.pt[i & 1];
+  const T* __restrict__ pt = (i & 1) ? v.pt[1] : v.pt[0];
   A pq = A(0.0), nq = A(0.0), npt = A(0.0);
-  const int stride = gridDim.x * blockDim.x;
-  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += stride) {
+  const int stride = g.n * blockDim.x;
+  for (int row = g.id * blockDim.x + threadIdx.x; row < op.n; row += stride) {
     T q = v.z[row], qt = v.zt[row];
     if (KT > 0) {
       const T* __restrict__ crow = v.C + (int64_t)row * v.ldk;
@@ -263,9 +271,9 @@ __global__ void __launch_bounds__(NTHREADS) k_phase2(OpArgs<V> op, VecArgs<T> v,
     npt += A((double)abs2(ptr));
   }
   A vals[3] = {pq, nq, npt};
-  write_partials(vals, 3, red, part);
-  if (!arrive_last(&st->cnt[1])) return;
-  reduce_cols(part, gridDim.x, 3, tot);
+  write_partials(vals, 3, red, part, g.id);
+  if (!arrive_last(&st->cnt[1], g.n)) return;
+  reduce_cols(part, g.n, 3, tot);
   if (threadIdx.x == 0) {
     const zd PQ = to_zd(tot[0]);
     const double NQ = real_of(tot[1]), NPT = real_of(tot[2]);
@@ -296,8 +304,8 @@ __global__ void __launch_bounds__(NTHREADS) k_phase2(OpArgs<V> op, VecArgs<T> v,
 // phase 3: x, r updates, rho, norms, stopping test, beta
 // ------------------------------------------------------------------------------------
 template <class V, class T>
-__global__ void __launch_bounds__(NTHREADS) k_phase3(OpArgs<V> op, VecArgs<T> v, DevState* st,
-                                                     typename traits<T>::acc* part) {
+__device__ __forceinline__ void phase3_body(const OpArgs<V> op, const VecArgs<T> v, DevState* st,
+                                            typename traits<T>::acc* part, Blk g) {
   typedef typename traits<T>::acc A;
   __shared__ A red[(NTHREADS / 32) * 3];
   __shared__ A tot[3];
@@ -309,11 +317,11 @@ __global__ void __launch_bounds__(NTHREADS) k_phase3(OpArgs<V> op, VecArgs<T> v,
   const T* __restrict__ rto = v.ringt + so;
   T* __restrict__ rn = v.ring + sn;
   T* __restrict__ rtn = v.ringt + sn;
-  const T* __restrict__ p = v.p[i & 1];
-  const T* __restrict__ pt = v.pt[i & 1];
+  const T* __restrict__ p = (i & 1) ? v.p[1] : v.p[0];
+  const T* __restrict__ pt = (i & 1) ? v.pt[1] : v.pt[0];
   A rho = A(0.0), n1 = A(0.0), n2 = A(0.0);
-  const int stride = gridDim.x * blockDim.x;
-  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += stride) {
+  const int stride = g.n * blockDim.x;
+  for (int row = g.id * blockDim.x + threadIdx.x; row < op.n; row += stride) {
     v.x[row] = v.x[row] + al * p[row];
     v.xt[row] = v.xt[row] + cal * pt[row];
     const T a = ro[row] - al * v.z[row];
@@ -325,9 +333,9 @@ __global__ void __launch_bounds__(NTHREADS) k_phase3(OpArgs<V> op, VecArgs<T> v,
     n2 += A((double)abs2(b));
   }
   A vals[3] = {rho, n1, n2};
-  write_partials(vals, 3, red, part);
-  if (!arrive_last(&st->cnt[2])) return;
-  reduce_cols(part, gridDim.x, 3, tot);
+  write_partials(vals, 3, red, part, g.id);
+  if (!arrive_last(&st->cnt[2], g.n)) return;
+  reduce_cols(part, g.n, 3, tot);
   if (threadIdx.x == 0) {
     const zd RHO = to_zd(tot[0]);
     const double rr = sqrt(real_of(tot[1])), rtr = sqrt(real_of(tot[2]));
@@ -347,6 +355,37 @@ __global__ void __launch_bounds__(NTHREADS) k_phase3(OpArgs<V> op, VecArgs<T> v,
     st->beta = beta;
   }
 }
+
+
+// Single-solve kernels and their batched forms (one launch for every request of a batch).
+template <class V, class T>
+__device__ __forceinline__ int batch_slot(const BatchArgs<V, T>* ba) {
+  int r = 0;
+  while (r + 1 < ba->nreq && (int)blockIdx.x >= ba->start[r + 1]) ++r;
+  return r;
+}
+// MINB resident blocks per SM: the unrolled slab projection of phase 1 otherwise takes 128
+// registers a thread and halves the warps that hide the gather latency.
+#define RB_PHASE_KERNELS(NAME, BODY, MINB, TPARAMS, TARGS)                                               \
+  template <TPARAMS>                                                                                    \
+  __global__ void __launch_bounds__(NTHREADS, MINB) NAME(OpArgs<V> op, VecArgs<T> v, DevState* st,     \
+                                                         typename traits<T>::acc* part) {              \
+    BODY<TARGS>(op, v, st, part, Blk{(int)blockIdx.x, (int)gridDim.x});                                 \
+  }                                                                                                     \
+  template <TPARAMS>                                                                                    \
+  __global__ void __launch_bounds__(NTHREADS, MINB) NAME##_b(const BatchArgs<V, T>* __restrict__ ba) { \
+    const int r = batch_slot(ba);                                                                       \
+    const OpArgs<V> op = ba->op[r];                                                                     \
+    const VecArgs<T> v = ba->v[r];                                                                      \
+    BODY<TARGS>(op, v, ba->st[r], reinterpret_cast<typename traits<T>::acc*>(ba->part[r]),             \
+                Blk{(int)blockIdx.x - ba->start[r], ba->start[r + 1] - ba->start[r]});                  \
+  }
+#define RB_COMMA ,
+RB_PHASE_KERNELS(k_phase1, phase1_body, 3, class V RB_COMMA class T RB_COMMA int LD, V RB_COMMA T RB_COMMA LD)
+RB_PHASE_KERNELS(k_phase2, phase2_body, 4, class V RB_COMMA class T RB_COMMA int KT, V RB_COMMA T RB_COMMA KT)
+RB_PHASE_KERNELS(k_phase3, phase3_body, 4, class V RB_COMMA class T, V RB_COMMA T)
+#undef RB_COMMA
+#undef RB_PHASE_KERNELS
 
 // ------------------------------------------------------------------------------------
 // initial projection, eq. (minusXR): r_{-1} = b - Op x_{-1}, coef = D_c^{-1} Ct^H r_{-1},
@@ -398,8 +437,8 @@ __global__ void __launch_bounds__(NTHREADS) k_init_a(OpArgs<V> op, VecArgs<T> v,
   for (int c = 0; c < KA; ++c) { vals[c] = cvt<A>(a1[c]); vals[KA + c] = cvt<A>(a2[c]); }
   vals[2 * KA] = nb;
   vals[2 * KA + 1] = nbt;
-  write_partials(vals, CNT, red, part);
-  if (!arrive_last(&st->cnt[3])) return;
+  write_partials(vals, CNT, red, part, (int)blockIdx.x);
+  if (!arrive_last(&st->cnt[3], (int)gridDim.x)) return;
   reduce_cols(part, gridDim.x, CNT, tot);
   if (threadIdx.x < k) {
     const double d = st->Dc[threadIdx.x];
@@ -454,8 +493,8 @@ __global__ void __launch_bounds__(NTHREADS) k_init_b(OpArgs<V> op, VecArgs<T> v,
     n2 += A((double)abs2(b));
   }
   A vals[3] = {rho, n1, n2};
-  write_partials(vals, 3, red, part);
-  if (!arrive_last(&st->cnt[4])) return;
+  write_partials(vals, 3, red, part, (int)blockIdx.x);
+  if (!arrive_last(&st->cnt[4], (int)gridDim.x)) return;
   reduce_cols(part, gridDim.x, 3, tot);
   if (threadIdx.x < KMAX) { st->zeta_c[threadIdx.x] = zd(); st->zetat_c[threadIdx.x] = zd(); }
   if (threadIdx.x == 0) {
@@ -523,8 +562,8 @@ __global__ void __launch_bounds__(NTHREADS) k_fin_b(OpArgs<V> op, VecArgs<T> v, 
     n2 += A((double)abs2(v.bt[row] - atx));
   }
   A vals[2] = {n1, n2};
-  write_partials(vals, 2, red, part);
-  if (!arrive_last(&st->cnt[5])) return;
+  write_partials(vals, 2, red, part, (int)blockIdx.x);
+  if (!arrive_last(&st->cnt[5], (int)gridDim.x)) return;
   reduce_cols(part, gridDim.x, 2, tot);
   if (threadIdx.x == 0) {
     st->true_rnorm = sqrt(real_of(tot[0]));
@@ -714,6 +753,32 @@ void launch_phase3(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void*
   k_phase3<V, T><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part);
 }
 template <class V, class T>
+void launch_phase1_batch(const BatchArgs<V, T>* ba, int blocks, int ld, cudaStream_t s) {
+#define RB_CALL(L) k_phase1_b<V, T, L><<<blocks, NTHREADS, 0, s>>>(ba)
+  switch (ld) {
+    case 0: RB_CALL(0); break;
+    case 4: RB_CALL(4); break;
+    case 8: RB_CALL(8); break;
+    case 12: RB_CALL(12); break;
+    case 16: RB_CALL(16); break;
+    case 20: RB_CALL(20); break;
+    case 24: RB_CALL(24); break;
+    case 28: RB_CALL(28); break;
+    default: RB_CALL(32); break;
+  }
+#undef RB_CALL
+}
+template <class V, class T>
+void launch_phase2_batch(const BatchArgs<V, T>* ba, int blocks, int kt, cudaStream_t s) {
+#define RB_CALL(K) k_phase2_b<V, T, K><<<blocks, NTHREADS, 0, s>>>(ba)
+  RB_KT_DISPATCH(kt, RB_CALL)
+#undef RB_CALL
+}
+template <class V, class T>
+void launch_phase3_batch(const BatchArgs<V, T>* ba, int blocks, cudaStream_t s) {
+  k_phase3_b<V, T><<<blocks, NTHREADS, 0, s>>>(ba);
+}
+template <class V, class T>
 void launch_init(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
                  int dual_only, cudaStream_t s) {
   typedef typename traits<T>::acc A;
@@ -794,6 +859,9 @@ int build_adjoint(int n, const int* rp, const int* ci, const V* va, int** trp, i
                                     cudaStream_t);                                                         \
   template void launch_phase2<V, T>(const OpArgs<V>&, const VecArgs<T>&, DevState*, void*, int, int,       \
                                     cudaStream_t);                                                         \
+  template void launch_phase1_batch<V, T>(const BatchArgs<V, T>*, int, int, cudaStream_t);                 \
+  template void launch_phase2_batch<V, T>(const BatchArgs<V, T>*, int, int, cudaStream_t);                 \
+  template void launch_phase3_batch<V, T>(const BatchArgs<V, T>*, int, cudaStream_t);                      \
   template void launch_phase3<V, T>(const OpArgs<V>&, const VecArgs<T>&, DevState*, void*, int,            \
                                     cudaStream_t);                                                         \
   template void launch_init<V, T>(const OpArgs<V>&, const VecArgs<T>&, DevState*, void*, int, int, int,    \

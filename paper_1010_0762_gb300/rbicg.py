@@ -212,6 +212,22 @@ class Solver:
 
 
 # ------------------------------------------------------------------ component entry points
+def solve_batch(solvers, ops, bs, bts, xs, xts):
+    """Solve len(solvers) dual pairs together (rbicg_solve_batch): one launch per iteration phase
+    for all of them; each solver keeps its own recycle space; results equal solving alone."""
+    cnt = len(solvers)
+    H = (C.c_void_p * cnt)(*[s_.h.value for s_ in solvers])
+    As = (C.POINTER(CSRStruct) * cnt)(*[C.pointer(o.struct) if o is not None else None for o in ops])
+    P = lambda ts: (C.c_void_p * cnt)(*[_ptr(t) for t in ts])
+    out = (Result * cnt)()
+    for s_, o in zip(solvers, ops):
+        if o is not None:
+            s_._op = o
+    st = lib.rbicg_solve_batch(H, As, P(bs), P(bts), P(xs), P(xts), cnt, out)
+    _check(st, solvers[0].h if cnt else None)
+    return [out[i].as_dict() for i in range(cnt)]
+
+
 def op_dual_spmv_project(op: Operator, r, rt, p_old, pt_old, beta, C_=None, Ct=None, Dc=None, stream=None):
     """Phase 1 of an iteration: returns (p, pt, z, zt, zeta, zetat)."""
     cx = r.dtype == torch.complex128

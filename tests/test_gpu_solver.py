@@ -276,6 +276,60 @@ def test_batch_equals_individual(R):
         assert np.array_equal(xts[i].cpu().numpy(), alone[i][2])
 
 
+def test_ragged_batch_with_recycling_equals_individual(R):
+    # three sequences on grids of different sizes, two pairs each: the second round recycles
+    # (refreshes and projections active); batched results are bit-identical to solo solves
+    grids = [(20, [10.0, 10.0]), (24, [3.0, 1.0]), (16, [5.0, 2.0])]
+    seqs = [I.convdiff_sequence(N, c, 2, 0.01, 300 + N, bt_kind="normal") for N, c in grids]
+    alone = []
+    for sq in seqs:
+        n = sq[0]["A"].n
+        S = R.Solver(n, k=6, s=20, tol=1e-9, setup_fp32=0)
+        alone.append([_solve_gpu(R, S, pr["A"], pr["b"], pr["bt"]) for pr in sq])
+    hs = [R.Solver(sq[0]["A"].n, k=6, s=20, tol=1e-9, setup_fp32=0) for sq in seqs]
+    for j in range(2):
+        ops = [R.Operator.from_csr(sq[j]["A"]) for sq in seqs]
+        bs = [_dev(sq[j]["b"]) for sq in seqs]
+        bts = [_dev(sq[j]["bt"]) for sq in seqs]
+        xs = [_dev(np.zeros(sq[j]["A"].n)) for sq in seqs]
+        xts = [_dev(np.zeros(sq[j]["A"].n)) for sq in seqs]
+        out = R.solve_batch(hs, ops, bs, bts, xs, xts)
+        for i in range(len(seqs)):
+            ref, xr, xtr = alone[i][j]
+            assert out[i]["iters"] == ref["iters"] and out[i]["recycle_dim"] == ref["recycle_dim"], (i, j)
+            assert out[i]["cycles"] == ref["cycles"]
+            assert np.array_equal(xs[i].cpu().numpy(), xr)
+            assert np.array_equal(xts[i].cpu().numpy(), xtr)
+        if j == 1:
+            assert any(o["recycle_dim"] > 0 for o in out)
+
+
+def test_shifted_complex_batch_equals_individual(R):
+    # IRKA-shaped: one real A, complex shifts in conjugate pairs, (sigma I - A) x = b in
+    # complex128; the batch shares A's arrays and adds each shift in the kernel
+    A = I.convdiff(16, [10.0, 10.0], dim=2)
+    n = A.n
+    shifts = [complex(-50.0, 300.0), complex(-50.0, -300.0), complex(-500.0, 40.0), complex(-500.0, -40.0)]
+    rng = np.random.default_rng(5)
+    b = [rng.standard_normal(n) + 0j for _ in shifts]
+    c = [rng.standard_normal(n) + 0j for _ in shifts]
+    alone = []
+    for i, sg in enumerate(shifts):
+        S = R.Solver(n, k=8, s=20, tol=1e-10, dtype=R.C128, setup_fp32=0)
+        alone.append(_solve_gpu(R, S, A, b[i], c[i], shift=sg, cx=True))
+    hs = [R.Solver(n, k=8, s=20, tol=1e-10, dtype=R.C128, setup_fp32=0) for _ in shifts]
+    ops = [R.Operator.from_csr(A, shift=sg) for sg in shifts]
+    xs = [_dev(np.zeros(n, complex), True) for _ in shifts]
+    xts = [_dev(np.zeros(n, complex), True) for _ in shifts]
+    out = R.solve_batch(hs, ops, [_dev(v, True) for v in b], [_dev(v, True) for v in c], xs, xts)
+    for i, sg in enumerate(shifts):
+        ref, xr, xtr = alone[i]
+        assert out[i]["status"] == R.OK and out[i]["iters"] == ref["iters"]
+        assert np.array_equal(xs[i].cpu().numpy(), xr) and np.array_equal(xts[i].cpu().numpy(), xtr)
+        Ad = (sg * sp.identity(n) - A.to_scipy()).tocsc()
+        assert _rel(xr, sp.linalg.spsolve(Ad, b[i])) < 1e-8
+
+
 @pytest.mark.parametrize("setup_fp32", [0, 1])
 def test_second_system_recycle_space_matches_oracle(R, setup_fp32):
     # later-system refresh cases of Section 4.2 (first cycle with C) and 4.1 (general cycle):
