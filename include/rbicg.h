@@ -93,6 +93,10 @@ typedef struct {
                               its current iterate and continues from it as plain BiCG (Algorithm 2
                               with an empty recycle space); rbicg_result.fallback reports it.
                               0 disables the guard. */
+  int grid_blocks;         /* blocks of 256 threads per iteration-phase launch (0: the default,
+                              min(ceil(n / 256), 8 x SMs)); rbicg_autotune picks one by timed
+                              trials.  Reductions follow the block partition, so results are
+                              reproducible for a given value. */
 } rbicg_params;
 
 /* A sparse operator.  Operator = A when has_shift == 0, (shift I - A) otherwise. */
@@ -148,13 +152,47 @@ rbicg_status rbicg_update_recycle(rbicg_handle h, const rbicg_csr *A);
 rbicg_status rbicg_solve_pair(rbicg_handle h, const rbicg_csr *A, const void *b, const void *bt,
                               void *x, void *xt, rbicg_result *res);
 
-/* Solve `count` independent dual pairs, one per handle, with their iterations interleaved on
- * the first handle's stream (each handle keeps its own recycle space).  Arrays are host
- * arrays of length count holding the per-pair arguments of rbicg_solve_pair.  Results are
- * the same as solving each pair alone. */
+/* Solve `count` (<= 32) independent dual pairs, one per handle, together on the first handle's
+ * stream through a continuous-batching engine (below): each iteration phase is one launch for
+ * all FP64 pairs; each handle keeps its own recycle space, stopping test and cycle refreshes.
+ * Arrays are host arrays of length count holding the per-pair arguments of rbicg_solve_pair
+ * (As[i] may be NULL to reuse the handle's operator).  Results are bit-identical to solving
+ * each pair alone with rbicg_solve_pair.  A handle may appear only once. */
 rbicg_status rbicg_solve_batch(rbicg_handle *hs, const rbicg_csr *const *As, const void *const *bs,
                                const void *const *bts, void *const *xs, void *const *xts, int count,
                                rbicg_result *res);
+
+/* Continuous batching.  An engine advances the FP64 requests in flight by one cycle (s
+ * iterations, Algorithm 2 step 5, plus each request's cycle refresh of Sections 4.1-4.3) per
+ * rbicg_engine_step, with ONE launch per iteration phase for all of them; requests join at
+ * submit time and leave when they finish, between steps.  Each request is one dual pair on its
+ * own handle (at most one in flight per handle; at most 32 in flight), and its results are
+ * bit-identical to rbicg_solve_pair on that handle: the batched launch gives every request its
+ * own blocks, partial sums and reduction order.  FP32_REFINED requests are solved whole inside
+ * submit.  The paper has no counterpart (serving layer).  Buffers must stay valid until the
+ * request is polled.  stream: the engine's cudaStream_t (NULL = legacy default stream); the
+ * handles' own streams are used again once their requests finish. */
+typedef struct rbicg_engine_s *rbicg_engine;
+rbicg_status rbicg_engine_create(void *stream, rbicg_engine *out);
+/* Start a request: operator update if A differs from the handle's (Section 4.3 system start),
+ * initial projection (eq. (minusXR)); tag is returned by rbicg_engine_poll. */
+rbicg_status rbicg_engine_submit(rbicg_engine e, rbicg_handle h, const rbicg_csr *A, const void *b,
+                                 const void *bt, void *x, void *xt, int64_t tag);
+/* One cycle for every request in flight; *in_flight receives the number still running. */
+rbicg_status rbicg_engine_step(rbicg_engine e, int *in_flight);
+/* Up to max finished requests (tags[i], res[i]); *count receives how many. */
+rbicg_status rbicg_engine_poll(rbicg_engine e, int64_t *tags, rbicg_result *res, int max, int *count);
+/* Finishes the requests in flight, then frees the engine. */
+rbicg_status rbicg_engine_destroy(rbicg_engine e);
+
+/* Autotuner (no counterpart in the paper).  Times the iteration phases of Algorithm 2 on the
+ * operator A (plain iterations from a random start, tolerance 0, on a private stream) for the
+ * candidate launch shapes {1, 2, 4, 8, 16} x SMs blocks (capped at ceil(n / 256)), keeps the
+ * fastest in a process-wide cache keyed by (n, nnz, dtype, value type, k), and returns it in
+ * *grid_blocks (with its time per iteration in *us_per_iter, which may be NULL).  A cached
+ * shape is returned without new trials.  Set params->grid_blocks to use it. */
+rbicg_status rbicg_autotune(const rbicg_params *params, rbicg_dtype dtype, const rbicg_csr *A, int trial_iters,
+                            int *grid_blocks, double *us_per_iter);
 
 /* Copy the recycle space for the next pair into caller buffers U, Ut (device, n x k row-major,
  * k = params->k columns, unused columns zero); *p receives the number of valid columns. */

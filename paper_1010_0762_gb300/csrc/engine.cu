@@ -2,6 +2,9 @@
 // Section 4 recycle-space refresh schedule, FP32 inner solves under FP64 refinement, and the
 // C ABI declared in include/rbicg.h.
 #include <algorithm>
+#include <chrono>
+#include <map>
+#include <mutex>
 #include <cstddef>
 #include <cstdio>
 #include <cstdlib>
@@ -214,7 +217,9 @@ struct Solver : SolverBase {
     RB_CUDA(cudaEventCreateWithFlags(&ev_g0, cudaEventDisableTiming));
     RB_CUDA(cudaEventCreateWithFlags(&ev_g1, cudaEventDisableTiming));
     const int sms = num_sms();
-    grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + NTHREADS - 1) / NTHREADS, (int64_t)sms * 8));
+    grid = prm.grid_blocks > 0
+               ? (int)std::min<int64_t>(prm.grid_blocks, std::max<int64_t>(1, (n + NTHREADS - 1) / NTHREADS))
+               : (int)std::max<int64_t>(1, std::min<int64_t>((n + NTHREADS - 1) / NTHREADS, (int64_t)sms * 8));
     gram_grid = 2 * sms;
     const int64_t ldv = ((n + 31) / 32) * 32;   // padded vector stride (256-byte aligned slots)
     ring = dmalloc<T>(ldv * R);
@@ -1053,6 +1058,7 @@ extern "C" void rbicg_default_params(rbicg_params* p) {
   p->refine_max = 12; p->precision = RBICG_FP64; p->seed = 0; p->setup_fp32 = 1; p->recycle = 1;
   p->inner_svd_tol = 1e-3;
   p->guard = 1.5;
+  p->grid_blocks = 0;
 }
 
 static std::string check_params(const rbicg_params* p, int64_t n) {
@@ -1065,6 +1071,7 @@ static std::string check_params(const rbicg_params* p, int64_t n) {
   if (p->max_itn < 1) return "max_itn must be positive";
   if (!(p->svd_tol >= 0.0)) return "svd_tol must be >= 0";
   if (!(p->guard >= 0.0)) return "guard must be >= 0";
+  if (p->grid_blocks < 0 || p->grid_blocks > (1 << 20)) return "grid_blocks must be in 0..2^20";
   if (p->precision == RBICG_FP32_REFINED && !(p->inner_tol > 0.0 && p->inner_tol < 1.0))
     return "inner_tol must be in (0, 1)";
   if (p->precision != RBICG_FP64 && p->precision != RBICG_FP32_REFINED) return "unknown precision";
@@ -1170,161 +1177,6 @@ static rbicg_result to_result(const P& o) {
   r.true_relres = o.true_relres; r.true_relres_dual = o.true_relres_dual;
   r.status = o.status; r.fallback = o.fallback;
   return r;
-}
-
-// A batch of FP64 pairs driven together: every iteration phase is ONE launch over all active
-// requests (request r owns its usual grid's blocks, so its arithmetic and reduction order are
-// exactly those of a solo solve); each request keeps its own stopping test, guard and cycle
-// refreshes (on its own refresh stream); finished requests leave the batch at cycle boundaries.
-template <class V, class T>
-static void run_batch(const std::vector<Solver<V, T>*>& sv, const std::vector<rbicg_handle>& hs,
-                      const void* const* bs, const void* const* bts, void* const* xs, void* const* xts,
-                      rbicg_result* res, cudaStream_t s0) {
-  const int nb = (int)sv.size();
-  std::vector<cudaStream_t> saved(nb);
-  for (int r = 0; r < nb; ++r) {
-    saved[r] = sv[r]->s;
-    sv[r]->s = s0;
-  }
-  struct Restore {
-    const std::vector<Solver<V, T>*>& sv;
-    std::vector<cudaStream_t>& saved;
-    ~Restore() {
-      for (size_t r = 0; r < sv.size(); ++r) sv[r]->s = saved[r];
-    }
-  } restore{sv, saved};
-  BatchArgs<V, T>* dba = dmalloc<BatchArgs<V, T>>(1);
-  std::unique_ptr<BatchArgs<V, T>> hb(new BatchArgs<V, T>());
-  struct Free {
-    void* p;
-    ~Free() { cudaFree(p); }
-  } free_dba{dba};
-  for (int r = 0; r < nb; ++r) {
-    const rbicg_params& q = hs[r]->prm;
-    sv[r]->begin(reinterpret_cast<const T*>(bs[r]), reinterpret_cast<const T*>(bts[r]), reinterpret_cast<T*>(xs[r]),
-                 reinterpret_cast<T*>(xts[r]), q.tol, q.max_itn, q.seed);
-  }
-  std::vector<int> active;
-  for (int r = 0; r < nb; ++r)
-    if (!sv[r]->run.done) active.push_back(r);
-  while (!active.empty()) {
-    int kt = 0, todo = 0, blocks = 0;
-    hb->nreq = (int)active.size();
-    hb->start[0] = 0;
-    for (size_t i = 0; i < active.size(); ++i) {
-      Solver<V, T>* q = sv[active[i]];
-      hb->op[i] = q->op;
-      hb->v[i] = q->run.v;
-      hb->st[i] = q->st;
-      hb->part[i] = q->part;
-      blocks += q->grid;
-      hb->start[i + 1] = blocks;
-      kt = std::max(kt, q->run.kt);
-      todo = std::max(todo, q->cycle_len());
-    }
-    const int ld = kt == 0 ? 0 : sv[active[0]]->ldk;
-    RB_CUDA(cudaMemcpyAsync(dba, hb.get(), sizeof(BatchArgs<V, T>), cudaMemcpyHostToDevice, s0));
-    for (int t = 0; t < todo; ++t) {
-      launch_phase1_batch<V, T>(dba, blocks, ld, s0);
-      launch_phase2_batch<V, T>(dba, blocks, kt, s0);
-      launch_phase3_batch<V, T>(dba, blocks, s0);
-    }
-    sv[active[0]]->count(3 * todo);
-    for (int r : active) sv[r]->fetch_async();
-    RB_CUDA(cudaStreamSynchronize(s0));
-    for (int r : active) sv[r]->prof->harvest();
-    std::vector<int> next;
-    for (int r : active) {
-      sv[r]->after_cycle();
-      if (!sv[r]->run.done) next.push_back(r);
-    }
-    active.swap(next);
-  }
-  for (int r = 0; r < nb; ++r) {
-    const rbicg_result o = to_result(sv[r]->end());
-    if (res) res[r] = o;
-  }
-}
-
-extern "C" rbicg_status rbicg_solve_batch(rbicg_handle* hs, const rbicg_csr* const* As, const void* const* bs,
-                                          const void* const* bts, void* const* xs, void* const* xts, int count,
-                                          rbicg_result* res) {
-  if (!hs || count < 0 || count > BMAX || (count > 0 && (!bs || !bts || !xs || !xts)))
-    return fail(nullptr, RBICG_ERR_ARG, "bad batch arguments (count must be 0..32, arrays non-null)");
-  if (count == 0) return RBICG_OK;
-  // operators first (as rbicg_solve_pair would), then decide whether the batch can run together
-  for (int i = 0; i < count; ++i) {
-    rbicg_handle h = hs[i];
-    if (!h) return fail(nullptr, RBICG_ERR_ARG, "handle is NULL");
-    if (!bs[i] || !bts[i] || !xs[i] || !xts[i]) return fail(h, RBICG_ERR_ARG, "null vector pointer");
-    for (int q = 0; q < i; ++q)
-      if (hs[q] == h) return fail(h, RBICG_ERR_ARG, "a handle appears twice in the batch");
-    const rbicg_csr* A = As ? As[i] : nullptr;
-    RB_GUARD(h, {
-      if (A) {
-        const std::string m = check_csr(h, A);
-        if (!m.empty()) return fail(h, RBICG_ERR_ARG, m);
-        OpKey k;
-        k.rp = A->row_ptr; k.ci = A->col_idx; k.va = A->val; k.n = A->n; k.nnz = A->nnz; k.has_shift = A->has_shift;
-        k.val_complex = A->val_complex; k.sr = A->shift_re; k.si = A->shift_im;
-        if (!h->impl || !(k == h->key)) do_update(h, A);
-      }
-      if (!h->impl) return fail(h, RBICG_ERR_ARG, "no operator set (pass A or call rbicg_update_recycle)");
-    })
-  }
-  int kind0 = -1;
-  bool together = true;
-  std::vector<void*> solvers(count);
-  for (int i = 0; i < count; ++i) {
-    int kind = -1;
-    solvers[i] = hs[i]->impl->batch_solver(&kind);
-    if (!solvers[i] || (i > 0 && (kind != kind0 || hs[i]->prm.k != hs[0]->prm.k))) together = false;
-    if (i == 0) kind0 = kind;
-  }
-  if (!together) {
-    // mixed kinds, recycle dimensions or FP32-refined handles: one after another
-    rbicg_status worst = RBICG_OK;
-    for (int i = 0; i < count; ++i) {
-      rbicg_result r{};
-      const rbicg_status st = rbicg_solve_pair(hs[i], nullptr, bs[i], bts[i], xs[i], xts[i], &r);
-      if (res) res[i] = r;
-      if (st < 0) return st;
-      if (st > worst) worst = st;
-    }
-    return worst;
-  }
-  std::vector<rbicg_handle> hv(hs, hs + count);
-  std::vector<rbicg_result> out(count);
-  RB_GUARD(hs[0], {
-    switch (kind0) {
-      case 0: {
-        std::vector<Solver<double, double>*> sv(count);
-        for (int i = 0; i < count; ++i) sv[i] = static_cast<Solver<double, double>*>(solvers[i]);
-        run_batch<double, double>(sv, hv, bs, bts, xs, xts, out.data(), hs[0]->s);
-        break;
-      }
-      case 1: {
-        std::vector<Solver<double, cplx<double>>*> sv(count);
-        for (int i = 0; i < count; ++i) sv[i] = static_cast<Solver<double, cplx<double>>*>(solvers[i]);
-        run_batch<double, cplx<double>>(sv, hv, bs, bts, xs, xts, out.data(), hs[0]->s);
-        break;
-      }
-      default: {
-        std::vector<Solver<cplx<double>, cplx<double>>*> sv(count);
-        for (int i = 0; i < count; ++i) sv[i] = static_cast<Solver<cplx<double>, cplx<double>>*>(solvers[i]);
-        run_batch<cplx<double>, cplx<double>>(sv, hv, bs, bts, xs, xts, out.data(), hs[0]->s);
-        break;
-      }
-    }
-  })
-  rbicg_status worst = RBICG_OK;
-  for (int i = 0; i < count; ++i) {
-    if (res) res[i] = out[i];
-    if (out[i].status < 0) return fail(hs[i], (rbicg_status)out[i].status, "non-finite value in the iteration");
-    if (out[i].status > worst) worst = (rbicg_status)out[i].status;
-    hs[i]->err.clear();
-  }
-  return worst;
 }
 
 extern "C" rbicg_status rbicg_export_recycle(rbicg_handle h, void* U, void* Ut, int* p) {
@@ -1617,4 +1469,376 @@ extern "C" rbicg_status rbicg_op_svd(rbicg_dtype dtype, int k, const void* S_hos
       }
     return RBICG_OK;
   })
+}
+
+// ------------------------------------------------------------------ continuous batching engine
+// Requests (one dual pair each, on their own handle) join and leave at cycle boundaries; every
+// step advances all in-flight FP64 requests of a kind by one cycle with one batched launch per
+// iteration phase.  A request's arithmetic is exactly its solo solve's (its own grid, partial
+// sums and reduction order), whatever else is in flight.
+struct EngineReq {
+  rbicg_handle h = nullptr;
+  int kind = -1;
+  void* solver = nullptr;
+  cudaStream_t saved = nullptr;
+  int64_t tag = 0;
+};
+
+struct rbicg_engine_s {
+  cudaStream_t s = nullptr;
+  std::vector<EngineReq> active;
+  std::vector<std::pair<int64_t, rbicg_result>> finished;
+  std::vector<std::pair<void*, void*>> bufs[3];   // per kind: (device BatchArgs, pinned staging)
+  std::string err;
+  int64_t steps = 0;
+  ~rbicg_engine_s() {
+    if (s) cudaStreamSynchronize(s);
+    for (auto& pool : bufs)
+      for (auto& b : pool) {
+        cudaFree(b.first);
+        cudaFreeHost(b.second);
+      }
+  }
+};
+
+template <class V, class T>
+static Solver<V, T>* as_solver(const EngineReq& q) { return static_cast<Solver<V, T>*>(q.solver); }
+
+template <class V, class T>
+static void engine_finish(rbicg_engine e, EngineReq& q) {
+  Solver<V, T>* sv = as_solver<V, T>(q);
+  const rbicg_result r = to_result(sv->end());
+  sv->s = q.saved;
+  q.h->err.clear();
+  e->finished.push_back({q.tag, r});
+}
+
+// one cycle for every in-flight request of kind (V, T): one batched launch sequence per
+// basis stride (the slab projection's stride is a template parameter), one sync for all
+template <class V, class T>
+static void engine_step_kind(rbicg_engine e, int kind) {
+  std::vector<int> idx;
+  for (size_t i = 0; i < e->active.size(); ++i)
+    if (e->active[i].kind == kind) idx.push_back((int)i);
+  if (idx.empty()) return;
+  std::vector<int> strides;
+  for (int i : idx) {
+    const int l = as_solver<V, T>(e->active[i])->ldk;
+    if (std::find(strides.begin(), strides.end(), l) == strides.end()) strides.push_back(l);
+  }
+  auto& pool = e->bufs[kind];
+  while (pool.size() < strides.size()) {
+    void* d = dmalloc<BatchArgs<V, T>>(1);
+    void* hp = nullptr;
+    if (cudaMallocHost(&hp, sizeof(BatchArgs<V, T>)) != cudaSuccess) {
+      cudaFree(d);
+      throw Err{RBICG_ERR_OOM, "pinned batch arguments"};
+    }
+    pool.push_back({d, hp});
+  }
+  int launched = 0;
+  for (size_t g = 0; g < strides.size(); ++g) {
+    // the previous step's copies from these staging buffers have completed: every step ends
+    // with a stream sync
+    BatchArgs<V, T>* hb = static_cast<BatchArgs<V, T>*>(pool[g].second);
+    auto* dba = static_cast<BatchArgs<V, T>*>(pool[g].first);
+    int kt = 0, todo = 0, blocks = 0, nreq = 0;
+    hb->start[0] = 0;
+    for (int i : idx) {
+      Solver<V, T>* q = as_solver<V, T>(e->active[i]);
+      if (q->ldk != strides[g]) continue;
+      hb->op[nreq] = q->op;
+      hb->v[nreq] = q->run.v;
+      hb->st[nreq] = q->st;
+      hb->part[nreq] = q->part;
+      blocks += q->grid;
+      hb->start[nreq + 1] = blocks;
+      ++nreq;
+      kt = std::max(kt, q->run.kt);
+      todo = std::max(todo, q->cycle_len());
+    }
+    hb->nreq = nreq;
+    const int ld = kt == 0 ? 0 : strides[g];
+    RB_CUDA(cudaMemcpyAsync(dba, hb, sizeof(BatchArgs<V, T>), cudaMemcpyHostToDevice, e->s));
+    for (int t = 0; t < todo; ++t) {
+      launch_phase1_batch<V, T>(dba, blocks, ld, e->s);
+      launch_phase2_batch<V, T>(dba, blocks, kt, e->s);
+      launch_phase3_batch<V, T>(dba, blocks, e->s);
+    }
+    launched += 3 * todo;
+  }
+  as_solver<V, T>(e->active[idx[0]])->count(launched);
+  for (int i : idx) as_solver<V, T>(e->active[i])->fetch_async();
+  RB_CUDA(cudaStreamSynchronize(e->s));
+  for (int i : idx) {
+    Solver<V, T>* q = as_solver<V, T>(e->active[i]);
+    q->prof->harvest();
+    q->after_cycle();
+  }
+  std::vector<EngineReq> keep;
+  for (size_t i = 0; i < e->active.size(); ++i) {
+    EngineReq& q = e->active[i];
+    if (q.kind == kind && as_solver<V, T>(q)->run.done) engine_finish<V, T>(e, q);
+    else keep.push_back(q);
+  }
+  e->active.swap(keep);
+}
+
+extern "C" rbicg_status rbicg_engine_create(void* stream, rbicg_engine* out) {
+  if (!out) return fail(nullptr, RBICG_ERR_ARG, "out is NULL");
+  rbicg_engine e = new (std::nothrow) rbicg_engine_s();
+  if (!e) return fail(nullptr, RBICG_ERR_OOM, "engine allocation failed");
+  e->s = reinterpret_cast<cudaStream_t>(stream);
+  *out = e;
+  return RBICG_OK;
+}
+
+extern "C" rbicg_status rbicg_engine_submit(rbicg_engine e, rbicg_handle h, const rbicg_csr* A, const void* b,
+                                           const void* bt, void* x, void* xt, int64_t tag) {
+  if (!e || !h) return fail(h, RBICG_ERR_ARG, "engine or handle is NULL");
+  if (!b || !bt || !x || !xt) return fail(h, RBICG_ERR_ARG, "null vector pointer");
+  for (const EngineReq& q : e->active)
+    if (q.h == h) return fail(h, RBICG_ERR_ARG, "this handle already has a request in flight");
+  if ((int)e->active.size() >= BMAX) return fail(h, RBICG_ERR_ARG, "engine full (32 requests in flight)");
+  RB_GUARD(h, {
+    if (A) {
+      const std::string m = check_csr(h, A);
+      if (!m.empty()) return fail(h, RBICG_ERR_ARG, m);
+      OpKey k;
+      k.rp = A->row_ptr; k.ci = A->col_idx; k.va = A->val; k.n = A->n; k.nnz = A->nnz; k.has_shift = A->has_shift;
+      k.val_complex = A->val_complex; k.sr = A->shift_re; k.si = A->shift_im;
+      if (!h->impl || !(k == h->key)) do_update(h, A);
+    }
+    if (!h->impl) return fail(h, RBICG_ERR_ARG, "no operator set (pass A or call rbicg_update_recycle)");
+    EngineReq q;
+    q.h = h;
+    q.tag = tag;
+    q.solver = h->impl->batch_solver(&q.kind);
+    if (!q.solver) {
+      // FP32-refined requests run their refinement loop whole, on the engine's stream order
+      RB_CUDA(cudaStreamSynchronize(e->s));
+      const rbicg_result r = h->impl->solve(b, bt, x, xt);
+      e->finished.push_back({tag, r});
+      return RBICG_OK;
+    }
+    const rbicg_params& p = h->prm;
+    switch (q.kind) {
+      case 0: {
+        auto* sv = static_cast<Solver<double, double>*>(q.solver);
+        q.saved = sv->s; sv->s = e->s;
+        sv->begin((const double*)b, (const double*)bt, (double*)x, (double*)xt, p.tol, p.max_itn, p.seed);
+        if (sv->run.done) { engine_finish<double, double>(e, q); return RBICG_OK; }
+        break;
+      }
+      case 1: {
+        auto* sv = static_cast<Solver<double, cplx<double>>*>(q.solver);
+        q.saved = sv->s; sv->s = e->s;
+        sv->begin((const zd*)b, (const zd*)bt, (zd*)x, (zd*)xt, p.tol, p.max_itn, p.seed);
+        if (sv->run.done) { engine_finish<double, cplx<double>>(e, q); return RBICG_OK; }
+        break;
+      }
+      default: {
+        auto* sv = static_cast<Solver<cplx<double>, cplx<double>>*>(q.solver);
+        q.saved = sv->s; sv->s = e->s;
+        sv->begin((const zd*)b, (const zd*)bt, (zd*)x, (zd*)xt, p.tol, p.max_itn, p.seed);
+        if (sv->run.done) { engine_finish<cplx<double>, cplx<double>>(e, q); return RBICG_OK; }
+        break;
+      }
+    }
+    e->active.push_back(q);
+    return RBICG_OK;
+  })
+}
+
+extern "C" rbicg_status rbicg_engine_step(rbicg_engine e, int* in_flight) {
+  if (!e) return fail(nullptr, RBICG_ERR_ARG, "engine is NULL");
+  try {
+    engine_step_kind<double, double>(e, 0);
+    engine_step_kind<double, cplx<double>>(e, 1);
+    engine_step_kind<cplx<double>, cplx<double>>(e, 2);
+  } catch (const Err& x) {
+    e->err = x.msg;
+    return fail(nullptr, x.st, x.msg);
+  }
+  ++e->steps;
+  if (in_flight) *in_flight = (int)e->active.size();
+  return RBICG_OK;
+}
+
+extern "C" rbicg_status rbicg_engine_poll(rbicg_engine e, int64_t* tags, rbicg_result* res, int max, int* count) {
+  if (!e || !count || max < 0 || (max > 0 && (!tags || !res))) return fail(nullptr, RBICG_ERR_ARG, "bad poll arguments");
+  const int c = std::min<int>(max, (int)e->finished.size());
+  for (int i = 0; i < c; ++i) {
+    tags[i] = e->finished[i].first;
+    res[i] = e->finished[i].second;
+  }
+  e->finished.erase(e->finished.begin(), e->finished.begin() + c);
+  *count = c;
+  return RBICG_OK;
+}
+
+extern "C" rbicg_status rbicg_engine_destroy(rbicg_engine e) {
+  if (!e) return RBICG_OK;
+  // requests still in flight are finished (their handles get their streams back)
+  try {
+    while (!e->active.empty()) {
+      int n = 0;
+      if (rbicg_engine_step(e, &n) != RBICG_OK) break;
+    }
+  } catch (...) {
+  }
+  delete e;
+  return RBICG_OK;
+}
+
+extern "C" rbicg_status rbicg_solve_batch(rbicg_handle* hs, const rbicg_csr* const* As, const void* const* bs,
+                                          const void* const* bts, void* const* xs, void* const* xts, int count,
+                                          rbicg_result* res) {
+  if (!hs || count < 0 || count > BMAX || (count > 0 && (!bs || !bts || !xs || !xts)))
+    return fail(nullptr, RBICG_ERR_ARG, "bad batch arguments (count must be 0..32, arrays non-null)");
+  if (count == 0) return RBICG_OK;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return fail(nullptr, RBICG_ERR_ARG, "handle is NULL");
+    for (int q = 0; q < i; ++q)
+      if (hs[q] == hs[i]) return fail(hs[i], RBICG_ERR_ARG, "a handle appears twice in the batch");
+  }
+  // the whole batch through a continuous-batching engine on the first handle's stream
+  rbicg_engine e = nullptr;
+  rbicg_status st = rbicg_engine_create(hs[0]->s, &e);
+  if (st != RBICG_OK) return st;
+  std::vector<rbicg_result> out(count);
+  std::vector<int> got(count, 0);
+  rbicg_status err = RBICG_OK;
+  for (int i = 0; i < count && err == RBICG_OK; ++i) {
+    st = rbicg_engine_submit(e, hs[i], As ? As[i] : nullptr, bs[i], bts[i], xs[i], xts[i], i);
+    if (st < 0) err = st;
+  }
+  int in_flight = 1;
+  while (err == RBICG_OK && in_flight > 0) {
+    st = rbicg_engine_step(e, &in_flight);
+    if (st < 0) err = st;
+  }
+  std::vector<int64_t> tags(count);
+  std::vector<rbicg_result> rr(count);
+  int c = 0;
+  rbicg_engine_poll(e, tags.data(), rr.data(), count, &c);
+  for (int i = 0; i < c; ++i) {
+    out[tags[i]] = rr[i];
+    got[tags[i]] = 1;
+  }
+  const std::string keep = g_last_error;
+  rbicg_engine_destroy(e);
+  if (err < 0) {
+    g_last_error = keep;
+    return err;
+  }
+  rbicg_status worst = RBICG_OK;
+  for (int i = 0; i < count; ++i) {
+    if (res) res[i] = out[i];
+    if (!got[i]) return fail(hs[i], RBICG_ERR_CUDA, "batch request did not finish");
+    if (out[i].status < 0) return fail(hs[i], (rbicg_status)out[i].status, "non-finite value in the iteration");
+    if (out[i].status > worst) worst = (rbicg_status)out[i].status;
+  }
+  return worst;
+}
+
+
+// ------------------------------------------------------------------ autotuner
+struct TuneKey {
+  int64_t n, nnz;
+  int dtype, vc, k;
+  bool operator<(const TuneKey& o) const {
+    if (n != o.n) return n < o.n;
+    if (nnz != o.nnz) return nnz < o.nnz;
+    if (dtype != o.dtype) return dtype < o.dtype;
+    if (vc != o.vc) return vc < o.vc;
+    return k < o.k;
+  }
+};
+static std::map<TuneKey, std::pair<int, double>> g_tune;
+static std::mutex g_tune_mu;
+
+extern "C" rbicg_status rbicg_autotune(const rbicg_params* params, rbicg_dtype dtype, const rbicg_csr* A,
+                                       int trial_iters, int* grid_blocks, double* us_per_iter) {
+  if (!params || !A || !grid_blocks) return fail(nullptr, RBICG_ERR_ARG, "null argument");
+  if (dtype != RBICG_R64 && dtype != RBICG_C128) return fail(nullptr, RBICG_ERR_ARG, "unknown dtype");
+  const std::string m = check_params(params, A->n);
+  if (!m.empty()) return fail(nullptr, RBICG_ERR_ARG, m);
+  if (trial_iters < 4 || trial_iters > 100000) return fail(nullptr, RBICG_ERR_ARG, "trial_iters must be in 4..100000");
+  const TuneKey key{A->n, A->nnz, (int)dtype, A->val_complex ? 1 : 0, params->k};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *grid_blocks = it->second.first;
+      if (us_per_iter) *us_per_iter = it->second.second;
+      return RBICG_OK;
+    }
+  }
+  const int64_t n = A->n;
+  const size_t w = dtype == RBICG_C128 ? sizeof(zd) : sizeof(double);
+  cudaStream_t s = nullptr;
+  void* buf = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(nullptr, RBICG_ERR_CUDA, "autotune stream");
+  if (cudaMalloc(&buf, 4 * w * (size_t)n) != cudaSuccess) {
+    cudaStreamDestroy(s);
+    return fail(nullptr, RBICG_ERR_OOM, "autotune vectors");
+  }
+  char* b = static_cast<char*>(buf);
+  char* bt = b + w * n;
+  char* x = bt + w * n;
+  char* xt = x + w * n;
+  if (dtype == RBICG_C128) {
+    launch_philox<cplx<double>>(reinterpret_cast<zd*>(b), n, 1, s);
+    launch_philox<cplx<double>>(reinterpret_cast<zd*>(bt), n, 2, s);
+  } else {
+    launch_philox<double>(reinterpret_cast<double*>(b), n, 1, s);
+    launch_philox<double>(reinterpret_cast<double*>(bt), n, 2, s);
+  }
+  const int sms = num_sms();
+  const int64_t cap = std::max<int64_t>(1, (n + NTHREADS - 1) / NTHREADS);
+  std::vector<int> cand;
+  for (int f : {1, 2, 4, 8, 16}) {
+    const int g = (int)std::min<int64_t>(cap, (int64_t)f * sms);
+    if (std::find(cand.begin(), cand.end(), g) == cand.end()) cand.push_back(g);
+  }
+  int best = 0;
+  double best_us = 1e300;
+  rbicg_status err = RBICG_OK;
+  for (int g : cand) {
+    rbicg_params q = *params;
+    q.grid_blocks = g;
+    q.recycle = 0;                 // plain iterations: the phases' SpMV and vector sweeps
+    q.tol = 1e-300;                // never met: exactly trial_iters iterations
+    q.max_itn = trial_iters;
+    q.precision = RBICG_FP64;
+    rbicg_handle h = nullptr;
+    rbicg_status st = rbicg_create(&q, n, dtype, s, &h);
+    if (st != RBICG_OK) { err = st; break; }
+    double t = 0.0;
+    for (int rep = 0; rep < 2 && st >= 0; ++rep) {   // the first solve warms up (and builds A^H)
+      cudaMemsetAsync(x, 0, 2 * w * (size_t)n, s);
+      cudaStreamSynchronize(s);
+      const auto t0 = std::chrono::steady_clock::now();
+      rbicg_result r{};
+      st = rbicg_solve_pair(h, A, b, bt, x, xt, &r);
+      cudaStreamSynchronize(s);
+      t = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count() /
+          std::max(1, r.iters);
+    }
+    rbicg_destroy(h);
+    if (st < 0) { err = st; break; }
+    if (t < best_us) { best_us = t; best = g; }
+  }
+  cudaFree(buf);
+  cudaStreamDestroy(s);
+  if (err < 0) return err;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = {best, best_us};
+  }
+  *grid_blocks = best;
+  if (us_per_iter) *us_per_iter = best_us;
+  return RBICG_OK;
 }

@@ -29,7 +29,8 @@ class Params(C.Structure):
     _fields_ = [("k", C.c_int), ("s", C.c_int), ("max_itn", C.c_int), ("tol", C.c_double),
                 ("svd_tol", C.c_double), ("inner_tol", C.c_double), ("refine_max", C.c_int),
                 ("precision", C.c_int), ("seed", C.c_uint64), ("setup_fp32", C.c_int),
-                ("recycle", C.c_int), ("inner_svd_tol", C.c_double), ("guard", C.c_double)]
+                ("recycle", C.c_int), ("inner_svd_tol", C.c_double), ("guard", C.c_double),
+                ("grid_blocks", C.c_int)]
 
 
 class CSRStruct(C.Structure):
@@ -78,6 +79,12 @@ def _load():
         "rbicg_op_gram": (ci, [ci, i64, vp, ci, ci, vp, ci, ci, ci, vp, vp]),
         "rbicg_op_eig_select": (ci, [ci, ci, vp, vp, ci, vp, vp, vp, C.POINTER(ci), vp]),
         "rbicg_op_svd": (ci, [ci, ci, vp, vp, vp, vp, vp]),
+        "rbicg_autotune": (ci, [C.POINTER(Params), ci, C.POINTER(CSRStruct), ci, C.POINTER(ci), C.POINTER(cd)]),
+        "rbicg_engine_create": (ci, [vp, C.POINTER(vp)]),
+        "rbicg_engine_submit": (ci, [vp, vp, C.POINTER(CSRStruct), vp, vp, vp, vp, i64]),
+        "rbicg_engine_step": (ci, [vp, C.POINTER(ci)]),
+        "rbicg_engine_poll": (ci, [vp, C.POINTER(i64), C.POINTER(Result), ci, C.POINTER(ci)]),
+        "rbicg_engine_destroy": (ci, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -212,6 +219,64 @@ class Solver:
 
 
 # ------------------------------------------------------------------ component entry points
+def autotune(op, dtype=None, trial_iters=60, **params):
+    """Launch shape (blocks per iteration phase) for operator `op` by timed trials; returns
+    (grid_blocks, microseconds per iteration).  Pass grid_blocks=... to Solver to use it."""
+    p = default_params(**params)
+    if dtype is None:
+        dtype = C128 if op.val.dtype == torch.complex128 else R64
+    g = C.c_int(0)
+    us = C.c_double(0.0)
+    _check(lib.rbicg_autotune(C.byref(p), dtype, C.byref(op.struct), int(trial_iters), C.byref(g), C.byref(us)))
+    return g.value, us.value
+
+
+class Engine:
+    """Continuous batching (rbicg_engine_*): submit requests, step cycles, poll results."""
+
+    def __init__(self, stream=None):
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib.rbicg_engine_create(_stream(self.stream), C.byref(h)))
+        self.h = h
+        self._keep = {}   # tag -> tensors that must outlive the request
+
+    def submit(self, solver, op, b, bt, x, xt, tag):
+        if op is not None:
+            solver._op = op
+        opp = C.byref(op.struct) if op is not None else None
+        st = lib.rbicg_engine_submit(self.h, solver.h, opp, _ptr(b), _ptr(bt), _ptr(x), _ptr(xt), int(tag))
+        _check(st, solver.h)
+        self._keep[int(tag)] = (op, b, bt, x, xt)
+
+    def step(self):
+        n = C.c_int(0)
+        _check(lib.rbicg_engine_step(self.h, C.byref(n)))
+        return n.value
+
+    def poll(self, max_count=64):
+        tags = (C.c_int64 * max_count)()
+        res = (Result * max_count)()
+        cnt = C.c_int(0)
+        _check(lib.rbicg_engine_poll(self.h, tags, res, max_count, C.byref(cnt)))
+        out = []
+        for i in range(cnt.value):
+            self._keep.pop(int(tags[i]), None)
+            out.append((int(tags[i]), res[i].as_dict()))
+        return out
+
+    def close(self):
+        if self.h:
+            lib.rbicg_engine_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def solve_batch(solvers, ops, bs, bts, xs, xts):
     """Solve len(solvers) dual pairs together (rbicg_solve_batch): one launch per iteration phase
     for all of them; each solver keeps its own recycle space; results equal solving alone."""

@@ -376,3 +376,23 @@ def test_stagnation_guard_matches_oracle_and_converges(R):
         assert _rel(x, ref[j].x) < 1e-5 and _rel(xt, ref[j].xt) < 1e-5
         fell += res["fallback"]
     assert fell >= 1
+
+
+def test_autotune_picks_a_launch_shape_and_caches_it(R):
+    import time
+    A = I.convdiff(128, [10.0, 10.0])
+    n = A.n
+    op = R.Operator.from_csr(A)
+    g, us = R.autotune(op, trial_iters=40, k=8, s=20)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cap = (n + 255) // 256
+    assert g in {min(cap, f * sms) for f in (1, 2, 4, 8, 16)} and us > 0
+    t0 = time.perf_counter()
+    g2, us2 = R.autotune(op, trial_iters=40, k=8, s=20)
+    assert (g2, us2) == (g, us) and time.perf_counter() - t0 < 0.05   # cached
+    b, bt = I.normal_vector(n, 1), I.normal_vector(n, 2)
+    S = R.Solver(n, k=8, s=20, tol=1e-9, grid_blocks=g)
+    res, x, xt = _solve_gpu(R, S, A, b, bt)
+    assert res["status"] in (R.OK, R.RECYCLE_EMPTY)
+    Ad = A.to_scipy()
+    assert np.linalg.norm(b - Ad @ x) / np.linalg.norm(b) < 2e-9
