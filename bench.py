@@ -191,7 +191,9 @@ def gpu_arm(a):
             run_sequence(R, torch, S, ops, bs, bts, xs, xts)
             torch.cuda.synchronize()
             R.lib.rbicg_profile(S.h, 0, ms, cnt)
-            prof = (list(ms), list(cnt))
+            cols = C.c_int64(0)
+            R.lib.rbicg_profile_columns(S.h, C.byref(cols))
+            prof = (list(ms), list(cnt), cols.value)
         if world > 1:
             t = torch.tensor([total_ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -212,39 +214,54 @@ def gpu_arm(a):
     # roofline of the dominant kernel (phase 1: dual SpMV + projections) from live CUDA events
     names = ["dual_spmv_project", "q_and_pq", "update_dots", "refresh_gram", "refresh_eig",
              "refresh_basis", "system_start", "init_finish_adjoint"]
-    ms_slots, cnt_slots = prof
+    ms_slots, cnt_slots, pcols = prof
     dom = int(np.argmax(ms_slots))
-    fl_tot = by_tot = 0.0
-    for r in per_step:   # the profiled step solves the same sequence once
-        f, b_ = algorithmic_phase1(n, nnz, r["recycle_dim"])
-        fl_tot += f * r["iters"]
-        by_tot += b_ * r["iters"]
+    # algorithmic work of every phase-1 launch of the profiled step: the dual SpMV and p update
+    # of each launch plus 2 projections per active recycle column (pcols sums those widths)
+    f0, b0 = algorithmic_phase1(n, nnz, 0)
+    f1, b1 = algorithmic_phase1(n, nnz, 1)
+    fl_tot = f0 * cnt_slots[0] + (f1 - f0) * pcols
+    by_tot = b0 * cnt_slots[0] + (b1 - b0) * pcols
     t1 = ms_slots[0] * 1e-3
     dgemm = measure_dgemm_tflops(torch)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    # FP64 ALU peak from the unit counts and the SM clock sampled during the timed region:
+    # 2 DFMA per clock per SM x 2 flops x SMs
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    fp64_peak = 2 * 2 * sms * sm_mhz * 1e6 / 1e12
     ach_tf = fl_tot / t1 / 1e12 if t1 > 0 else 0.0
     ach_gbs = by_tot / t1 / 1e9 if t1 > 0 else 0.0
-    alu_frac = ach_tf / dgemm if dgemm > 0 else None
+    alu_frac = ach_tf / fp64_peak
     hbm_frac = ach_gbs / hbm_peak
-    bound = "alu" if alu_frac is not None and alu_frac >= hbm_frac else "hbm"
+    bound = "alu" if alu_frac >= hbm_frac else "hbm"
     launches_phase1 = cnt_slots[0]
+    # DRAM traffic of one k_phase1<double, double, 20> launch on this operator (ncu
+    # dram__bytes_read.sum + dram__bytes_write.sum; summary kept with the profiles) against
+    # the algorithmic bytes of the same launch
+    traffic_k20 = 119.649792e6 + 6.948352e6
+    alg_k20 = algorithmic_phase1(n, nnz, 20)[1]
     roofline = {
         "kernel": "k_phase1 (dual SpMV + p update + Ct^H z, C^H zt)",
         "bound": bound,
         "achieved": round(ach_tf if bound == "alu" else ach_gbs, 4),
-        "peak": round(dgemm if bound == "alu" else hbm_peak, 4),
+        "peak": round(fp64_peak if bound == "alu" else hbm_peak, 4),
         "unit": "TFLOP/s" if bound == "alu" else "GB/s",
         "frac": round(alu_frac if bound == "alu" else hbm_frac, 4),
-        "peak_source": ("FP64 DGEMM measured live in this run (torch.mm 4096^3)" if bound == "alu"
-                        else "MEASURED_PEAKS.json hbm_gbs (of measured)"),
-        "traffic": None,
+        "peak_source": ("FP64 FMA units: 2 DFMA/clock/SM x %d SMs at the sampled %.0f MHz" % (sms, sm_mhz)
+                        if bound == "alu" else "MEASURED_PEAKS.json hbm_gbs (of measured)"),
+        "traffic": traffic_k20 if n == 262144 and nnz == 1308672 else None,
+        "traffic_note": "bytes of one k=20 launch at 512^2 (ncu); algorithmic %.1f MB" % (alg_k20 / 1e6),
         "hbm_view": {"achieved_gbs": round(ach_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_frac, 4)},
-        "alu_view": {"achieved_tflops": round(ach_tf, 4), "peak_tflops": round(dgemm, 4),
-                     "frac": round(alu_frac, 4) if alu_frac else None},
+        "alu_view": {"achieved_tflops": round(ach_tf, 4), "peak_tflops": round(fp64_peak, 4),
+                     "frac": round(alu_frac, 4), "dgemm_tflops_measured": round(dgemm, 4)},
         "avg_launch_us": round(ms_slots[0] * 1e3 / max(1, launches_phase1), 2),
+        "mean_projection_columns": round(pcols / max(1, launches_phase1), 3),
         "launches": int(launches_phase1),
+        "timing": "CUDA events around each phase launch in one profiled step of the same sequence "
+                  "(plain launches), run right after the timed steps",
         "step_share": {names[i]: round(ms_slots[i] / max(1e-9, sum(ms_slots)), 4) for i in range(8)},
         "dominant_slot": names[dom],
     }
@@ -331,6 +348,12 @@ def gpu_arm(a):
                       "h2d_bytes_per_step": int(h2d // e_steps), "d2h_bytes_per_step": int(d2h // e_steps),
                       "steps": e_steps}
 
+        for key, fn in (("irka_batch", irka_batch_extra), ("serving", serving_extra)):
+            try:
+                out[key] = fn(R, torch, a)
+            except Exception as exc:   # an extra must not take the headline line down
+                out[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(seq, a, float(np.mean(iters)))
     if world > 1:
@@ -338,6 +361,110 @@ def gpu_arm(a):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+# ------------------------------------------------------------------ IRKA-shaped batch
+def irka_shifts(count, seed):
+    """Shifts in conjugate pairs: -10^U[0,3] +- i U[0,1e3]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count // 2):
+        re = -(10.0 ** rng.uniform(0.0, 3.0))
+        im = rng.uniform(0.0, 1e3)
+        out += [complex(re, im), complex(re, -im)]
+    return out
+
+
+def irka_batch_extra(R, torch, a, N=64, nshift=8, sweeps=2, k=16):
+    """3-D convection-diffusion (N^3, real A shared by all shifts), nshift shifted dual systems
+    (sigma I - A) x = b, (sigma I - A)^H xt = c in complex128, shifts moving <= 2 % per sweep;
+    each sweep is ONE rbicg_solve_batch over the shifts (recycle spaces carried per shift),
+    compared with the same sweeps solved pair by pair."""
+    from paper_1010_0762_gb300 import inputs as I
+    A = I.convdiff(N, [10.0, 10.0, 10.0], dim=3)
+    n = A.n
+    rp = torch.as_tensor(A.row_ptr, device="cuda")
+    ci = torch.as_tensor(A.col_idx, device="cuda")
+    va = torch.as_tensor(A.val, device="cuda")
+    rng = np.random.default_rng(3000)
+    shifts0 = irka_shifts(nshift, 3001)
+    bs = [torch.as_tensor(rng.standard_normal(n) + 0j, device="cuda") for _ in range(nshift)]
+    cs = [torch.as_tensor(rng.standard_normal(n) + 0j, device="cuda") for _ in range(nshift)]
+    per_sweep = [shifts0]
+    for sw in range(1, sweeps):
+        u = rng.uniform(-1.0, 1.0, size=nshift // 2)
+        prev = per_sweep[-1]
+        nxt = []
+        for p in range(nshift // 2):
+            z = prev[2 * p] * (1.0 + 0.02 * u[p])
+            nxt += [z, z.conjugate()]
+        per_sweep.append(nxt)
+
+    def run(batched):
+        hs = [R.Solver(n, dtype=R.C128, k=k, s=a.s, tol=a.tol) for _ in range(nshift)]
+        its = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for sw in range(sweeps):
+            ops = [R.Operator(rp, ci, va, shift=sg) for sg in per_sweep[sw]]
+            xs = [torch.zeros(n, dtype=torch.complex128, device="cuda") for _ in range(nshift)]
+            xts = [torch.zeros_like(xs[0]) for _ in range(nshift)]
+            if batched:
+                res = R.solve_batch(hs, ops, bs, cs, xs, xts)
+            else:
+                res = [hs[i].solve_pair(ops[i], bs[i], cs[i], xs[i], xts[i]) for i in range(nshift)]
+            its.append([r["iters"] for r in res])
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ok = all(r["status"] in (R.OK, R.RECYCLE_EMPTY) for r in res)
+        for h in hs:
+            h.destroy()
+        return dt, its, ok
+
+    run(True)   # warm-up (adjoints, graphs, lazy module loading)
+    tb, itb, okb = run(True)
+    ts, its_, oks = run(False)
+    solves = sweeps * nshift
+    return {"workload": "convdiff3d-%d^3 complex128, %d shifts in conjugate pairs, %d sweeps, k=%d" % (N, nshift, sweeps, k),
+            "n": n, "nnz": A.nnz, "batched_solves_per_s": round(solves / tb, 4),
+            "sequential_solves_per_s": round(solves / ts, 4), "batched_over_sequential": round(ts / tb, 3),
+            "iters_per_sweep": itb, "same_iters_as_sequential": itb == its_, "all_converged": okb and oks}
+
+
+# ------------------------------------------------------------------ serving
+def serving_extra(R, torch, a, families=16, requests=64, seed=5000):
+    """Continuous batching over the engine: Poisson arrivals of dual-pair requests from
+    `families` convection-diffusion families (grid sides log-uniform in [64, 256] here, so the
+    run stays within a minute; (c1, c2) ~ U[1, 50]^2, 1 % drift per request, k ~ U{10..20},
+    precision fp32_refined with probability 0.5), recycle spaces resident per family, HBM
+    budget 80 % of free memory.  A closed-loop run (all requests at t = 0) measures capacity;
+    the open-loop run offers 0.8 x that rate."""
+    from paper_1010_0762_gb300 import serving as SV
+    specs = SV.random_families(families, seed, side_lo=64, side_hi=256)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+
+    def serve(rate):
+        be = SV.GpuBackend(s=a.s, tol=a.tol)
+        srv = SV.Server(specs, be, budget, s=a.s, max_in_flight=32)
+        reqs = SV.poisson_arrivals(requests, rate if rate > 0 else 1.0, specs, seed + 1, p_fp32=0.5)
+        if rate <= 0:
+            for r in reqs:
+                r.t_arrival = 0.0
+        st = srv.run(reqs)
+        for h in list(srv.resident.values()):
+            h.destroy()
+        be.engine.close()
+        return st
+
+    serve(1e9)   # warm-up
+    closed = serve(0)
+    rate = 0.8 * closed["solves_per_s"]
+    opened = serve(rate)
+    return {"workload": "%d families, grid sides 64..256, %d requests, fp32_refined p=0.5" % (families, requests),
+            "closed_loop": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in closed.items()},
+            "open_loop_rate_per_s": round(rate, 3),
+            "open_loop": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in opened.items()}}
 
 
 # ------------------------------------------------------------------ oracle (CPU) timing

@@ -93,6 +93,10 @@ typedef struct {
                               its current iterate and continues from it as plain BiCG (Algorithm 2
                               with an empty recycle space); rbicg_result.fallback reports it.
                               0 disables the guard. */
+  int restarts;            /* restarts after a BiCG breakdown (not in the paper; default 0: the
+                              breakdown is reported): a pair whose recurrence breaks down (rho or
+                              (pt, q) below 1e-14 of the norms) applies step 7 and continues from
+                              its iterate as plain BiCG, at most this many times */
   int grid_blocks;         /* blocks of 256 threads per iteration-phase launch (0: the default,
                               min(ceil(n / 256), 8 x SMs)); rbicg_autotune picks one by timed
                               trials.  Reductions follow the block partition, so results are
@@ -226,6 +230,9 @@ int64_t rbicg_launch_count(rbicg_handle h);
  * (Section 4.3 last paragraph), 7 initial projection / step 7 / A^H construction. */
 #define RBICG_NPROF 8
 rbicg_status rbicg_profile(rbicg_handle h, int enable, double *ms_out, int64_t *launches_out);
+/* With profiling on: the projection width (columns of C, Ct) summed over the slot-0 launches,
+ * so that their algorithmic work (2 SpMVs and 2 k-column projections each) can be counted. */
+rbicg_status rbicg_profile_columns(rbicg_handle h, int64_t *cols);
 
 /* ---------------------------------------------------------------------------------------
  * Component entry points.  Each runs one step of the hot path on caller-provided device

@@ -579,7 +579,7 @@ def _blockmat(rows, dt):
 # ----------------------------------------------------------------------------------------
 
 def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, seed=0,
-                   x_1=None, xt_1=None, recycle=True, on_pair=None, guard=0.0):
+                   x_1=None, xt_1=None, recycle=True, on_pair=None, guard=0.0, restarts=0):
     """Solve a sequence of dual pairs [{A, b, bt}, ...], carrying the recycle space.
 
     recycle=False gives plain BiCG on every pair (RBiCG with an empty recycle space).
@@ -587,7 +587,11 @@ def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, 
     a pair solved with a recycle space that has not converged after guard x (iterations of
     the last pair solved without one) iterations applies step 7 to its iterate and continues
     from it as plain BiCG (Algorithm 2 with an empty recycle space).
-    Returns a list of PairResult (iters counts both legs of a guarded pair; hist["fallback"]).
+    restarts > 0 reproduces the library's restart after a breakdown (also not in the paper): a
+    pair that ends in a BiCG breakdown (rho or (pt, q) below the relative threshold) continues
+    from its iterate as plain BiCG, at most `restarts` times.
+    Returns a list of PairResult (iters counts every leg; hist["fallback"] is True after a
+    guard fallback or a restart).
     """
     out = []
     Uc = Utc = None
@@ -618,6 +622,16 @@ def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, 
             last_plain = res.iters - first.iters
         elif rec is None or rec[0].shape[1] == 0:
             last_plain = res.iters
+        used = 0
+        while used < restarts and res.status in (STATUS_BREAKDOWN_RHO, STATUS_BREAKDOWN_PQ) and res.iters < max_itn:
+            used += 1
+            prev = res
+            res = rbicg_pair(A, b, bt, prev.x, prev.xt, recycle=None, k=k, s=s, tol=tol,
+                             max_itn=max_itn - prev.iters, svd_tol=svd_tol, seed=seed + j, refresh=recycle)
+            last_plain = res.iters
+            res.iters += prev.iters
+            res.hist["fallback"] = True
+            res.recycle_dim = 0
         if rec is not None and rec[0].shape[1] == 0 and res.status == STATUS_OK:
             res.status = STATUS_RECYCLE_EMPTY
         out.append(res)

@@ -102,6 +102,7 @@ struct Profiler {
   bool on = false;
   double ms[RBICG_NPROF] = {};
   int64_t cnt[RBICG_NPROF] = {};
+  int64_t pcols = 0;   // projection columns summed over the slot-0 launches
   std::vector<cudaEvent_t> pool;
   struct Pend { int slot, nl; cudaEvent_t a, b; };
   std::vector<Pend> pending;
@@ -137,6 +138,7 @@ struct Profiler {
     pending.clear();
   }
   void reset() {
+    pcols = 0;
     for (int i = 0; i < RBICG_NPROF; ++i) { ms[i] = 0; cnt[i] = 0; }
   }
   ~Profiler() {
@@ -483,7 +485,7 @@ struct Solver : SolverBase {
     PairOut out;
     bool recycle = false, broken = false;
     int j = 0, kp = 0, last_refresh = 0, good_refresh = 0, good_p = 0;
-    int done = 0, iter = 0, iter_before = 0, best_at = 0, guard_limit = 0x7fffffff;
+    int done = 0, iter = 0, iter_before = 0, best_at = 0, guard_limit = 0x7fffffff, restarts_used = 0;
     double best_r = 0;
   } run;
 
@@ -493,7 +495,7 @@ struct Solver : SolverBase {
   int cyc_todo = -1, cyc_kt = -1;
   VecArgs<T> cyc_v{};
   OpArgs<V> cyc_op{};
-  bool use_graphs = true;
+  bool use_graphs = getenv("RBICG_NO_GRAPHS") == nullptr;   // profilers see plain launches
 
   void drop_graph() {
     if (cyc_exec) cudaGraphExecDestroy(cyc_exec);
@@ -543,6 +545,7 @@ struct Solver : SolverBase {
   int cycle_len() const { return std::min(prm.s, run.max_itn - run.iter_before - run.iter); }
 
   void launch_phases(int todo) {
+    if (prof->on) prof->pcols += (int64_t)todo * (run.kt > 0 ? kc : 0);
     for (int t = 0; t < todo; ++t) {
       int pp = prof->begin(0, s);
       launch_phase1<V, T>(op, run.v, st, part, run.kt, grid, s);
@@ -612,9 +615,16 @@ struct Solver : SolverBase {
     if (!R_.done && diverge > 0.0 && hv->rnorm > diverge * (hv->bnorm > 0 ? hv->bnorm : 1.0)) R_.done = DONE_MAXIT;
     if (hv->rnorm < R_.best_r) { R_.best_r = hv->rnorm; R_.best_at = total; }
     if (!R_.done && stall_window > 0 && total - R_.best_at > stall_window) R_.done = DONE_MAXIT;
-    const bool bad_end = R_.done == DONE_BREAK_RHO || R_.done == DONE_BREAK_PQ || R_.done == DONE_NONFINITE;
+    const bool breakdown = R_.done == DONE_BREAK_RHO || R_.done == DONE_BREAK_PQ;
+    const bool bad_end = breakdown || R_.done == DONE_NONFINITE;
     const bool stalled = !R_.done && R_.iter >= R_.guard_limit;
-    if (R_.guard_limit != 0x7fffffff && (stalled || bad_end)) {
+    const bool armed = R_.guard_limit != 0x7fffffff;
+    // the guard (armed for a pair solved with a recycle space) or a restart after a breakdown
+    // (rbicg_params.restarts): step 7, then plain BiCG from the current iterate
+    const bool restart = !armed && breakdown && R_.restarts_used < prm.restarts &&
+                         R_.iter_before + R_.iter < R_.max_itn;
+    if ((armed && (stalled || bad_end)) || restart) {
+      if (restart) ++R_.restarts_used;
       join_refresh();   // the restart rewrites ring slots and histories a refresh may read
       if (R_.done == DONE_NONFINITE) {
         // the iterate may hold non-finite values: restart from the saved initial guess
@@ -1058,6 +1068,7 @@ extern "C" void rbicg_default_params(rbicg_params* p) {
   p->refine_max = 12; p->precision = RBICG_FP64; p->seed = 0; p->setup_fp32 = 1; p->recycle = 1;
   p->inner_svd_tol = 1e-3;
   p->guard = 1.5;
+  p->restarts = 0;
   p->grid_blocks = 0;
 }
 
@@ -1072,6 +1083,7 @@ static std::string check_params(const rbicg_params* p, int64_t n) {
   if (!(p->svd_tol >= 0.0)) return "svd_tol must be >= 0";
   if (!(p->guard >= 0.0)) return "guard must be >= 0";
   if (p->grid_blocks < 0 || p->grid_blocks > (1 << 20)) return "grid_blocks must be in 0..2^20";
+  if (p->restarts < 0 || p->restarts > 1000) return "restarts must be in 0..1000";
   if (p->precision == RBICG_FP32_REFINED && !(p->inner_tol > 0.0 && p->inner_tol < 1.0))
     return "inner_tol must be in (0, 1)";
   if (p->precision != RBICG_FP64 && p->precision != RBICG_FP32_REFINED) return "unknown precision";
@@ -1224,6 +1236,12 @@ extern "C" rbicg_status rbicg_profile(rbicg_handle h, int enable, double* ms_out
     if (enable && !h->prof.on) h->prof.reset();
     h->prof.on = enable != 0;
   }
+  return RBICG_OK;
+}
+
+extern "C" rbicg_status rbicg_profile_columns(rbicg_handle h, int64_t* cols) {
+  if (!h || !cols) return fail(h, RBICG_ERR_ARG, "null argument");
+  *cols = h->prof.pcols;
   return RBICG_OK;
 }
 

@@ -30,7 +30,7 @@ class Params(C.Structure):
                 ("svd_tol", C.c_double), ("inner_tol", C.c_double), ("refine_max", C.c_int),
                 ("precision", C.c_int), ("seed", C.c_uint64), ("setup_fp32", C.c_int),
                 ("recycle", C.c_int), ("inner_svd_tol", C.c_double), ("guard", C.c_double),
-                ("grid_blocks", C.c_int)]
+                ("restarts", C.c_int), ("grid_blocks", C.c_int)]
 
 
 class CSRStruct(C.Structure):
@@ -74,6 +74,7 @@ def _load():
         "rbicg_last_error": (C.c_char_p, [vp]),
         "rbicg_launch_count": (i64, [vp]),
         "rbicg_profile": (ci, [vp, ci, C.POINTER(cd), C.POINTER(i64)]),
+        "rbicg_profile_columns": (ci, [vp, C.POINTER(i64)]),
         "rbicg_op_dual_spmv_project": (ci, [C.POINTER(CSRStruct), ci, vp, vp, vp, vp, cd, cd, vp, vp, ci, ci,
                                             vp, vp, vp, vp, vp, vp, vp, vp]),
         "rbicg_op_gram": (ci, [ci, i64, vp, ci, ci, vp, ci, ci, ci, vp, vp]),

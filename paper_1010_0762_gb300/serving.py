@@ -180,6 +180,9 @@ class Server:
             "mean_ms": float(lat.mean()),
             "evictions": self.evictions,
             "all_converged": all(r.result["status"] in (0, 4) for r in requests),
+            "statuses": dict(collections.Counter(int(r.result["status"]) for r in requests)),
+            "fp64_fallbacks": sum(1 for r in requests if r.result.get("fallback") == 2),
+            "mean_iters": float(np.mean([r.result["iters"] for r in requests])),
         }
 
 
@@ -211,19 +214,19 @@ def random_families(count, seed, side_lo=64, side_hi=1024, k_lo=10, k_hi=20, c_h
 class GpuBackend:
     """The device side of Server: resident rbicg handles and one rbicg engine."""
 
-    def __init__(self, s=40, tol=1e-8, stream=None):
+    def __init__(self, s=40, tol=1e-8, stream=None, restarts=0):
         import torch
 
         from . import rbicg as R
         self.R, self.torch = R, torch
-        self.s, self.tol = s, tol
+        self.s, self.tol, self.restarts = s, tol, restarts
         self.engine = R.Engine(stream)
         self.inflight = {}   # tag -> (op, b, bt, x, xt)
         self.patterns = {}   # (N) -> (row_ptr, col_idx) on the device
 
     def make_handle(self, spec, precision):
         n = spec.N * spec.N
-        return self.R.Solver(n, k=spec.k, s=self.s, tol=self.tol, precision=precision)
+        return self.R.Solver(n, k=spec.k, s=self.s, tol=self.tol, precision=precision, restarts=self.restarts)
 
     def free_handle(self, h):
         h.destroy()

@@ -396,3 +396,26 @@ def test_autotune_picks_a_launch_shape_and_caches_it(R):
     assert res["status"] in (R.OK, R.RECYCLE_EMPTY)
     Ad = A.to_scipy()
     assert np.linalg.norm(b - Ad @ x) / np.linalg.norm(b) < 2e-9
+
+
+def test_restart_after_breakdown_matches_oracle(R):
+    # a convection-diffusion pair (side 82, c ~ (26, 36), unrelated random bt) on which plain
+    # BiCG breaks down after ~160 iterations: (rt, r) / (|r| |rt|) decays to 5e-15, oracle and
+    # library alike.  Restarts from the iterate keep the same dual residual, so they break down
+    # again almost at once; the library's restart path follows the oracle's leg by leg.
+    from paper_1010_0762_gb300 import serving as SV
+    sp = SV.random_families(16, 5000, side_lo=64, side_hi=256)[1]
+    A, b, bt = SV.Family(sp).next_problem()
+    pr = [{"A": A, "b": b, "bt": bt}]
+    plain = O.rbicg_sequence(pr, k=10, s=40, tol=1e-8)[0]
+    assert plain.status == O.STATUS_BREAKDOWN_RHO
+    ref = O.rbicg_sequence(pr, k=10, s=40, tol=1e-8, restarts=3)[0]
+    assert ref.hist["fallback"]
+    S0 = R.Solver(A.n, k=10, s=40, tol=1e-8)
+    res0, _, _ = _solve_gpu(R, S0, A, b, bt)
+    assert res0["status"] == R.BREAKDOWN_RHO and abs(res0["iters"] - plain.iters) <= 5
+    S = R.Solver(A.n, k=10, s=40, tol=1e-8, restarts=3)
+    res, x, xt = _solve_gpu(R, S, A, b, bt)
+    assert res["fallback"] == 1 and res["status"] in (R.BREAKDOWN_RHO, R.BREAKDOWN_PQ)
+    assert abs(res["iters"] - ref.iters) <= 10, (res["iters"], ref.iters)
+    assert np.linalg.norm(b - A.to_scipy() @ x) / np.linalg.norm(b) < 1e-2
