@@ -263,6 +263,8 @@ def gpu_arm(a):
         "timing": "CUDA events around each phase launch in one profiled step of the same sequence "
                   "(plain launches), run right after the timed steps",
         "step_share": {names[i]: round(ms_slots[i] / max(1e-9, sum(ms_slots)), 4) for i in range(8)},
+        "slot_ms": {names[i]: round(ms_slots[i], 2) for i in range(8)},
+        "slot_launches": {names[i]: int(cnt_slots[i]) for i in range(8)},
         "dominant_slot": names[dom],
     }
 

@@ -111,31 +111,34 @@ void launch_gram(const ColList<T>& X, const ColList<T>& Y, int64_t n, int fp32, 
 }
 
 // out[row, c] = sum_a src_a[row] * W[a, c]   (c < ncols, read on the device)
-template <class T, class Cm>
+// KC: accumulators per row, a multiple of 8 >= ncols_max (the recycle dimension)
+template <class T, class Cm, int KC>
 __global__ void __launch_bounds__(256) k_combine(ColList<T> src, const zd* W, int ldw, const int* ncols_dev,
                                                  int ncols_max, T* out, int ldo, int64_t n) {
   extern __shared__ unsigned char smraw[];
-  Cm* Ws = reinterpret_cast<Cm*>(smraw);   // src.m x KMAX
+  Cm* Ws = reinterpret_cast<Cm*>(smraw);   // src.m x KC
   const int nc = min(*ncols_dev, ncols_max);
-  for (int e = threadIdx.x; e < src.m * KMAX; e += blockDim.x) {
-    const int a = e / KMAX, c = e % KMAX;
+  for (int e = threadIdx.x; e < src.m * KC; e += blockDim.x) {
+    const int a = e / KC, c = e % KC;
     Ws[e] = c < nc ? from_zd<Cm>(W[a * ldw + c]) : Cm(0);
   }
   __syncthreads();
   for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x) {
-    Cm acc[KMAX];
+    Cm acc[KC];
 #pragma unroll
-    for (int c = 0; c < KMAX; ++c) acc[c] = Cm(0);
+    for (int c = 0; c < KC; ++c) acc[c] = Cm(0);
+#pragma unroll 4
     for (int a = 0; a < src.m; ++a) {
       const ColSrc<T> sc = src.c[a];
       const Cm xv = cvt<Cm>(sc.p[row * sc.ld]);
-      const Cm* w = Ws + a * KMAX;
+      const Cm* w = Ws + a * KC;
 #pragma unroll
-      for (int c = 0; c < KMAX; ++c) acc[c] += xv * w[c];
+      for (int c = 0; c < KC; ++c) acc[c] += xv * w[c];
     }
     T* o = out + row * ldo;
-    for (int c = 0; c < nc; ++c) o[c] = cvt<T>(acc[c]);
-    for (int c = nc; c < ldo; ++c) o[c] = T(0);
+#pragma unroll
+    for (int c = 0; c < KC; ++c)   // constant indices keep acc in registers (ldo <= KC)
+      if (c < ldo) o[c] = c < nc ? cvt<T>(acc[c]) : T(0);
   }
 }
 
@@ -145,38 +148,46 @@ void launch_combine(const ColList<T>& src, const zd* W, int ldw, const int* ncol
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
   // src.m <= MMAX + 2 columns; complex FP64 coefficients can exceed the 48 KB default
   const int maxsm = (MMAX + 2) * KMAX * (int)sizeof(T);
-  if (fp32) {
-    typedef typename comp_of<T, true>::type Cm;
-    cudaFuncSetAttribute(k_combine<T, Cm>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
-    k_combine<T, Cm><<<grid, 256, src.m * KMAX * sizeof(Cm), s>>>(src, W, ldw, ncols_dev, ncols_max, out, ldo, n);
-  } else {
-    cudaFuncSetAttribute(k_combine<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
-    k_combine<T, T><<<grid, 256, src.m * KMAX * sizeof(T), s>>>(src, W, ldw, ncols_dev, ncols_max, out, ldo, n);
+#define RB_COMB(KC)                                                                                           \
+  if (fp32) {                                                                                                 \
+    typedef typename comp_of<T, true>::type Cm;                                                               \
+    cudaFuncSetAttribute(k_combine<T, Cm, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);           \
+    k_combine<T, Cm, KC><<<grid, 256, src.m * KC * sizeof(Cm), s>>>(src, W, ldw, ncols_dev, ncols_max, out, ldo, n); \
+  } else {                                                                                                    \
+    cudaFuncSetAttribute(k_combine<T, T, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);            \
+    k_combine<T, T, KC><<<grid, 256, src.m * KC * sizeof(T), s>>>(src, W, ldw, ncols_dev, ncols_max, out, ldo, n); \
   }
+  if (ncols_max <= 8) { RB_COMB(8) }
+  else if (ncols_max <= 16) { RB_COMB(16) }
+  else if (ncols_max <= 24) { RB_COMB(24) }
+  else { RB_COMB(32) }
+#undef RB_COMB
 }
 
 // in-place B[row, 0..kout) <- sum_{a < kin} B[row, a] N[a, c]
-template <class T, class Cm>
+template <class T, class Cm, int KC>
 __global__ void __launch_bounds__(256) k_rotate(T* B, int ld, const zd* Nmat, const int* kin_dev, const int* kout_dev,
                                                 int kmax, int64_t n) {
-  __shared__ Cm Ns[KMAX * KMAX];
+  __shared__ Cm Ns[KC * KC];
   const int kin = min(*kin_dev, kmax), kout = min(*kout_dev, kmax);
-  for (int e = threadIdx.x; e < KMAX * KMAX; e += blockDim.x) {
-    const int a = e / KMAX, c = e % KMAX;
+  for (int e = threadIdx.x; e < KC * KC; e += blockDim.x) {
+    const int a = e / KC, c = e % KC;
     Ns[e] = (a < kin && c < kout) ? from_zd<Cm>(Nmat[a * KMAX + c]) : Cm(0);
   }
   __syncthreads();
   for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x) {
     T* b = B + row * ld;
-    Cm acc[KMAX];
+    Cm acc[KC];
 #pragma unroll
-    for (int c = 0; c < KMAX; ++c) acc[c] = Cm(0);
+    for (int c = 0; c < KC; ++c) acc[c] = Cm(0);
     for (int a = 0; a < kin; ++a) {
       const Cm xv = cvt<Cm>(b[a]);
 #pragma unroll
-      for (int c = 0; c < KMAX; ++c) acc[c] += xv * Ns[a * KMAX + c];
+      for (int c = 0; c < KC; ++c) acc[c] += xv * Ns[a * KC + c];
     }
-    for (int c = 0; c < ld; ++c) b[c] = c < kout ? cvt<T>(acc[c]) : T(0);
+#pragma unroll
+    for (int c = 0; c < KC; ++c)   // constant indices keep acc in registers (ld <= KC)
+      if (c < ld) b[c] = c < kout ? cvt<T>(acc[c]) : T(0);
   }
 }
 
@@ -184,14 +195,20 @@ template <class T>
 void launch_rotate(T* B, int ld, const zd* Nmat, const int* kin_dev, const int* kout_dev, int kmax, int64_t n,
                    int fp32, cudaStream_t s) {
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
-  if (fp32)
-    k_rotate<T, typename comp_of<T, true>::type><<<grid, 256, 0, s>>>(B, ld, Nmat, kin_dev, kout_dev, kmax, n);
-  else
-    k_rotate<T, T><<<grid, 256, 0, s>>>(B, ld, Nmat, kin_dev, kout_dev, kmax, n);
+#define RB_ROT(KC)                                                                                         \
+  if (fp32)                                                                                                \
+    k_rotate<T, typename comp_of<T, true>::type, KC><<<grid, 256, 0, s>>>(B, ld, Nmat, kin_dev, kout_dev, kmax, n); \
+  else                                                                                                     \
+    k_rotate<T, T, KC><<<grid, 256, 0, s>>>(B, ld, Nmat, kin_dev, kout_dev, kmax, n);
+  if (kmax <= 8) { RB_ROT(8) }
+  else if (kmax <= 16) { RB_ROT(16) }
+  else if (kmax <= 24) { RB_ROT(24) }
+  else { RB_ROT(32) }
+#undef RB_ROT
 }
 
 // out[row, c] = (Op U)[row, c]  for c < ncols; Op = A (adjoint = 0) or Op^H (adjoint = 1)
-template <class V, class T, class Cm>
+template <class V, class T, class Cm, int KC>
 __global__ void __launch_bounds__(256) k_spmm(OpArgs<V> op, int adjoint, const T* U, int ldu, const int* ncols_dev,
                                               int ncols_max, T* out) {
   const int nc = min(*ncols_dev, ncols_max);
@@ -200,20 +217,22 @@ __global__ void __launch_bounds__(256) k_spmm(OpArgs<V> op, int adjoint, const T
   const V* va = adjoint ? op.tva : op.va;
   Cm sh = from_zd<Cm>(zd(op.sh_re, adjoint ? -op.sh_im : op.sh_im));
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += gridDim.x * blockDim.x) {
-    Cm acc[KMAX];
+    Cm acc[KC];
 #pragma unroll
-    for (int c = 0; c < KMAX; ++c) acc[c] = Cm(0);
+    for (int c = 0; c < KC; ++c) acc[c] = Cm(0);
     for (int e = rp[row]; e < rp[row + 1]; ++e) {
       const Cm a = cvt<Cm>(va[e]);
       const T* u = U + (int64_t)ci[e] * ldu;
 #pragma unroll
-      for (int c = 0; c < KMAX; ++c)
+      for (int c = 0; c < KC; ++c)
         if (c < nc) acc[c] += a * cvt<Cm>(u[c]);
     }
     T* o = out + (int64_t)row * ldu;
     const T* ur = U + (int64_t)row * ldu;
-    for (int c = 0; c < ldu; ++c) {
-      Cm v = acc[c < KMAX ? c : 0];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      if (c >= ldu) break;
+      Cm v = acc[c];
       if (op.has_shift) v = sh * cvt<Cm>(ur[c]) - v;
       o[c] = c < nc ? cvt<T>(v) : T(0);
     }
@@ -224,8 +243,18 @@ template <class V, class T>
 void launch_spmm(const OpArgs<V>& op, int adjoint, const T* U, int ldu, const int* ncols_dev, int ncols_max, T* out,
                  int fp32, cudaStream_t s) {
   const int grid = std::max(1, std::min((op.n + 255) / 256, 152 * 8));
-  (void)fp32;
-  k_spmm<V, T, T><<<grid, 256, 0, s>>>(op, adjoint, U, ldu, ncols_dev, ncols_max, out);
+  // fp32: per-cycle C_j = A U_j in FP32 arithmetic (it feeds only the FP32 Grams and SVD of
+  // the refreshes; the system start forms C = A U in FP64)
+#define RB_SPMM(KC)                                                                                          \
+  if (fp32)                                                                                                  \
+    k_spmm<V, T, typename comp_of<T, true>::type, KC><<<grid, 256, 0, s>>>(op, adjoint, U, ldu, ncols_dev, ncols_max, out); \
+  else                                                                                                       \
+    k_spmm<V, T, T, KC><<<grid, 256, 0, s>>>(op, adjoint, U, ldu, ncols_dev, ncols_max, out);
+  if (ldu <= 8) { RB_SPMM(8) }
+  else if (ldu <= 16) { RB_SPMM(16) }
+  else if (ldu <= 24) { RB_SPMM(24) }
+  else { RB_SPMM(32) }
+#undef RB_SPMM
 }
 
 template <class Tfrom, class Tto>

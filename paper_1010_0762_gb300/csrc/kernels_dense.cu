@@ -1013,7 +1013,7 @@ __device__ __forceinline__ bool jacobi_rot(double app, double aqq, zd apq, doubl
 }
 
 // Block-wide one-sided Jacobi sweeps on the k x k column-major A (V accumulates the right
-// rotations), round-robin (circle) pair ordering, warp w handles pairs w, w + 8, ...  A pair is
+// rotations), round-robin (circle) pair ordering, warp w handles pairs w, w + nwarps, ...  A pair is
 // converged when |a^H b|^2 <= tol2 |a|^2 |b|^2.  Returns the sweeps run.
 template <class C, class Rl>
 __device__ int jacobi_sweeps(C* A, C* V, int k, int max_sweeps, Rl tol2, int* s_rot) {
@@ -1065,7 +1065,7 @@ __device__ int jacobi_sweeps(C* A, C* V, int k, int max_sweeps, Rl tol2, int* s_
   return sweep;
 }
 
-__global__ void __launch_bounds__(256) k_svd(int real_path, const int* k_dev, int kmax, const zd* S2, double svd_tol,
+__global__ void __launch_bounds__(512) k_svd(int real_path, const int* k_dev, int kmax, const zd* S2, double svd_tol,
                                              zd* Nmat, zd* Mmat, double* sigma, int* p_dev, double* Dc_dev,
                                              int* status) {
   extern __shared__ unsigned char smraw[];
@@ -1185,7 +1185,7 @@ void launch_dense_svd(int real_path, const int* k_dev, int kmax, const zd* S, co
     cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  k_svd<<<1, 256, smem, s>>>(real_path, k_dev, kmax, S, svd_tol, Nmat, Mmat, sigma, p_dev, Dc_dev, status_dev);
+  k_svd<<<1, 512, smem, s>>>(real_path, k_dev, kmax, S, svd_tol, Nmat, Mmat, sigma, p_dev, Dc_dev, status_dev);
 }
 
 template void launch_dense_refresh<double>(const RefreshInfo&, DevState*, const double*, zd*, zd*, zd*, int, double*,
