@@ -5,12 +5,13 @@
 //    scalings v_m = r_{m-1}/||r_{m-1}||, vt_m = rt_{m-1}/(v_m, rt_{m-1}) applied to the raw
 //    Gram, and the pencil L = Ht^H (Psit^H Psi) H, R = Ht^H (Psit^H Phi) of eq.
 //    (finalGenEigValue).  Many blocks (plain dense products of order <= 130).
-//  * k_eig: one block.  M = R^{-1} L (complex LU with partial pivoting), Householder
-//    reduction to Hessenberg form, shifted QR to Schur form M = Q T Q^H, selection of the
-//    eigenvalues closest to the origin, right eigenvectors W = Q y and left eigenvectors of
-//    the pencil Wt = R^{-H} Q yl (y, yl eigenvectors of the triangular T).
+//  * k_eig_cl / k_eig_h / k_eig_c: the eigen pipeline of the pencil (L, R) -- FP64 Gauss-Jordan
+//    and Householder reduction on a thread-block cluster, FP32 QR eigenvalues as shifts, FP64
+//    inverse iteration per candidate, selection of the eigenvalues closest to the origin with
+//    their right and left eigenvectors (described in full above k_eig_cl).
 //  * k_svd: one block.  One-sided (Hestenes) Jacobi SVD of Ct_j^H C_j after unit-norm column
-//    scaling (Section 4.3, eq. (equationSVD)); truncation at svd_tol; rotation coefficients.
+//    scaling (Section 4.3, eq. (equationSVD)): FP32 sweeps, FP64 Newton-Schulz
+//    re-orthonormalisation, FP64 polish sweeps; truncation at svd_tol; rotation coefficients.
 #include <algorithm>
 
 #include <cooperative_groups.h>
@@ -375,9 +376,10 @@ __device__ bool qr_eigs_warp_f32(zf* T, int m, int ld, int* dbg) {
         T[row + (k + 1) * ld] = cs * q - sn * p;
       }
       __syncwarp();
+      // the bulge entry is read again only by the next sweep: no barrier needed here
       if (k > lo && lane == 0) T[k + 1 + (k - 1) * ld] = zf(0.f, 0.f);
-      __syncwarp();
     }
+    __syncwarp();
   }
   return true;
 }
