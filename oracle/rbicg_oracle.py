@@ -585,8 +585,9 @@ def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, 
     recycle=False gives plain BiCG on every pair (RBiCG with an empty recycle space).
     guard > 0 reproduces the CUDA library's stagnation guard, which is NOT part of the paper:
     a pair solved with a recycle space that has not converged after guard x (iterations of
-    the last pair solved without one) iterations applies step 7 to its iterate and continues
-    from it as plain BiCG (Algorithm 2 with an empty recycle space).
+    the last pair solved without one) iterations, rounded up to whole cycles of s, applies
+    step 7 to its iterate and continues from it as plain BiCG (Algorithm 2 with an empty
+    recycle space).
     restarts > 0 reproduces the library's restart after a breakdown (also not in the paper): a
     pair that ends in a BiCG breakdown (rho or (pt, q) below the relative threshold) continues
     from its iterate as plain BiCG, at most `restarts` times.
@@ -607,7 +608,9 @@ def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, 
             rec = biorth_recycle(A, Uc, Utc, svd_tol)
         limit = max_itn
         if guard > 0 and rec is not None and rec[0].shape[1] > 0 and last_plain > 0:
-            limit = min(max_itn, int(guard * last_plain))
+            # the library tests the guard when a cycle of s iterations ends, so the recycled leg
+            # runs to the first multiple of s at or above guard x last_plain
+            limit = min(max_itn, -(-int(guard * last_plain) // s) * s)
         res = rbicg_pair(A, b, bt, x0, xt0, recycle=rec, k=k, s=s, tol=tol, max_itn=limit,
                          svd_tol=svd_tol, seed=seed + j, refresh=recycle)
         res.hist["fallback"] = False
