@@ -91,6 +91,21 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ------------------------------------------------------------------ replicas
+def max_over_ranks(value, dist, device):
+    """The job's timed region ends with its slowest rank: max of `value` over all ranks."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, units_per_rank, ms):
+    """Whole-job throughput of `world` independent replicas that each processed units_per_rank
+    units, with the job's time ms (max over ranks)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 # ------------------------------------------------------------------ GPU arm
 def algorithmic_phase1(n, nnz, k, w=8):
     """Algorithmic flops and bytes of one phase-1 launch (dual SpMV with on-the-fly p update and
@@ -195,16 +210,14 @@ def gpu_arm(a):
             R.lib.rbicg_profile_columns(S.h, C.byref(cols))
             prof = (list(ms), list(cnt), cols.value)
         if world > 1:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+            total_ms = max_over_ranks(total_ms, dist, "cuda")
         return total_ms, results, ck, prof, launches
 
     # --- plain FP64 RBiCG (the configuration's own form) ---
     S = R.Solver(n, k=a.k, s=a.s, tol=a.tol)
     ms64, res64, clocks, prof, launches = timed(S, a.steps, a.warmup, profile=True)
     pairs_done = a.pairs * a.steps
-    value = world * pairs_done / (ms64 * 1e-3)
+    value = replica_value(world, pairs_done, ms64)
     per_step = res64[:a.pairs]
     iters = [r["iters"] for r in per_step]
     ok = all(r["status"] in (R.OK, R.RECYCLE_EMPTY) for r in res64)
@@ -500,7 +513,9 @@ def reference_arm(a):
     from oracle import rbicg_oracle as O
     pr = seq[0]
     n = pr["A"].n
-    full = O.rbicg_pair(pr["A"], pr["b"], pr["bt"], np.zeros(n), np.zeros(n), None, k=a.k, s=a.s, tol=a.tol)
+    # pair 0 has no recycle space yet, so its RBiCG iteration count is plain BiCG's (Algorithm 2
+    # with empty U reduces to Algorithm 1); the BiCG oracle gives it without the refresh work
+    full = O.bicg(pr["A"], pr["b"], pr["bt"], np.zeros(n), np.zeros(n), a.tol, 20000)
     n_ref = full.iters
     its = 2 * a.s
     for i in range(a.warmup):
