@@ -384,6 +384,113 @@ __device__ bool qr_eigs_warp_f32(zf* T, int m, int ld, int* dbg) {
   return true;
 }
 
+// Block-wide (all threads): eigenvalues of the Hessenberg H (FP32, ld) by implicit QR with
+// several shifts per sweep, each chased as its own bulge by one warp, the bulges three rows
+// apart and advanced in lockstep: step t moves bulge w to rotation k = lo + t - 3 w.  Within a
+// step the bulges' row (left) updates touch disjoint row pairs and their column (right) updates
+// disjoint column pairs, and left and right rotations commute, so a sweep equals the sweeps of
+// the single shifts one after another while taking (hi - lo) + 3 (nb - 1) steps instead of
+// nb (hi - lo).  Shifts: eigenvalues of the trailing 2 x 2 blocks, nearest ones first; an
+// exceptional shift after 10 sweeps without deflation.  Returns false (with diagnostics) on a
+// non-finite entry or after 60 m sweeps.
+__device__ bool qr_eigs_block_f32(zf* T, int m, int ld, int* dbg) {
+  __shared__ int s_lo, s_hi, s_nb, s_fail;
+  __shared__ zf s_mu[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int NB = nwarp < 8 ? nwarp : 8;
+  const float eps = 1.1920929e-07f;
+  int stall = 0, total = 0;   // thread 0's counters
+  if (threadIdx.x == 0) { s_hi = m - 1; s_fail = 0; }
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int hi = s_hi, lo = hi;
+      for (;;) {
+        if (hi <= 0) break;
+        lo = hi;
+        while (lo > 0) {
+          const float sub = cabs1f_(T[lo + (lo - 1) * ld]);
+          const float dsum = cabs1f_(T[lo + lo * ld]) + cabs1f_(T[lo - 1 + (lo - 1) * ld]);
+          if (sub <= eps * (dsum > 0.f ? dsum : 1.f)) { T[lo + (lo - 1) * ld] = zf(0.f, 0.f); break; }
+          --lo;
+        }
+        if (lo == hi) { --hi; stall = 0; continue; }
+        break;
+      }
+      s_hi = hi;
+      s_lo = lo;
+      if (hi > 0) {
+        ++stall;
+        const zf dd = T[hi + hi * ld], cc = T[hi + (hi - 1) * ld];
+        if (!isfinite(dd.re) || !isfinite(dd.im) || !isfinite(cc.re) || !isfinite(cc.im)) {
+          dbg[0] = 3; dbg[1] = lo; dbg[2] = hi; dbg[3] = stall; dbg[4] = total;
+          s_fail = 1;
+        } else if (++total > 60 * m) {
+          dbg[0] = 2; dbg[1] = lo; dbg[2] = hi; dbg[3] = stall; dbg[4] = total;
+          s_fail = 1;
+        }
+        const int w = hi - lo + 1;
+        int nb = (w - 1) / 3 + 1;
+        if (nb > NB) nb = NB;
+        if (w <= 4) nb = 1;
+        int cnt = 0;
+        for (int r = hi; cnt < nb && r - 1 >= lo; r -= 2) {
+          const zf a = T[r - 1 + (r - 1) * ld], b = T[r - 1 + r * ld], c = T[r + (r - 1) * ld], d = T[r + r * ld];
+          const zf half = (a + d) * 0.5f;
+          const zf disc = half * half - (a * d - b * c);
+          const float rdisc = cabsf_(disc);
+          // radicands clamped: hypotf's rounding can put |disc| + Re(disc) below zero
+          float sr = sqrtf(fmaxf(0.f, 0.5f * (rdisc + disc.re))), si = sqrtf(fmaxf(0.f, 0.5f * (rdisc - disc.re)));
+          if (disc.im < 0.f) si = -si;
+          const zf l1 = half + zf(sr, si), l2 = half - zf(sr, si);
+          const bool first1 = cabsf_(l1 - d) < cabsf_(l2 - d);
+          s_mu[cnt++] = first1 ? l1 : l2;
+          if (cnt < nb) s_mu[cnt++] = first1 ? l2 : l1;
+        }
+        while (cnt < nb) s_mu[cnt++] = T[hi + hi * ld];
+        if (stall % 11 == 10) s_mu[0] = T[hi + hi * ld] + zf(cabsf_(T[hi + (hi - 1) * ld]) * 0.75f, 0.f);
+        s_nb = nb;
+      }
+    }
+    __syncthreads();
+    if (s_fail) return false;
+    const int hi = s_hi;
+    if (hi <= 0) break;
+    const int lo = s_lo, nb = s_nb;
+    const int nsteps = (hi - lo) + 3 * (nb - 1);
+    for (int t = 0; t < nsteps; ++t) {
+      const int k = lo + t - 3 * warp;
+      const bool active = warp < nb && k >= lo && k < hi;
+      float cs = 1.f;
+      zf sn = zf(0.f, 0.f);
+      if (active) {
+        if (k == lo) givens_f(T[lo + lo * ld] - s_mu[warp], T[lo + 1 + lo * ld], &cs, &sn);
+        else givens_f(T[k + (k - 1) * ld], T[k + 1 + (k - 1) * ld], &cs, &sn);
+        __syncwarp();   // all lanes have read the rotation's defining entries
+        const int c0 = k > lo ? k - 1 : lo;
+        for (int col = c0 + lane; col <= hi; col += 32) {
+          const zf p = T[k + col * ld], q = T[k + 1 + col * ld];
+          T[k + col * ld] = cs * p + sn * q;
+          T[k + 1 + col * ld] = cs * q - conjg(sn) * p;
+        }
+      }
+      __syncthreads();   // every bulge's row update before any column update
+      if (active) {
+        const int r1 = k + 2 < hi ? k + 2 : hi;
+        for (int row = lo + lane; row <= r1; row += 32) {
+          const zf p = T[row + k * ld], q = T[row + (k + 1) * ld];
+          T[row + k * ld] = cs * p + conjg(sn) * q;
+          T[row + (k + 1) * ld] = cs * q - sn * p;
+        }
+        __syncwarp();
+        if (k > lo && lane == 0) T[k + 1 + (k - 1) * ld] = zf(0.f, 0.f);
+      }
+      __syncthreads();
+    }
+  }
+  return true;
+}
+
 struct EigInts {   // integer area of the dense work buffer
   int* piv; int* sel; int* pair; int* units; int* cols; int* ncand;
 };
@@ -611,8 +718,8 @@ k_eig_cl(RefreshInfo f, DevState* st, zd* work, int has_R, int m) {
   __shared__ int s_ok;
   if (tid == 0) s_ok = 1;
   __syncthreads();
-  if (tid < 32) {
-    const bool ok = qr_eigs_warp_f32(H, m, ld, st->dbg);
+  {
+    const bool ok = qr_eigs_block_f32(H, m, ld, st->dbg);
     if (tid == 0 && !ok) s_ok = 0;
   }
   __syncthreads();
