@@ -98,7 +98,7 @@ typedef struct {
                               (pt, q) below 1e-14 of the norms) applies step 7 and continues from
                               its iterate as plain BiCG, at most this many times */
   int grid_blocks;         /* blocks of 256 threads per iteration-phase launch (0: the default,
-                              min(ceil(n / 256), 8 x SMs)); rbicg_autotune picks one by timed
+                              min(ceil(n / 256), 3 x SMs)); rbicg_autotune picks one by timed
                               trials.  Reductions follow the block partition, so results are
                               reproducible for a given value. */
 } rbicg_params;

@@ -11,6 +11,27 @@ namespace rb {
 // ------------------------------------------------------------------------------------
 // Complex numbers (interleaved re, im; layout-compatible with C99 / numpy complex).
 // ------------------------------------------------------------------------------------
+// A product rounded on its own (never fused into a neighbouring add), and a fused
+// multiply-add.  The complex products below say which of their two products is fused and which
+// is rounded, so that every kernel that inlines them -- a solve's kernel and its batched twin
+// among them -- computes the same bits.
+RB_HD double mul_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+RB_HD float mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+RB_HD double fmar(double a, double b, double c) { return fma(a, b, c); }
+RB_HD float fmar(float a, float b, float c) { return fmaf(a, b, c); }
+
 template <class R>
 struct alignas(2 * sizeof(R)) cplx {
   R re, im;
@@ -24,7 +45,7 @@ template <class R> RB_HD cplx<R> operator+(cplx<R> a, cplx<R> b) { return {a.re 
 template <class R> RB_HD cplx<R> operator-(cplx<R> a, cplx<R> b) { return {a.re - b.re, a.im - b.im}; }
 template <class R> RB_HD cplx<R> operator-(cplx<R> a) { return {-a.re, -a.im}; }
 template <class R> RB_HD cplx<R> operator*(cplx<R> a, cplx<R> b) {
-  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+  return {fmar(a.re, b.re, -mul_rn(a.im, b.im)), fmar(a.re, b.im, mul_rn(a.im, b.re))};
 }
 template <class R> RB_HD cplx<R> operator*(R a, cplx<R> b) { return {a * b.re, a * b.im}; }
 template <class R> RB_HD cplx<R> operator*(cplx<R> b, R a) { return {a * b.re, a * b.im}; }
@@ -51,7 +72,7 @@ template <class R> RB_HD cplx<R> conjg(cplx<R> a) { return {a.re, -a.im}; }
 
 RB_HD double abs2(double a) { return a * a; }
 RB_HD float abs2(float a) { return a * a; }
-template <class R> RB_HD R abs2(cplx<R> a) { return a.re * a.re + a.im * a.im; }
+template <class R> RB_HD R abs2(cplx<R> a) { return fmar(a.re, a.re, mul_rn(a.im, a.im)); }
 
 RB_HD double absval(double a) { return fabs(a); }
 template <class R> RB_HD R absval(cplx<R> a) { return hypot(a.re, a.im); }
@@ -67,7 +88,7 @@ template <class R> RB_HD R imag_of(cplx<R> a) { return a.im; }
 RB_HD double cmul(double a, double b) { return a * b; }
 RB_HD float cmul(float a, float b) { return a * b; }
 template <class R> RB_HD cplx<R> cmul(cplx<R> a, cplx<R> b) {
-  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+  return {fmar(a.re, b.re, mul_rn(a.im, b.im)), fmar(a.re, b.im, -mul_rn(a.im, b.re))};
 }
 
 RB_HD bool finite_of(double a) { return isfinite(a); }
@@ -110,6 +131,10 @@ __device__ __forceinline__ cplx<double> shfl_down(cplx<double> v, int o) {
 __device__ __forceinline__ float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ cplx<float> shfl_down(cplx<float> v, int o) {
   return {__shfl_down_sync(0xffffffffu, v.re, o), __shfl_down_sync(0xffffffffu, v.im, o)};
+}
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ cplx<double> shfl_xor(cplx<double> v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.re, o), __shfl_xor_sync(0xffffffffu, v.im, o)};
 }
 template <class A>
 __device__ __forceinline__ A warp_sum(A v) {

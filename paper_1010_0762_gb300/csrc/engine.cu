@@ -219,9 +219,11 @@ struct Solver : SolverBase {
     RB_CUDA(cudaEventCreateWithFlags(&ev_g0, cudaEventDisableTiming));
     RB_CUDA(cudaEventCreateWithFlags(&ev_g1, cudaEventDisableTiming));
     const int sms = num_sms();
+    // default: one wave of the recycling phase-1 kernel (3 resident blocks per SM); every block
+    // walks an equal share of whole 32-row chunks, so each SM gets the same rows
     grid = prm.grid_blocks > 0
                ? (int)std::min<int64_t>(prm.grid_blocks, std::max<int64_t>(1, (n + NTHREADS - 1) / NTHREADS))
-               : (int)std::max<int64_t>(1, std::min<int64_t>((n + NTHREADS - 1) / NTHREADS, (int64_t)sms * 8));
+               : (int)std::max<int64_t>(1, std::min<int64_t>((n + NTHREADS - 1) / NTHREADS, (int64_t)sms * 3));
     gram_grid = 2 * sms;
     const int64_t ldv = ((n + 31) / 32) * 32;   // padded vector stride (256-byte aligned slots)
     ring = dmalloc<T>(ldv * R);
@@ -239,8 +241,7 @@ struct Solver : SolverBase {
     ring_ld = ldv;
     st = dmalloc<DevState>(1);
     RB_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
-    const size_t part_elems =
-        std::max<size_t>((size_t)grid * (2 * KMAX + 2), (size_t)gram_grid * 64 * 64);
+    const size_t part_elems = std::max<size_t>(part_elems_for(grid), (size_t)gram_grid * 64 * 64);
     part = dmalloc<A>(part_elems);
     gpart = dmalloc<A>((size_t)gram_grid * 64 * 64);
     G = dmalloc<A>((size_t)GRAM_MAXCOLS * GRAM_MAXCOLS);
@@ -550,9 +551,11 @@ struct Solver : SolverBase {
       int pp = prof->begin(0, s);
       launch_phase1<V, T>(op, run.v, st, part, run.kt, grid, s);
       prof->end(pp, 1, s);
-      pp = prof->begin(1, s);
-      launch_phase2<V, T>(op, run.v, st, part, run.kt, grid, s);
-      prof->end(pp, 1, s);
+      if (run.kt > 0) {   // without a recycle space phase 1 also finishes alpha
+        pp = prof->begin(1, s);
+        launch_phase2<V, T>(op, run.v, st, part, run.kt, grid, s);
+        prof->end(pp, 1, s);
+      }
       pp = prof->begin(2, s);
       launch_phase3<V, T>(op, run.v, st, part, grid, s);
       prof->end(pp, 1, s);
@@ -563,7 +566,7 @@ struct Solver : SolverBase {
   // be the legacy default stream, which cannot be captured), ordered after and before the work
   // of s by two events.  If capture or instantiation fails, the cycle runs as plain launches.
   void launch_cycle(int todo) {
-    count(3 * todo);
+    count((run.kt > 0 ? 3 : 2) * todo);
     if (!use_graphs || prof->on || todo <= 0) { launch_phases(todo); return; }
     if (!cyc_exec || cyc_todo != todo || cyc_kt != run.kt || memcmp(&cyc_v, &run.v, sizeof(cyc_v)) != 0 ||
         memcmp(&cyc_op, &op, sizeof(cyc_op)) != 0) {
@@ -1279,7 +1282,7 @@ static void op_spmv_project_impl(const rbicg_csr* A, const void* r, const void* 
   DevState* st = dmalloc<DevState>(1);
   RB_CUDA(cudaMemcpyAsync(st, &hst, sizeof hst, cudaMemcpyHostToDevice, s));
   const int grid = std::max(1, std::min((op.n + NTHREADS - 1) / NTHREADS, num_sms() * 8));
-  Acc* part = dmalloc<Acc>((size_t)grid * (2 * KMAX + 2));
+  Acc* part = dmalloc<Acc>(part_elems_for(grid));
   VecArgs<T> v{};
   v.n = A->n;
   v.ring = const_cast<T*>(reinterpret_cast<const T*>(r));
@@ -1580,10 +1583,10 @@ static void engine_step_kind(rbicg_engine e, int kind) {
     RB_CUDA(cudaMemcpyAsync(dba, hb, sizeof(BatchArgs<V, T>), cudaMemcpyHostToDevice, e->s));
     for (int t = 0; t < todo; ++t) {
       launch_phase1_batch<V, T>(dba, blocks, ld, e->s);
-      launch_phase2_batch<V, T>(dba, blocks, kt, e->s);
+      if (kt > 0) launch_phase2_batch<V, T>(dba, blocks, kt, e->s);
       launch_phase3_batch<V, T>(dba, blocks, e->s);
     }
-    launched += 3 * todo;
+    launched += (kt > 0 ? 3 : 2) * todo;
   }
   as_solver<V, T>(e->active[idx[0]])->count(launched);
   for (int i : idx) as_solver<V, T>(e->active[i])->fetch_async();
@@ -1817,7 +1820,7 @@ extern "C" rbicg_status rbicg_autotune(const rbicg_params* params, rbicg_dtype d
   const int sms = num_sms();
   const int64_t cap = std::max<int64_t>(1, (n + NTHREADS - 1) / NTHREADS);
   std::vector<int> cand;
-  for (int f : {1, 2, 4, 8, 16}) {
+  for (int f : {1, 2, 3, 4, 6, 8, 16}) {
     const int g = (int)std::min<int64_t>(cap, (int64_t)f * sms);
     if (std::find(cand.begin(), cand.end(), g) == cand.end()) cand.push_back(g);
   }

@@ -10,6 +10,18 @@ constexpr int MMAX = 80;          // largest pencil order (k + s)
 constexpr int HR = 2 * SMAX + 4;  // history ring length (iteration scalars)
 constexpr int NTHREADS = 256;     // threads per block of the streaming kernels
 constexpr double BREAKDOWN_EPS = 1e-14;
+constexpr int GMAX = 1024;        // block groups of the two-level grid reduction (iteration kernels)
+constexpr int RCNT = 2 * KMAX + 2;  // widest row of per-block partial sums
+
+// Blocks of one solve form groups of consecutive ids for the two-level grid reduction: 32 a
+// group, or more when the grid has more than 32 * GMAX blocks.
+RB_HD int group_size(int nblk) {
+  return nblk <= 32 * GMAX ? 32 : ((nblk + GMAX - 1) / GMAX + 31) / 32 * 32;
+}
+RB_HD int group_count(int nblk) { return (nblk + group_size(nblk) - 1) / group_size(nblk); }
+// Elements of the per-solve partial-sum buffer of the iteration kernels: one row per block and
+// one per group, RCNT wide.
+inline size_t part_elems_for(int nblk) { return ((size_t)nblk + group_count(nblk)) * RCNT; }
 
 // done codes (DevState::done)
 enum { RUNNING = 0, DONE_CONVERGED = 1, DONE_BREAK_RHO = 2, DONE_BREAK_PQ = 3, DONE_MAXIT = 4,
@@ -40,7 +52,8 @@ struct DevState {
   int refresh_ok;
   int nonfinite;
   int dbg[8];                    // diagnostics of the last dense failure (stage, window, counts)
-  unsigned int cnt[8];           // last-block counters
+  unsigned int cnt[8];           // last-block counters (one-level reductions)
+  unsigned int gcnt[GMAX + 1];   // group counters and the final counter of the two-level reduction
   zd zeta[KMAX], zetat[KMAX];    // zeta_i, zetat_i (Algorithm 2)
   zd zeta_c[KMAX], zetat_c[KMAX];
   zd coef[KMAX], coeft[KMAX];    // initial projection coefficients (eq. (minusXR))

@@ -12,6 +12,7 @@
 //   phase 3: x_i, xt_i, r_i, rt_i updates, rho_i = (rt_i, r_i), ||r_i||, ||rt_i||,
 //            stopping test, beta_i = rho_i / rho_{i-1}
 #include <algorithm>
+#include <cstdlib>
 
 #include "internal.cuh"
 
@@ -34,19 +35,63 @@ struct Blk {
 };
 
 // Returns true in every thread of the block that arrives last at `cnt` (after all other
-// blocks' partial writes are visible); the last block resets the counter.
+// blocks' partial writes are visible); the last block resets the counter.  The barrier orders
+// the block's writes before thread 0's fence, which publishes them before the arrival; the last
+// block's thread 0 fences again before its threads read the others' rows.
 __device__ __forceinline__ bool arrive_last(unsigned int* cnt, int nblk) {
   __shared__ int s_last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned int t = atomicAdd(cnt, 1u);
-    s_last = (t == (unsigned int)nblk - 1);
-    if (s_last) *cnt = 0u;
+    __threadfence();
+    const unsigned int t = atomicAdd(cnt, 1u);
+    const int last = t == (unsigned int)nblk - 1;
+    if (last) {
+      *cnt = 0u;
+      __threadfence();
+    }
+    s_last = last;
   }
   __syncthreads();
-  if (s_last) __threadfence();
   return s_last;
+}
+
+// Programmatic dependent launch.  A phase kernel launched with programmatic stream
+// serialization may be scheduled while the kernel before it in the stream finishes its
+// reduction tail; pdl_wait() holds it until that kernel has completed and its writes are
+// visible, so it comes before the first access to anything the previous kernel wrote.
+// pdl_release() lets the next kernel be scheduled once every block of this one has passed it.
+// Without that launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Block sums of three per-thread values with fewer FP64 adds than three shuffle trees: in each
+// warp a reduce-scatter butterfly (offset 16 splits the values between the lane halves, offset 8
+// between quarters, offsets 4, 2, 1 finish one value per group of 8 lanes: 6 adds a lane instead
+// of 15), then the warps' results in warp order.  Fixed order throughout.  out[0..2] (shared)
+// holds the totals on return; smem holds NTHREADS / 32 * 4 values.
+template <class A>
+__device__ void block_sum3(A v0, A v1, A v2, A* smem, A* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  const A z = A(0.0);
+  A k0 = h16 ? v2 : v0, k1 = h16 ? z : v1;
+  const A s0 = h16 ? v0 : v2, s1 = h16 ? v1 : z;
+  k0 += shfl_xor(s0, 16);
+  k1 += shfl_xor(s1, 16);
+  A r = h8 ? k1 : k0;
+  r += shfl_xor(h8 ? k0 : k1, 8);
+  r += shfl_xor(r, 4);
+  r += shfl_xor(r, 2);
+  r += shfl_xor(r, 1);
+  // lane 0: v0, lane 8: v1, lane 16: v2 (lane 24 holds the zero pad)
+  if ((lane & 7) == 0 && lane < 24) smem[warp * 4 + (lane >> 3)] = r;
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    A t = smem[threadIdx.x];
+    for (int w = 1; w < NTHREADS / 32; ++w) t += smem[w * 4 + threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();
 }
 
 // Sum part[b * cnt + c] over b = 0..G-1 for every column c (fixed order: lane-strided per
@@ -68,6 +113,100 @@ template <class A>
 __device__ void write_partials(A* vals, int cnt, A* smem, A* part, int bid) {
   block_sum_vec(vals, cnt, smem);
   if (threadIdx.x < cnt) part[(int64_t)bid * cnt + threadIdx.x] = smem[threadIdx.x];
+}
+
+// Rows [r0, r1) of block g of a solve: a contiguous range of whole 32-row chunks, the chunk
+// count split as evenly as it divides.  With a grid that is a multiple of the blocks resident
+// on the GPU, every SM then receives the same number of rows.
+__device__ __forceinline__ void block_rows(int n, Blk g, int& r0, int& r1) {
+  const int64_t nch = (n + 31) >> 5;
+  r0 = (int)((nch * g.id / g.n) << 5);
+  const int e = (int)((nch * (g.id + 1) / g.n) << 5);
+  r1 = e < n ? e : n;
+}
+
+// Sum CNT columns over `nrows` rows of `rows` (row stride CNT) in a fixed order: lane-strided
+// per warp, then the fixed shuffle tree.  out (shared) receives the CNT sums.
+template <class A, int CNT>
+__device__ void sum_rows(const A* rows, int nrows, A* out) {
+  constexpr int NW = NTHREADS / 32;
+  constexpr int CPW = (CNT + NW - 1) / NW;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  A acc[CPW];
+#pragma unroll
+  for (int u = 0; u < CPW; ++u) acc[u] = A(0.0);
+  for (int b = lane; b < nrows; b += 32) {
+#pragma unroll
+    for (int u = 0; u < CPW; ++u)
+      if (w + NW * u < CNT) acc[u] += ld_cg(rows + (int64_t)b * CNT + w + NW * u);
+  }
+#pragma unroll
+  for (int u = 0; u < CPW; ++u) {
+    const A t = warp_sum(acc[u]);
+    if (lane == 0 && w + NW * u < CNT) out[w + NW * u] = t;
+  }
+  __syncthreads();
+}
+
+// Deterministic two-level grid reduction of CNT values per block.  The blocks of a solve form
+// groups of consecutive ids (group_size); the last block of a group to arrive sums the group's
+// rows in id order, and the last group to finish sums the group rows in group order.  So the
+// result does not depend on arrival order, and the critical path after the last arrival is two
+// short L2 round trips instead of one block reading every block's row.  `tot` (shared) holds
+// this block's CNT totals on entry; the function returns true only in the block that finishes,
+// with the grand totals in `tot`.  part: g.n rows, then group_count(g.n) rows, CNT wide.
+template <class A, int CNT>
+__device__ bool grid_reduce(A* tot, A* part, unsigned int* ctr, Blk g) {
+  const int gs = group_size(g.n), ng = (g.n + gs - 1) / gs;
+  const int grp = g.id / gs, b0 = grp * gs;
+  const int gsz = g.n - b0 < gs ? g.n - b0 : gs;
+  A* gpart = part + (int64_t)g.n * CNT;
+  if (threadIdx.x < CNT) part[(int64_t)g.id * CNT + threadIdx.x] = tot[threadIdx.x];
+  if (!arrive_last(&ctr[grp], gsz)) return false;
+  sum_rows<A, CNT>(part + (int64_t)b0 * CNT, gsz, tot);
+  if (threadIdx.x < CNT) gpart[(int64_t)grp * CNT + threadIdx.x] = tot[threadIdx.x];
+  if (!arrive_last(&ctr[GMAX], ng)) return false;
+  sum_rows<A, CNT>(gpart, ng, tot);
+  return true;
+}
+
+// The three sums of one row that decide alpha_i: (pt_i, q_i), ||q_i||^2, ||pt_i||^2.
+template <class A, class T>
+__device__ __forceinline__ void alpha_terms(A& pq, A& nq, A& npt, T ptr, T q) {
+  pq += cmul(cvt<A>(ptr), cvt<A>(q));
+  nq += A((double)abs2(q));
+  npt += A((double)abs2(ptr));
+}
+
+// In the block that finished the (pt, q) reduction (tot = the three sums): alpha_i =
+// rho_{i-1} / (pt_i, q_i) with the finiteness and breakdown tests, then zeta_c += alpha zeta
+// and zetat_c += conj(alpha) zetat for the k recycle columns (Algorithm 2).
+template <class A>
+__device__ void finish_alpha(DevState* st, const A* tot, int i, int k) {
+  if (threadIdx.x == 0) {
+    const zd PQ = to_zd(tot[0]);
+    const double NQ = real_of(tot[1]), NPT = real_of(tot[2]);
+    if (!isfinite(PQ.re) || !isfinite(PQ.im) || !isfinite(NQ) || !isfinite(NPT)) {
+      st->done = DONE_NONFINITE;
+    } else if (absval(PQ) <= BREAKDOWN_EPS * sqrt(NQ) * sqrt(NPT)) {
+      st->done = DONE_BREAK_PQ;
+    } else {
+      const zd al = st->rho / PQ;
+      st->alpha = al;
+      st->h_alpha[i % HR] = al;
+    }
+  }
+  __syncthreads();
+  if (st->done) return;
+  if (threadIdx.x < k) {
+    const zd al = st->alpha;
+    const int c = threadIdx.x;
+    const zd zc = st->zeta[c], ztc = st->zetat[c];
+    st->zeta_c[c] += al * zc;
+    st->zetat_c[c] += conjg(al) * ztc;
+    st->h_zeta[i % HR][c] = zc;
+    st->h_zetat[i % HR][c] = ztc;
+  }
 }
 
 template <class T> struct shift_of {
@@ -100,6 +239,11 @@ template <> __device__ __forceinline__ bool finite_acc<zd>(zd v) { return isfini
 // multiple of 4, lane `lane` only ever meets the P = LD / gcd(LD, 32) <= 7 columns
 // (lane + 32 u) % LD, u < P, and keeps one accumulator per such column (slot u = t mod P).
 // The block then folds the slots back to columns in a fixed order.
+//
+// Without a recycle space (LD = 0) q_i = z_i, so phase 2 has nothing left but the (pt, q)
+// reduction; phase 1 does it and a plain iteration takes two launches.  Its rows are walked in
+// the order of phase 2 (thread t: rows r0 + t + 256 j), so alpha is the same bit for bit either
+// way (a request without recycle space in a batch with recycling requests runs both phases).
 // ------------------------------------------------------------------------------------
 constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
 
@@ -143,9 +287,10 @@ __device__ __forceinline__ void phase1_body(const OpArgs<V> op, const VecArgs<T>
   constexpr int LDA = LD > 0 ? LD : 4;
   constexpr int P = Slab<LDA>::P;
   __shared__ T zs[NW][32], zts[NW][32];
-  __shared__ A red[LD > 0 ? NW * 32 * P : 1];       // one side at a time
+  __shared__ A red[LD > 0 ? NW * 32 * P : NW * 4];  // one side at a time
   __shared__ A wpart[LD > 0 ? LDA * NW : 1];
   __shared__ A tot[2 * LDA];
+  pdl_wait();
   if (st->done) return;
   const int i = st->iter + 1;
   const T beta = from_zd<T>(st->beta), cbeta = conjg(beta);
@@ -162,11 +307,13 @@ __device__ __forceinline__ void phase1_body(const OpArgs<V> op, const VecArgs<T>
   T a1[P], a2[P];
 #pragma unroll
   for (int u = 0; u < P; ++u) { a1[u] = T(0); a2[u] = T(0); }
-  const int stride = g.n * blockDim.x;
-  for (int base = g.id * blockDim.x + warp * 32; base < op.n; base += stride) {
+  A pq = A(0.0), nq = A(0.0), npt = A(0.0);
+  int r0, r1;
+  block_rows(op.n, g, r0, r1);
+  for (int base = r0 + warp * 32; base < r1; base += NTHREADS) {
     const int row = base + lane;
     T z = T(0), zt = T(0);
-    if (row < op.n) {
+    if (row < r1) {
       const int e0 = op.rp[row], e1 = op.rp[row + 1];
       if (op.shared) {
         for (int e = e0; e < e1; ++e) {
@@ -192,12 +339,13 @@ __device__ __forceinline__ void phase1_body(const OpArgs<V> op, const VecArgs<T>
       if (op.has_shift) { z = sh * prow - z; zt = shc * ptrow - zt; }
       v.z[row] = z;
       v.zt[row] = zt;
+      if (LD == 0) alpha_terms(pq, nq, npt, ptrow, z);
     }
     if (LD > 0) {
       zs[warp][lane] = z;
       zts[warp][lane] = zt;
       __syncwarp();
-      const int nvalid = op.n - base < 32 ? op.n - base : 32;
+      const int nvalid = r1 - base < 32 ? r1 - base : 32;
       const T* __restrict__ ctb = v.Ct + (int64_t)base * LDA;
       const T* __restrict__ cb = v.C + (int64_t)base * LDA;
 #pragma unroll
@@ -212,7 +360,13 @@ __device__ __forceinline__ void phase1_body(const OpArgs<V> op, const VecArgs<T>
       __syncwarp();
     }
   }
-  if (LD == 0) return;
+  pdl_release();
+  if (LD == 0) {
+    block_sum3(pq, nq, npt, red, tot);
+    if (!grid_reduce<A, 3>(tot, part, st->gcnt, g)) return;
+    finish_alpha(st, tot, i, 0);
+    return;
+  }
 #pragma unroll
   for (int u = 0; u < P; ++u) red[(warp * 32 + lane) * P + u] = cvt<A>(a1[u]);
   __syncthreads();
@@ -221,9 +375,7 @@ __device__ __forceinline__ void phase1_body(const OpArgs<V> op, const VecArgs<T>
   for (int u = 0; u < P; ++u) red[(warp * 32 + lane) * P + u] = cvt<A>(a2[u]);
   __syncthreads();
   fold_slots<A, LDA>(red, wpart, NW, tot + LDA);    // C^H zt  -> tot[LD .. 2 LD)
-  if (threadIdx.x < 2 * LDA) part[(int64_t)g.id * (2 * LDA) + threadIdx.x] = tot[threadIdx.x];
-  if (!arrive_last(&st->cnt[0], g.n)) return;
-  reduce_cols(part, g.n, 2 * LDA, tot);
+  if (!grid_reduce<A, 2 * LDA>(tot, part, st->gcnt, g)) return;
   const int k = st->kc;
   if (threadIdx.x < k) {
     const double d = st->Dc[threadIdx.x];
@@ -240,9 +392,10 @@ __device__ __forceinline__ void phase2_body(const OpArgs<V> op, const VecArgs<T>
                                             typename traits<T>::acc* part, Blk g) {
   typedef typename traits<T>::acc A;
   constexpr int KA = KT > 0 ? KT : 1;
-  __shared__ A red[(NTHREADS / 32) * 3];
+  __shared__ A red[(NTHREADS / 32) * 4];
   __shared__ A tot[3];
   __shared__ T ze[KA], zet[KA];   // zeta, zetat broadcast from shared memory (few registers)
+  pdl_wait();
   if (st->done) return;
   const int i = st->iter + 1;
   const int k = KT > 0 ? st->kc : 0;
@@ -253,8 +406,9 @@ __device__ __forceinline__ void phase2_body(const OpArgs<V> op, const VecArgs<T>
   __syncthreads();
   const T* __restrict__ pt = (i & 1) ? v.pt[1] : v.pt[0];
   A pq = A(0.0), nq = A(0.0), npt = A(0.0);
-  const int stride = g.n * blockDim.x;
-  for (int row = g.id * blockDim.x + threadIdx.x; row < op.n; row += stride) {
+  int r0, r1;
+  block_rows(op.n, g, r0, r1);
+  for (int row = r0 + threadIdx.x; row < r1; row += NTHREADS) {
     T q = v.z[row], qt = v.zt[row];
     if (KT > 0) {
       const T* __restrict__ crow = v.C + (int64_t)row * v.ldk;
@@ -265,39 +419,12 @@ __device__ __forceinline__ void phase2_body(const OpArgs<V> op, const VecArgs<T>
       v.z[row] = q;
       v.zt[row] = qt;
     }
-    const T ptr = pt[row];
-    pq += cmul(cvt<A>(ptr), cvt<A>(q));
-    nq += A((double)abs2(q));
-    npt += A((double)abs2(ptr));
+    alpha_terms(pq, nq, npt, pt[row], q);
   }
-  A vals[3] = {pq, nq, npt};
-  write_partials(vals, 3, red, part, g.id);
-  if (!arrive_last(&st->cnt[1], g.n)) return;
-  reduce_cols(part, g.n, 3, tot);
-  if (threadIdx.x == 0) {
-    const zd PQ = to_zd(tot[0]);
-    const double NQ = real_of(tot[1]), NPT = real_of(tot[2]);
-    if (!isfinite(PQ.re) || !isfinite(PQ.im) || !isfinite(NQ) || !isfinite(NPT)) {
-      st->done = DONE_NONFINITE;
-    } else if (absval(PQ) <= BREAKDOWN_EPS * sqrt(NQ) * sqrt(NPT)) {
-      st->done = DONE_BREAK_PQ;
-    } else {
-      const zd al = st->rho / PQ;
-      st->alpha = al;
-      st->h_alpha[i % HR] = al;
-    }
-  }
-  __syncthreads();
-  if (st->done) return;
-  if (threadIdx.x < k) {
-    const zd al = st->alpha;
-    const int c = threadIdx.x;
-    const zd zc = st->zeta[c], ztc = st->zetat[c];
-    st->zeta_c[c] += al * zc;
-    st->zetat_c[c] += conjg(al) * ztc;
-    st->h_zeta[i % HR][c] = zc;
-    st->h_zetat[i % HR][c] = ztc;
-  }
+  pdl_release();
+  block_sum3(pq, nq, npt, red, tot);
+  if (!grid_reduce<A, 3>(tot, part, st->gcnt, g)) return;
+  finish_alpha(st, tot, i, k);
 }
 
 // ------------------------------------------------------------------------------------
@@ -307,8 +434,9 @@ template <class V, class T>
 __device__ __forceinline__ void phase3_body(const OpArgs<V> op, const VecArgs<T> v, DevState* st,
                                             typename traits<T>::acc* part, Blk g) {
   typedef typename traits<T>::acc A;
-  __shared__ A red[(NTHREADS / 32) * 3];
+  __shared__ A red[(NTHREADS / 32) * 4];
   __shared__ A tot[3];
+  pdl_wait();
   if (st->done) return;
   const int i = st->iter + 1;
   const T al = from_zd<T>(st->alpha), cal = conjg(al);
@@ -320,8 +448,9 @@ __device__ __forceinline__ void phase3_body(const OpArgs<V> op, const VecArgs<T>
   const T* __restrict__ p = (i & 1) ? v.p[1] : v.p[0];
   const T* __restrict__ pt = (i & 1) ? v.pt[1] : v.pt[0];
   A rho = A(0.0), n1 = A(0.0), n2 = A(0.0);
-  const int stride = g.n * blockDim.x;
-  for (int row = g.id * blockDim.x + threadIdx.x; row < op.n; row += stride) {
+  int r0, r1;
+  block_rows(op.n, g, r0, r1);
+  for (int row = r0 + threadIdx.x; row < r1; row += NTHREADS) {
     v.x[row] = v.x[row] + al * p[row];
     v.xt[row] = v.xt[row] + cal * pt[row];
     const T a = ro[row] - al * v.z[row];
@@ -332,10 +461,9 @@ __device__ __forceinline__ void phase3_body(const OpArgs<V> op, const VecArgs<T>
     n1 += A((double)abs2(a));
     n2 += A((double)abs2(b));
   }
-  A vals[3] = {rho, n1, n2};
-  write_partials(vals, 3, red, part, g.id);
-  if (!arrive_last(&st->cnt[2], g.n)) return;
-  reduce_cols(part, g.n, 3, tot);
+  pdl_release();
+  block_sum3(rho, n1, n2, red, tot);
+  if (!grid_reduce<A, 3>(tot, part, st->gcnt, g)) return;
   if (threadIdx.x == 0) {
     const zd RHO = to_zd(tot[0]);
     const double rr = sqrt(real_of(tot[1])), rtr = sqrt(real_of(tot[2]));
@@ -718,13 +846,34 @@ __global__ void k_sort_rows(int n, const int* trp, int* tci, V* tva) {
     default: CALL(32); break;    \
   }
 
+// Iteration-phase launches use programmatic stream serialization (pdl_wait / pdl_release in
+// the kernels), unless RBICG_NO_PDL is set in the environment.
+static bool pdl_enabled() {
+  static const bool on = getenv("RBICG_NO_PDL") == nullptr;
+  return on;
+}
+template <class... KArgs, class... Args>
+static void launch_phase_kernel(void (*k)(KArgs...), int grid, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <class V, class T>
 void launch_phase1(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
                    cudaStream_t s) {
   typedef typename traits<T>::acc A;
   // kt == 0: no recycle space (no projection); otherwise dispatch on the bases' row stride
   const int ld = kt == 0 ? 0 : v.ldk;
-#define RB_CALL(L) k_phase1<V, T, L><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part)
+#define RB_CALL(L) launch_phase_kernel(k_phase1<V, T, L>, grid, s, op, v, st, (A*)part)
   switch (ld) {
     case 0: RB_CALL(0); break;
     case 4: RB_CALL(4); break;
@@ -742,7 +891,7 @@ template <class V, class T>
 void launch_phase2(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
                    cudaStream_t s) {
   typedef typename traits<T>::acc A;
-#define RB_CALL(K) k_phase2<V, T, K><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part)
+#define RB_CALL(K) launch_phase_kernel(k_phase2<V, T, K>, grid, s, op, v, st, (A*)part)
   RB_KT_DISPATCH(kt, RB_CALL)
 #undef RB_CALL
 }
@@ -750,11 +899,11 @@ template <class V, class T>
 void launch_phase3(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int grid,
                    cudaStream_t s) {
   typedef typename traits<T>::acc A;
-  k_phase3<V, T><<<grid, NTHREADS, 0, s>>>(op, v, st, (A*)part);
+  launch_phase_kernel(k_phase3<V, T>, grid, s, op, v, st, (A*)part);
 }
 template <class V, class T>
 void launch_phase1_batch(const BatchArgs<V, T>* ba, int blocks, int ld, cudaStream_t s) {
-#define RB_CALL(L) k_phase1_b<V, T, L><<<blocks, NTHREADS, 0, s>>>(ba)
+#define RB_CALL(L) launch_phase_kernel(k_phase1_b<V, T, L>, blocks, s, ba)
   switch (ld) {
     case 0: RB_CALL(0); break;
     case 4: RB_CALL(4); break;
@@ -770,13 +919,13 @@ void launch_phase1_batch(const BatchArgs<V, T>* ba, int blocks, int ld, cudaStre
 }
 template <class V, class T>
 void launch_phase2_batch(const BatchArgs<V, T>* ba, int blocks, int kt, cudaStream_t s) {
-#define RB_CALL(K) k_phase2_b<V, T, K><<<blocks, NTHREADS, 0, s>>>(ba)
+#define RB_CALL(K) launch_phase_kernel(k_phase2_b<V, T, K>, blocks, s, ba)
   RB_KT_DISPATCH(kt, RB_CALL)
 #undef RB_CALL
 }
 template <class V, class T>
 void launch_phase3_batch(const BatchArgs<V, T>* ba, int blocks, cudaStream_t s) {
-  k_phase3_b<V, T><<<blocks, NTHREADS, 0, s>>>(ba);
+  launch_phase_kernel(k_phase3_b<V, T>, blocks, s, ba);
 }
 template <class V, class T>
 void launch_init(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
