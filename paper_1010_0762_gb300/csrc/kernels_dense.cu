@@ -218,6 +218,16 @@ __device__ __forceinline__ float cabs_(zf a) { return hypotf(a.re, a.im); }
 // sqrt(2) of the modulus).  FP64 hypot costs dozens of FP64 instructions on this part.
 __device__ __forceinline__ double cabs1_(zd a) { return fabs(a.re) + fabs(a.im); }
 __device__ __forceinline__ float cabs1_(zf a) { return fabsf(a.re) + fabsf(a.im); }
+// 1 / z as conj(z) / |z|^2: one real division.  A dependent FP64 operation costs about 60
+// cycles on this part, a division about 570 and the scaled (Smith) complex quotient about
+// 2000, so pivots and reflector factors on the dense kernels' critical paths use this form;
+// |z|^2 falls back to the scaled quotient when it would over- or underflow.
+__device__ __forceinline__ zd crcp(zd z) {
+  const double n2 = fma(z.re, z.re, z.im * z.im);
+  if (!(n2 > 1e-290 && n2 < 1e290)) return zd(1.0) / z;
+  const double d = 1.0 / n2;
+  return zd(z.re * d, -z.im * d);
+}
 
 // Selection of eigenvalue indices (reading: k closest to the origin; on a real problem a
 // conjugate pair is one unit of two columns, k-1 columns if it straddles the cut).
@@ -244,8 +254,7 @@ __device__ int select_units(const zd* lam, int m, int k, int real_path, int* sel
   for (int t = 0; t < cnt; ++t) {
     const int i = order[t];
     if (used[i]) continue;
-    const double al = sqrt(mag[i]);
-    const bool isreal = !real_path || fabs(lam[i].im) <= 1e-10 * (al > 0.0 ? al : 1.0);
+    const bool isreal = !real_path || lam[i].im * lam[i].im <= 1e-20 * (mag[i] > 0.0 ? mag[i] : 1.0);
     if (!real_path || isreal) {
       if (cols + 1 > k) break;
       sel[units] = i; pairflag[units] = 0; ++units; ++cols; used[i] = true;
@@ -309,81 +318,6 @@ __device__ void givens_f(zf a, zf b, float* c, zf* s) {
   *s = (a * ria) * conjg(b) * rn;
 }
 
-// Warp 0: eigenvalues of the Hessenberg H (FP32, ld) by implicit single-shift QR with Wilkinson
-// shifts, updating only the active window.  Returns false (with diagnostics) on failure.
-__device__ bool qr_eigs_warp_f32(zf* T, int m, int ld, int* dbg) {
-  const int lane = threadIdx.x & 31;
-  const float eps = 1.1920929e-07f;
-  int hi = m - 1, iter = 0, total = 0;
-  while (hi > 0) {
-    int lo = hi;
-    while (lo > 0) {
-      const float sub = cabs1f_(T[lo + (lo - 1) * ld]);
-      const float dsum = cabs1f_(T[lo + lo * ld]) + cabs1f_(T[lo - 1 + (lo - 1) * ld]);
-      if (sub <= eps * (dsum > 0.f ? dsum : 1.f)) {
-        __syncwarp();
-        if (lane == 0) T[lo + (lo - 1) * ld] = zf(0.f, 0.f);
-        __syncwarp();
-        break;
-      }
-      --lo;
-    }
-    if (lo == hi) { --hi; iter = 0; continue; }
-    if (!finite_of(T[hi + hi * ld].re) || !finite_of(T[hi + (hi - 1) * ld].re) ||
-        !isfinite(T[hi + hi * ld].im) || !isfinite(T[hi + (hi - 1) * ld].im)) {
-      if (lane == 0) { dbg[0] = 3; dbg[1] = lo; dbg[2] = hi; dbg[3] = iter; dbg[4] = total; }
-      return false;
-    }
-    if (++total > 60 * m) {
-      if (lane == 0) { dbg[0] = 2; dbg[1] = lo; dbg[2] = hi; dbg[3] = iter; dbg[4] = total; }
-      return false;
-    }
-    ++iter;
-    const zf a = T[hi - 1 + (hi - 1) * ld], b = T[hi - 1 + hi * ld], c = T[hi + (hi - 1) * ld], d = T[hi + hi * ld];
-    zf mu;
-    if (iter % 11 == 10) {
-      mu = d + zf(cabsf_(c) * 0.75f, 0.f);   // exceptional shift
-    } else {
-      const zf tr = a + d, det = a * d - b * c;
-      const zf half = tr * 0.5f;
-      const zf disc = half * half - det;
-      const float rdisc = cabsf_(disc);
-      // radicands clamped: hypotf's rounding can put |disc| + Re(disc) below zero
-      float sr = sqrtf(fmaxf(0.f, 0.5f * (rdisc + disc.re))), si = sqrtf(fmaxf(0.f, 0.5f * (rdisc - disc.re)));
-      if (disc.im < 0.f) si = -si;
-      const zf sq(sr, si);
-      const zf l1 = half + sq, l2 = half - sq;
-      mu = cabsf_(l1 - d) < cabsf_(l2 - d) ? l1 : l2;
-    }
-    const zf x = T[lo + lo * ld] - mu, y = T[lo + 1 + lo * ld];
-    for (int k = lo; k < hi; ++k) {
-      float cs;
-      zf sn;
-      if (k == lo) givens_f(x, y, &cs, &sn);
-      else givens_f(T[k + (k - 1) * ld], T[k + 1 + (k - 1) * ld], &cs, &sn);
-      __syncwarp();   // all lanes have read the rotation's defining entries
-      const int c0 = k > lo ? k - 1 : lo;
-      for (int col = c0 + lane; col <= hi; col += 32) {
-        const zf p = T[k + col * ld], q = T[k + 1 + col * ld];
-        T[k + col * ld] = cs * p + sn * q;
-        T[k + 1 + col * ld] = cs * q - conjg(sn) * p;
-      }
-      __syncwarp();
-      const int r1 = k + 2 < hi ? k + 2 : hi;
-      for (int row = lo + lane; row <= r1; row += 32) {
-        const zf p = T[row + k * ld], q = T[row + (k + 1) * ld];
-        T[row + k * ld] = cs * p + conjg(sn) * q;
-        T[row + (k + 1) * ld] = cs * q - sn * p;
-      }
-      __syncwarp();
-      // the bulge entry is read again only by the next sweep: no barrier needed here
-      if (k > lo && lane == 0) T[k + 1 + (k - 1) * ld] = zf(0.f, 0.f);
-    }
-    __syncwarp();
-  }
-  return true;
-}
-
 // Block-wide (all threads): eigenvalues of the Hessenberg H (FP32, ld) by implicit QR with
 // several shifts per sweep, each chased as its own bulge by one warp, the bulges three rows
 // apart and advanced in lockstep: step t moves bulge w to rotation k = lo + t - 3 w.  Within a
@@ -394,8 +328,9 @@ __device__ bool qr_eigs_warp_f32(zf* T, int m, int ld, int* dbg) {
 // exceptional shift after 10 sweeps without deflation.  Returns false (with diagnostics) on a
 // non-finite entry or after 60 m sweeps.
 __device__ bool qr_eigs_block_f32(zf* T, int m, int ld, int* dbg) {
-  __shared__ int s_lo, s_hi, s_nb, s_fail;
+  __shared__ int s_lo, s_hi, s_nb, s_fail, s_hmax, s_lmax;
   __shared__ zf s_mu[8];
+  __shared__ unsigned char s_neg[MMAX];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int NB = nwarp < 8 ? nwarp : 8;
   const float eps = 1.1920929e-07f;
@@ -403,53 +338,71 @@ __device__ bool qr_eigs_block_f32(zf* T, int m, int ld, int* dbg) {
   if (threadIdx.x == 0) { s_hi = m - 1; s_fail = 0; }
   __syncthreads();
   for (;;) {
-    if (threadIdx.x == 0) {
-      int hi = s_hi, lo = hi;
-      for (;;) {
-        if (hi <= 0) break;
-        lo = hi;
-        while (lo > 0) {
-          const float sub = cabs1f_(T[lo + (lo - 1) * ld]);
-          const float dsum = cabs1f_(T[lo + lo * ld]) + cabs1f_(T[lo - 1 + (lo - 1) * ld]);
-          if (sub <= eps * (dsum > 0.f ? dsum : 1.f)) { T[lo + (lo - 1) * ld] = zf(0.f, 0.f); break; }
-          --lo;
-        }
-        if (lo == hi) { --hi; stall = 0; continue; }
-        break;
+    // Deflation, all threads at once: row i (1 <= i <= hi) is split off when its subdiagonal
+    // is negligible against its two diagonal neighbours (such entries are set to zero).  The
+    // window's bottom moves up past split-off 1 x 1 blocks (hi' = the largest i <= hi whose
+    // subdiagonal is not negligible, 0 if none) and its top is the largest split point below
+    // hi' (lo, 0 if none) -- what a scan from hi downwards finds.
+    const int hi0 = s_hi;
+    if (threadIdx.x == 0) { s_hmax = 0; s_lmax = 0; }
+    __syncthreads();
+    for (int i = 1 + threadIdx.x; i <= hi0; i += blockDim.x) {
+      const float sub = cabs1f_(T[i + (i - 1) * ld]);
+      const float dsum = cabs1f_(T[i + i * ld]) + cabs1f_(T[i - 1 + (i - 1) * ld]);
+      const bool neg = sub <= eps * (dsum > 0.f ? dsum : 1.f);
+      s_neg[i] = neg;
+      if (neg) T[i + (i - 1) * ld] = zf(0.f, 0.f);
+      else atomicMax(&s_hmax, i);
+    }
+    __syncthreads();
+    const int hi1 = s_hmax;
+    for (int i = 1 + threadIdx.x; i < hi1; i += blockDim.x)
+      if (s_neg[i]) atomicMax(&s_lmax, i);
+    __syncthreads();
+    const int lo1 = s_lmax;
+    // shifts: eigenvalues of the 2 x 2 blocks ending at rows hi1, hi1 - 2, ..., the one nearer
+    // the block's bottom entry first, one thread per block
+    const int w = hi1 - lo1 + 1;
+    int nb1 = (w - 1) / 3 + 1;
+    if (nb1 > NB) nb1 = NB;
+    if (w <= 4) nb1 = 1;
+    if (hi1 > 0 && threadIdx.x < (nb1 + 1) / 2) {
+      const int r = hi1 - 2 * threadIdx.x;
+      const int c0 = 2 * threadIdx.x;
+      if (r - 1 >= lo1) {
+        const zf a = T[r - 1 + (r - 1) * ld], b = T[r - 1 + r * ld], c = T[r + (r - 1) * ld], d = T[r + r * ld];
+        const zf half = (a + d) * 0.5f;
+        const zf disc = half * half - (a * d - b * c);
+        const float rdisc = cabsf_(disc);
+        // radicands clamped: hypotf's rounding can put |disc| + Re(disc) below zero
+        float sr = sqrtf(fmaxf(0.f, 0.5f * (rdisc + disc.re))), si = sqrtf(fmaxf(0.f, 0.5f * (rdisc - disc.re)));
+        if (disc.im < 0.f) si = -si;
+        const zf l1 = half + zf(sr, si), l2 = half - zf(sr, si);
+        const bool first1 = cabsf_(l1 - d) < cabsf_(l2 - d);
+        s_mu[c0] = first1 ? l1 : l2;
+        if (c0 + 1 < nb1) s_mu[c0 + 1] = first1 ? l2 : l1;
+      } else {
+        s_mu[c0] = T[hi1 + hi1 * ld];
+        if (c0 + 1 < nb1) s_mu[c0 + 1] = T[hi1 + hi1 * ld];
       }
-      s_hi = hi;
-      s_lo = lo;
-      if (hi > 0) {
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (hi1 < hi0) stall = 0;
+      s_hi = hi1;
+      s_lo = lo1;
+      s_nb = nb1;
+      if (hi1 > 0) {
         ++stall;
-        const zf dd = T[hi + hi * ld], cc = T[hi + (hi - 1) * ld];
+        const zf dd = T[hi1 + hi1 * ld], cc = T[hi1 + (hi1 - 1) * ld];
         if (!isfinite(dd.re) || !isfinite(dd.im) || !isfinite(cc.re) || !isfinite(cc.im)) {
-          dbg[0] = 3; dbg[1] = lo; dbg[2] = hi; dbg[3] = stall; dbg[4] = total;
+          dbg[0] = 3; dbg[1] = lo1; dbg[2] = hi1; dbg[3] = stall; dbg[4] = total;
           s_fail = 1;
         } else if (++total > 60 * m) {
-          dbg[0] = 2; dbg[1] = lo; dbg[2] = hi; dbg[3] = stall; dbg[4] = total;
+          dbg[0] = 2; dbg[1] = lo1; dbg[2] = hi1; dbg[3] = stall; dbg[4] = total;
           s_fail = 1;
         }
-        const int w = hi - lo + 1;
-        int nb = (w - 1) / 3 + 1;
-        if (nb > NB) nb = NB;
-        if (w <= 4) nb = 1;
-        int cnt = 0;
-        for (int r = hi; cnt < nb && r - 1 >= lo; r -= 2) {
-          const zf a = T[r - 1 + (r - 1) * ld], b = T[r - 1 + r * ld], c = T[r + (r - 1) * ld], d = T[r + r * ld];
-          const zf half = (a + d) * 0.5f;
-          const zf disc = half * half - (a * d - b * c);
-          const float rdisc = cabsf_(disc);
-          // radicands clamped: hypotf's rounding can put |disc| + Re(disc) below zero
-          float sr = sqrtf(fmaxf(0.f, 0.5f * (rdisc + disc.re))), si = sqrtf(fmaxf(0.f, 0.5f * (rdisc - disc.re)));
-          if (disc.im < 0.f) si = -si;
-          const zf l1 = half + zf(sr, si), l2 = half - zf(sr, si);
-          const bool first1 = cabsf_(l1 - d) < cabsf_(l2 - d);
-          s_mu[cnt++] = first1 ? l1 : l2;
-          if (cnt < nb) s_mu[cnt++] = first1 ? l2 : l1;
-        }
-        while (cnt < nb) s_mu[cnt++] = T[hi + hi * ld];
-        if (stall % 11 == 10) s_mu[0] = T[hi + hi * ld] + zf(cabsf_(T[hi + (hi - 1) * ld]) * 0.75f, 0.f);
-        s_nb = nb;
+        if (stall % 11 == 10) s_mu[0] = T[hi1 + hi1 * ld] + zf(cabsf_(T[hi1 + (hi1 - 1) * ld]) * 0.75f, 0.f);
       }
     }
     __syncthreads();
@@ -502,29 +455,43 @@ __device__ __host__ inline EigInts eig_ints(zd* work) {
   return e;
 }
 
+// Scalar helpers of the cluster kernel, real (double: a real pencil) or complex (zd).
+__device__ __forceinline__ double cabs1_(double a) { return fabs(a); }
+__device__ __forceinline__ double crcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ bool nonzero(double a) { return a != 0.0; }
+__device__ __forceinline__ bool nonzero(zd a) { return a.re != 0.0 || a.im != 0.0; }
+__device__ __forceinline__ double bcast0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ zd bcast0(zd v) { return zd(__shfl_sync(0xffffffffu, v.re, 0), __shfl_sync(0xffffffffu, v.im, 0)); }
+__device__ __forceinline__ float bcast0(float v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ zf bcast0(zf v) { return zf(__shfl_sync(0xffffffffu, v.re, 0), __shfl_sync(0xffffffffu, v.im, 0)); }
+
 constexpr int ECL = 8;                                   // CTAs of the eigen cluster (portable size)
 constexpr int ECL_COLS = (3 * MMAX + ECL - 1) / ECL;     // local columns of [R | L | I] per CTA
 
+template <class S>
 struct EclBcast {   // one elimination / reflection step, written by the CTA owning its column
-  zd col[MMAX];     // Gauss-Jordan: pivot column after the row exchange; Householder: v
-  zd f;             // Householder: 2 / ||v||^2
+  S col[MMAX];      // Gauss-Jordan: pivot column after the row exchange; Householder: v
+  S f;              // Householder: 2 / ||v||^2
   int piv, flag;    // Gauss-Jordan: pivot row, 1 = zero pivot; Householder: 1 = no reflection
 };
 
+// S = double for a real pencil (real problems: L, R, the Hessenberg form and the reflectors are
+// real, so the reduction runs in real arithmetic, a quarter of the complex FP64 work), zd else.
+template <class S>
 __global__ void __cluster_dims__(ECL, 1, 1) __launch_bounds__(256)
 k_eig_cl(RefreshInfo f, DevState* st, zd* work, int has_R, int m) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  zd* cols = reinterpret_cast<zd*>(smraw);   // local column lc at cols + lc * MMAX
-  __shared__ EclBcast bc[2];
-  __shared__ zd up[2][MMAX];   // this CTA's part of T v (right Householder update)
-  __shared__ zd lv[MMAX];      // local copy of the broadcast column
-  __shared__ zd uvec[MMAX];
-  __shared__ zd tv[ECL_COLS];
+  S* cols = reinterpret_cast<S*>(smraw);   // local column lc at cols + lc * MMAX
+  __shared__ EclBcast<S> bc[2];
+  __shared__ S up[2][MMAX];    // this CTA's part of T v (right Householder update)
+  __shared__ S lv[MMAX];       // local copy of the broadcast column
+  __shared__ S uvec[MMAX];
+  __shared__ S tv[ECL_COLS];
   __shared__ double s_red[8];
   __shared__ int s_piv, s_skip;
-  __shared__ zd s_inva, s_f;
+  __shared__ S s_inva, s_f;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   const zd* Lm = work + W_L;
   const zd* Rm = work + W_R;
@@ -536,11 +503,11 @@ k_eig_cl(RefreshInfo f, DevState* st, zd* work, int has_R, int m) {
   const int nloc = ncol > rank ? (ncol - rank + ECL - 1) / ECL : 0;
   for (int e = tid; e < nloc * m; e += blockDim.x) {
     const int lc = e / m, r = e % m, g = rank + lc * ECL;
-    zd v;
-    if (!has_R) v = Lm[r + g * MMAX];
-    else if (g < m) v = Rm[r + g * MMAX];
-    else if (g < 2 * m) v = Lm[r + (g - m) * MMAX];
-    else v = (r == g - 2 * m) ? zd(1.0) : zd();
+    S v;
+    if (!has_R) v = from_zd<S>(Lm[r + g * MMAX]);
+    else if (g < m) v = from_zd<S>(Rm[r + g * MMAX]);
+    else if (g < 2 * m) v = from_zd<S>(Lm[r + (g - m) * MMAX]);
+    else v = (r == g - 2 * m) ? S(1.0) : S();
     cols[lc * MMAX + r] = v;
   }
   if (tid == 0) s_skip = 1;
@@ -552,7 +519,7 @@ k_eig_cl(RefreshInfo f, DevState* st, zd* work, int has_R, int m) {
   for (int k = 0; has_R && k < m; ++k) {
     const int owner = k % ECL;
     if (rank == owner && warp == 0 && !failed) {
-      const zd* c = cols + (k / ECL) * MMAX;
+      const S* c = cols + (k / ECL) * MMAX;
       double best = -1.0;
       int bi = k;
       for (int r = k + lane; r < m; r += 32) {
@@ -566,36 +533,37 @@ k_eig_cl(RefreshInfo f, DevState* st, zd* work, int has_R, int m) {
       }
       bi = __shfl_sync(0xffffffffu, bi, 0);
       best = __shfl_sync(0xffffffffu, best, 0);
-      EclBcast& B = bc[k & 1];
+      EclBcast<S>& B = bc[k & 1];
       for (int r = lane; r < m; r += 32) B.col[r] = c[r == k ? bi : (r == bi ? k : r)];
       if (lane == 0) { B.piv = bi; B.flag = (best > 0.0 && isfinite(best)) ? 0 : 1; }
     }
     cl.sync();
     if (!failed) {
-      const EclBcast* rb = cl.map_shared_rank(&bc[k & 1], owner);
+      const EclBcast<S>* rb = cl.map_shared_rank(&bc[k & 1], owner);
       for (int r = tid; r < m; r += blockDim.x) lv[r] = rb->col[r];
       if (tid == 0) s_piv = rb->piv;
       if (rb->flag) failed = true;
       __syncthreads();
       if (!failed) {
         const int p = s_piv;
-        if (tid == 0) s_inva = zd(1.0) / lv[k];
+        if (tid == 0) s_inva = crcp(lv[k]);
         __syncthreads();
-        const zd inva = s_inva;
+        const S inva = s_inva;
         for (int lc = tid; lc < nloc; lc += blockDim.x) {   // row exchange, pivot row scaled
-          zd* c = cols + lc * MMAX;
-          if (rank + lc * ECL == k) { tv[lc] = zd(); continue; }
-          if (p != k) { const zd t = c[k]; c[k] = c[p]; c[p] = t; }
-          const zd t = c[k] * inva;
+          S* c = cols + lc * MMAX;
+          if (rank + lc * ECL == k) { tv[lc] = S(); continue; }
+          if (p != k) { const S t = c[k]; c[k] = c[p]; c[p] = t; }
+          const S t = c[k] * inva;
           c[k] = t;
           tv[lc] = t;
         }
         __syncthreads();
         for (int e = tid; e < nloc * m; e += blockDim.x) {   // elimination in every other row
           const int lc = e / m, r = e % m;
-          zd* c = cols + lc * MMAX;
-          if (rank + lc * ECL == k) c[r] = r == k ? zd(1.0) : zd();
-          else if (r != k) c[r] -= lv[r] * tv[lc];
+          S* c = cols + lc * MMAX;
+          const S t = tv[lc];
+          if (rank + lc * ECL == k) c[r] = r == k ? S(1.0) : S();
+          else if (r != k && nonzero(t)) c[r] -= lv[r] * t;   // unit columns stay
         }
         __syncthreads();
       }
@@ -608,68 +576,73 @@ k_eig_cl(RefreshInfo f, DevState* st, zd* work, int has_R, int m) {
   for (int j = 0; j + 2 < m; ++j) {
     const int gj = mcol0 + j, owner = gj % ECL, len = m - j - 1;
     if (rank == owner && warp == 0 && !failed) {
-      zd* c = cols + (gj / ECL) * MMAX;
-      EclBcast& B = bc[j & 1];
+      S* c = cols + (gj / ECL) * MMAX;
+      EclBcast<S>& B = bc[j & 1];
       double nx2 = 0.0;
       for (int i = lane; i < len; i += 32) nx2 += abs2(c[j + 1 + i]);
       nx2 = __shfl_sync(0xffffffffu, warp_sum(nx2), 0);
-      const zd x0 = c[j + 1];
+      const S x0 = c[j + 1];
       const double tail = nx2 - abs2(x0);
       const bool skip = !(tail > 0.0) || tail <= nx2 * 1e-30;
       if (!skip) {
-        const double nx = sqrt(nx2), ax0 = cabs_(x0);
-        const zd ph = ax0 > 0.0 ? x0 * (1.0 / ax0) : zd(1.0);
-        const zd alpha = -(ph * nx);
-        const zd fct = zd(2.0 / (tail + abs2(x0 - alpha)));
+        const double nx = sqrt(nx2), a2 = abs2(x0);
+        const S ph = a2 > 0.0 ? x0 * rsqrt(a2) : S(1.0);
+        const S alpha = -(ph * nx);
+        const S fct = S(2.0 / (tail + abs2(x0 - alpha)));
         for (int i = lane; i < len; i += 32) {
-          const zd vi = i == 0 ? x0 - alpha : c[j + 1 + i];
+          const S vi = i == 0 ? x0 - alpha : c[j + 1 + i];
           B.col[i] = vi;
-          QV[i + j * MMAX] = vi;
+          QV[i + j * MMAX] = to_zd(vi);
         }
         __syncwarp();
-        for (int i = lane; i < len; i += 32) c[j + 1 + i] = i == 0 ? alpha : zd();   // P x = alpha e_1
-        if (lane == 0) { B.f = fct; QF[j] = fct; }
+        for (int i = lane; i < len; i += 32) c[j + 1 + i] = i == 0 ? alpha : S();   // P x = alpha e_1
+        if (lane == 0) { B.f = fct; QF[j] = to_zd(fct); }
       } else if (lane == 0) {
-        B.f = zd();
+        B.f = S();
         QF[j] = zd();
       }
       if (lane == 0) B.flag = skip ? 1 : 0;
     }
     cl.sync();
     if (!failed) {
-      const EclBcast* rb = cl.map_shared_rank(&bc[j & 1], owner);
+      const EclBcast<S>* rb = cl.map_shared_rank(&bc[j & 1], owner);
       for (int i = tid; i < len; i += blockDim.x) lv[i] = rb->col[i];
       if (tid == 0) { s_skip = rb->flag; s_f = rb->f; }
       __syncthreads();
       if (!s_skip) {
-        const zd fct = s_f;
+        const S fct = s_f;
         // left: T[j+1:, c] -= f v (v^H T[j+1:, c]) for this CTA's columns c > j (warp per column)
         for (int lc = warp; lc < nloc; lc += nwarp) {
           const int cc = rank + lc * ECL - mcol0;
           if (cc <= j || cc >= m) continue;
-          zd* c = cols + lc * MMAX;
-          zd w = zd();
+          S* c = cols + lc * MMAX;
+          S w = S();
           for (int i = lane; i < len; i += 32) w += cmul(lv[i], c[j + 1 + i]);
           w = warp_sum(w);
-          w = zd(__shfl_sync(0xffffffffu, w.re, 0), __shfl_sync(0xffffffffu, w.im, 0)) * fct;
+          w = bcast0(w) * fct;
           for (int i = lane; i < len; i += 32) c[j + 1 + i] -= lv[i] * w;
         }
         __syncthreads();
-        // right, this CTA's part of u = T[:, j+1:] v
-        for (int r = tid; r < m; r += blockDim.x) {
-          zd acc = zd();
-          for (int lc = 0; lc < nloc; ++lc) {
-            const int cc = rank + lc * ECL - mcol0;
-            if (cc > j && cc < m) acc += cols[lc * MMAX + r] * lv[cc - j - 1];
-          }
-          up[j & 1][r] = acc;
+        // right, this CTA's part of u = T[:, j+1:] v: four threads per row (a quarter of the
+        // local columns each, lanes 8 apart in one warp), combined in a fixed order
+        for (int base = 0; base < m; base += blockDim.x / 4) {
+          const int r = base + (warp * 8 + (lane & 7)), qtr = (lane >> 3) & 3;
+          S acc = S();
+          if (r < m)
+            for (int lc = qtr; lc < nloc; lc += 4) {
+              const int cc = rank + lc * ECL - mcol0;
+              if (cc > j && cc < m) acc += cols[lc * MMAX + r] * lv[cc - j - 1];
+            }
+          acc += shfl_xor(acc, 8);
+          acc += shfl_xor(acc, 16);
+          if (r < m && qtr == 0) up[j & 1][r] = acc;
         }
       }
     }
     cl.sync();
     if (!failed && !s_skip) {
       for (int r = tid; r < m; r += blockDim.x) {
-        zd acc = zd();
+        S acc = S();
         for (int q = 0; q < ECL; ++q) acc += cl.map_shared_rank(&up[j & 1][0], q)[r];
         uvec[r] = acc * s_f;
       }
@@ -685,8 +658,8 @@ k_eig_cl(RefreshInfo f, DevState* st, zd* work, int has_R, int m) {
   // ---- H and R^{-1} to the work buffer, then CTA 0 alone
   for (int e = tid; e < nloc * m; e += blockDim.x) {
     const int lc = e / m, r = e % m, g = rank + lc * ECL;
-    if (g >= mcol0 && g < mcol0 + m) work[W_H + r + (g - mcol0) * MMAX] = cols[lc * MMAX + r];
-    else if (has_R && g >= 2 * m) work[W_RI + r + (g - 2 * m) * MMAX] = cols[lc * MMAX + r];
+    if (g >= mcol0 && g < mcol0 + m) work[W_H + r + (g - mcol0) * MMAX] = to_zd(cols[lc * MMAX + r]);
+    else if (has_R && g >= 2 * m) work[W_RI + r + (g - 2 * m) * MMAX] = to_zd(cols[lc * MMAX + r]);
   }
   __threadfence();
   cl.sync();   // every CTA's writes are visible; no shared memory of another CTA is read after this
@@ -752,30 +725,37 @@ k_eig_cl(RefreshInfo f, DevState* st, zd* work, int has_R, int m) {
   }
 }
 
-// One warp: LU with partial pivoting of the upper Hessenberg A = H - sigma I (ld MMAX) in place.
+// Leading dimension of the shared copy of H - sigma I in k_eig_h: MMAX + 1 makes a row of 16-byte
+// entries fall on distinct bank groups (with MMAX every lane of a row access hit the same banks).
+constexpr int LDH = MMAX + 1;
+
+// One warp: LU with partial pivoting of the upper Hessenberg A = H - sigma I (ld LDH) in place.
 // Step k exchanges rows k and k+1 when that gives the larger pivot (sw[k]) and stores the
 // multiplier at A[k+1, k]; dinv[k] receives 1 / U[k, k] (a zero pivot is replaced by a tiny one:
 // sigma is then an eigenvalue to working precision, which inverse iteration tolerates).
 __device__ void hess_lu_warp(zd* A, int m, int* sw, zd* dinv, double tiny) {
   const int lane = threadIdx.x & 31;
   for (int k = 0; k + 1 < m; ++k) {
-    const bool swp = cabs1_(A[k + 1 + k * MMAX]) > cabs1_(A[k + k * MMAX]);
+    const bool swp = cabs1_(A[k + 1 + k * LDH]) > cabs1_(A[k + k * LDH]);
     if (swp)
       for (int c = k + lane; c < m; c += 32) {
-        const zd t = A[k + c * MMAX]; A[k + c * MMAX] = A[k + 1 + c * MMAX]; A[k + 1 + c * MMAX] = t;
+        const zd t = A[k + c * LDH]; A[k + c * LDH] = A[k + 1 + c * LDH]; A[k + 1 + c * LDH] = t;
       }
     __syncwarp();
-    zd piv = A[k + k * MMAX];
+    zd piv = A[k + k * LDH];
     if (cabs1_(piv) == 0.0) piv = zd(tiny);
-    const zd l = A[k + 1 + k * MMAX] / piv;
+    const zd rp = crcp(piv);
+    const zd l = A[k + 1 + k * LDH] * rp;
     __syncwarp();
-    for (int c = k + 1 + lane; c < m; c += 32) A[k + 1 + c * MMAX] -= l * A[k + c * MMAX];
-    if (lane == 0) { A[k + k * MMAX] = piv; A[k + 1 + k * MMAX] = l; sw[k] = swp; }
+    for (int c = k + 1 + lane; c < m; c += 32) A[k + 1 + c * LDH] -= l * A[k + c * LDH];
+    if (lane == 0) { A[k + k * LDH] = piv; A[k + 1 + k * LDH] = l; sw[k] = swp; dinv[k] = rp; }
     __syncwarp();
   }
-  if (lane == 0 && cabs1_(A[(m - 1) + (m - 1) * MMAX]) == 0.0) A[(m - 1) + (m - 1) * MMAX] = zd(tiny);
-  __syncwarp();
-  for (int k = lane; k < m; k += 32) dinv[k] = zd(1.0) / A[k + k * MMAX];
+  if (lane == 0) {
+    zd& d = A[(m - 1) + (m - 1) * LDH];
+    if (cabs1_(d) == 0.0) d = zd(tiny);
+    dinv[m - 1] = crcp(d);
+  }
   __syncwarp();
 }
 
@@ -785,14 +765,14 @@ __device__ void hess_solve_warp(const zd* A, int m, const int* sw, const zd* din
   if (lane == 0)
     for (int k = 0; k + 1 < m; ++k) {
       if (sw[k]) { const zd t = y[k]; y[k] = y[k + 1]; y[k + 1] = t; }
-      y[k + 1] -= A[k + 1 + k * MMAX] * y[k];
+      y[k + 1] -= A[k + 1 + k * LDH] * y[k];
     }
   __syncwarp();
   for (int c = m - 1; c >= 0; --c) {   // U x = y, column oriented
     const zd yc = y[c] * dinv[c];
     __syncwarp();
     if (lane == 0) y[c] = yc;
-    for (int r = lane; r < c; r += 32) y[r] -= A[r + c * MMAX] * yc;
+    for (int r = lane; r < c; r += 32) y[r] -= A[r + c * LDH] * yc;
     __syncwarp();
   }
 }
@@ -805,12 +785,12 @@ __device__ void hess_solve_adj_warp(const zd* A, int m, const int* sw, const zd*
     const zd yc = y[c] * conjg(dinv[c]);
     __syncwarp();
     if (lane == 0) y[c] = yc;
-    for (int r = c + 1 + lane; r < m; r += 32) y[r] -= conjg(A[c + r * MMAX]) * yc;
+    for (int r = c + 1 + lane; r < m; r += 32) y[r] -= conjg(A[c + r * LDH]) * yc;
     __syncwarp();
   }
   if (lane == 0)
     for (int k = m - 2; k >= 0; --k) {
-      y[k] -= conjg(A[k + 1 + k * MMAX]) * y[k + 1];
+      y[k] -= conjg(A[k + 1 + k * LDH]) * y[k + 1];
       if (sw[k]) { const zd t = y[k]; y[k] = y[k + 1]; y[k + 1] = t; }
     }
   __syncwarp();
@@ -843,13 +823,25 @@ __device__ void normalise_warp(const zd* t, zd* y, int m) {
   __syncwarp();
 }
 
+// sum of f(c) over c in [c0, c1) as four interleaved partial sums added in a fixed order: four
+// independent FP64 dependency chains instead of one (a dependent FP64 operation costs about 60
+// cycles on this part)
+template <class F>
+__device__ __forceinline__ zd dot4(int c0, int c1, F f) {
+  zd s0 = zd(), s1 = zd(), s2 = zd(), s3 = zd();
+  int c = c0;
+  for (; c + 3 < c1; c += 4) { s0 += f(c); s1 += f(c + 1); s2 += f(c + 2); s3 += f(c + 3); }
+  for (; c < c1; ++c) s0 += f(c);
+  return (s0 + s1) + (s2 + s3);
+}
+
 __global__ void __launch_bounds__(64) k_eig_h(zd* work, int m, int has_R) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const EigInts ei = eig_ints(work);
   const int cand = blockIdx.x;
   if (cand >= *ei.ncand) return;
-  zd* A = reinterpret_cast<zd*>(smraw);   // H - sigma I and its LU (ld MMAX)
-  zd* z = A + MMAX * m;
+  zd* A = reinterpret_cast<zd*>(smraw);   // H - sigma I and its LU (ld LDH)
+  zd* z = A + LDH * m;
   zd* zl = z + MMAX;
   zd* t = zl + MMAX;
   zd* tl = t + MMAX;
@@ -871,7 +863,7 @@ __global__ void __launch_bounds__(64) k_eig_h(zd* work, int m, int has_R) {
   for (int pass = 0; pass < 2; ++pass) {
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       const int r = e % m, c = e / m;
-      A[r + c * MMAX] = r == c ? Hg[r + c * MMAX] - sigma : Hg[r + c * MMAX];
+      A[r + c * LDH] = r == c ? Hg[r + c * MMAX] - sigma : Hg[r + c * MMAX];
     }
     __syncthreads();
     if (warp == 0) hess_lu_warp(A, m, sw, dinv, tiny);
@@ -895,8 +887,7 @@ __global__ void __launch_bounds__(64) k_eig_h(zd* work, int m, int has_R) {
     if (warp == 0) {
       zd num = zd(), den = zd();
       for (int r = lane; r < m; r += 32) {
-        zd hz = zd();
-        for (int c = (r > 0 ? r - 1 : 0); c < m; ++c) hz += Hg[r + c * MMAX] * z[c];
+        const zd hz = dot4(r > 0 ? r - 1 : 0, m, [&](int c) { return Hg[r + c * MMAX] * z[c]; });
         num += cmul(zl[r], hz);
         den += cmul(zl[r], z[r]);
       }
@@ -919,9 +910,7 @@ __global__ void __launch_bounds__(64) k_eig_h(zd* work, int m, int has_R) {
     if (has_R) {
       const zd* RI = work + W_RI;
       for (int r = lane; r < m; r += 32) {
-        zd acc = zd();
-        for (int c = 0; c < m; ++c) acc += cmul(RI[c + r * MMAX], zl[c]);
-        tl[r] = acc;
+        tl[r] = dot4(0, m, [&](int c) { return cmul(RI[c + r * MMAX], zl[c]); });
       }
       __syncwarp();
       for (int r = lane; r < m; r += 32) zl[r] = tl[r];
@@ -937,11 +926,8 @@ __global__ void __launch_bounds__(64) k_eig_h(zd* work, int m, int has_R) {
     const zd* Rm = work + W_R;
     zd num = zd(), den = zd();
     for (int r = lane; r < m; r += 32) {
-      zd ly = zd(), ry = zd();
-      for (int c = 0; c < m; ++c) {
-        ly += Lm[r + c * MMAX] * z[c];
-        ry += (has_R ? Rm[r + c * MMAX] : (r == c ? zd(1.0) : zd())) * z[c];
-      }
+      const zd ly = dot4(0, m, [&](int c) { return Lm[r + c * MMAX] * z[c]; });
+      const zd ry = has_R ? dot4(0, m, [&](int c) { return Rm[r + c * MMAX] * z[c]; }) : z[r];
       num += cmul(zl[r], ly);
       den += cmul(zl[r], ry);
     }
@@ -956,18 +942,22 @@ __global__ void __launch_bounds__(256) k_eig_c(RefreshInfo f, DevState* st, zd* 
   const Layout Lay = make_layout(f);
   const EigInts ei = eig_ints(work);
   __shared__ int s_units;
+  __shared__ zd s_raw[KMAX + NCAND_EXTRA], s_lam[KMAX + NCAND_EXTRA];
+  const int nc = st->eig_status == 0 ? *ei.ncand : 0;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) s_raw[c] = work[W_LAM2 + c];
+  __syncthreads();
+  // a candidate that refined to the eigenvalue of an earlier one is dropped (candidate c is
+  // compared with every earlier refined value; one thread per candidate)
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    zd lc = s_raw[c];
+    for (int q = 0; q < c; ++q)
+      if (cabs1_(lc - s_raw[q]) <= 1e-8 * cabs1_(lc)) { lc = zd(nan(""), 0.0); break; }
+    s_lam[c] = lc;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int units = 0, cols = 0;
-    if (st->eig_status == 0 && *ei.ncand > 0) {
-      zd lam[KMAX + NCAND_EXTRA];
-      for (int c = 0; c < *ei.ncand; ++c) {
-        // a candidate that refined to the eigenvalue of an earlier one is dropped
-        lam[c] = work[W_LAM2 + c];
-        for (int q = 0; q < c; ++q)
-          if (cabs1_(lam[c] - work[W_LAM2 + q]) <= 1e-8 * cabs1_(lam[c])) { lam[c] = zd(nan(""), 0.0); break; }
-      }
-      units = select_units(lam, *ei.ncand, f.k, f.real_path, ei.sel, ei.pair, &cols);
-    }
+    if (nc > 0) units = select_units(s_lam, nc, f.k, f.real_path, ei.sel, ei.pair, &cols);
     *ei.units = units;
     *ei.cols = cols;
     st->kk = cols;
@@ -990,16 +980,26 @@ __global__ void __launch_bounds__(256) k_eig_c(RefreshInfo f, DevState* st, zd* 
     Lv[r + u * MMAX] = work[W_YL + ei.sel[u] * MMAX + r];
   }
   __syncthreads();
-  if (threadIdx.x < 2 * units) {   // unit norm, largest component real and positive
-    const int u = threadIdx.x % units;
-    const bool left = threadIdx.x >= units;
-    zd* w = (left ? Lv : Rv) + u * MMAX;
-    double nrm = 0.0, big = -1.0;
-    int bi = 0;
-    for (int r = 0; r < m; ++r) { const double a2 = abs2(w[r]); nrm += a2; if (a2 > big) { big = a2; bi = r; } }
-    nrm = sqrt(nrm);
-    const zd ph = nrm > 0.0 && big > 0.0 ? conjg(w[bi]) * (1.0 / (cabs_(w[bi]) * nrm)) : zd(1.0);
-    for (int r = 0; r < m; ++r) w[r] = w[r] * ph;
+  {   // unit norm, largest component real and positive: one warp per vector
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int vi = wp; vi < 2 * units; vi += nw) {
+      const int u = vi % units;
+      zd* w = (vi >= units ? Lv : Rv) + u * MMAX;
+      double nrm = 0.0, big = -1.0;
+      int bi = 0;
+      for (int r = lane; r < m; r += 32) { const double a2 = abs2(w[r]); nrm += a2; if (a2 > big) { big = a2; bi = r; } }
+      for (int o = 16; o > 0; o >>= 1) {   // sum (lane 0's order is broadcast) and first argmax
+        nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+        const double ob = __shfl_xor_sync(0xffffffffu, big, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > big || (ob == big && oi < bi)) { big = ob; bi = oi; }
+      }
+      nrm = __shfl_sync(0xffffffffu, nrm, 0);
+      const zd wb = w[bi];
+      const zd ph = nrm > 0.0 && big > 0.0 ? conjg(wb) * rsqrt(abs2(wb) * nrm) : zd(1.0);
+      __syncwarp();
+      for (int r = lane; r < m; r += 32) w[r] = w[r] * ph;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0 && lam_out) {
@@ -1042,14 +1042,16 @@ __global__ void __launch_bounds__(256) k_eig_c(RefreshInfo f, DevState* st, zd* 
 static void launch_eig3(const RefreshInfo& info, DevState* st, zd* work, zd* Wphi, zd* Wphit, int ldw,
                         double* lam_out, int has_R, int m, int raw, cudaStream_t s) {
   const size_t smem_cl = std::max<size_t>((size_t)ECL_COLS * MMAX * sizeof(zd), (size_t)MMAX * (MMAX + 1) * sizeof(zf));
-  const size_t smem_h = (size_t)(MMAX * m + 5 * MMAX) * sizeof(zd);
+  const size_t smem_h = (size_t)(LDH * m + 5 * MMAX) * sizeof(zd);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_eig_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl);
-    cudaFuncSetAttribute(k_eig_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((MMAX * MMAX + 5 * MMAX) * sizeof(zd)));
+    cudaFuncSetAttribute(k_eig_cl<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl);
+    cudaFuncSetAttribute(k_eig_cl<zd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl);
+    cudaFuncSetAttribute(k_eig_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((LDH * MMAX + 5 * MMAX) * sizeof(zd)));
     attr_set = true;
   }
-  k_eig_cl<<<ECL, 256, smem_cl, s>>>(info, st, work, has_R, m);
+  if (info.real_path) k_eig_cl<double><<<ECL, 256, smem_cl, s>>>(info, st, work, has_R, m);
+  else k_eig_cl<zd><<<ECL, 256, smem_cl, s>>>(info, st, work, has_R, m);
   k_eig_h<<<KMAX + NCAND_EXTRA, 64, smem_h, s>>>(work, m, has_R);
   k_eig_c<<<1, 256, 0, s>>>(info, st, work, Wphi, Wphit, ldw, lam_out, m, raw);
 }
@@ -1097,7 +1099,8 @@ void launch_dense_eig_host(int real_path, int m, const zd* L, const zd* R, int h
 // inner product apq = a^H b (|apq|^2 = g2 > 0): cosine cs, sine sn and phase e, so that
 // [a, b] <- [cs a - sn conj(e) b, sn e a + cs b] makes the two columns orthogonal.
 // FP32 version: everything in FP32.
-__device__ __forceinline__ bool jacobi_rot(float app, float aqq, zf apq, float g2, float* cs, float* sn, zf* e) {
+template <class E>   // E: zf, or float for a real matrix
+__device__ __forceinline__ bool jacobi_rot(float app, float aqq, E apq, float g2, float* cs, float* sn, E* e) {
   const float rg = rsqrtf(g2);
   const float zeta = (aqq - app) * 0.5f * rg, az = fabsf(zeta);
   const float t = az > 1e18f ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(1.f + zeta * zeta));
@@ -1109,15 +1112,17 @@ __device__ __forceinline__ bool jacobi_rot(float app, float aqq, zf apq, float g
 }
 // FP64 version: the angle in FP32 (an inexact angle only leaves a little of a^H b for the next
 // sweep), cosine, sine and phase in FP64 so that the rotation is unitary to FP64 rounding.
-__device__ __forceinline__ bool jacobi_rot(double app, double aqq, zd apq, double g2, double* cs, double* sn, zd* e) {
-  const double zq = (aqq - app) / (2.0 * sqrt(g2));
+template <class E>   // E: zd, or double for a real matrix
+__device__ __forceinline__ bool jacobi_rot(double app, double aqq, E apq, double g2, double* cs, double* sn, E* e) {
+  const double rg = rsqrt(g2);   // one reciprocal square root serves the angle and the phase
+  const double zq = (aqq - app) * 0.5 * rg;
   const float zeta = (float)zq, az = fabsf(zeta);
   const float tf = az > 1e18f ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(1.f + zeta * zeta));
   if (tf == 0.f) return false;
   const double t = (double)tf;
   *cs = rsqrt(1.0 + t * t);
   *sn = *cs * t;
-  *e = apq * rsqrt(g2);
+  *e = apq * rg;
   return true;
 }
 
@@ -1148,7 +1153,7 @@ __device__ int jacobi_sweeps(C* A, C* V, int k, int max_sweeps, Rl tol2, int* s_
         }
         app = warp_sum(app); aqq = warp_sum(aqq); apq = warp_sum(apq);
         app = __shfl_sync(0xffffffffu, app, 0); aqq = __shfl_sync(0xffffffffu, aqq, 0);
-        apq = C(__shfl_sync(0xffffffffu, apq.re, 0), __shfl_sync(0xffffffffu, apq.im, 0));
+        apq = bcast0(apq);
         const Rl g2 = abs2(apq);
         if (g2 <= tol2 * (app * aqq) || g2 == Rl(0)) continue;
         Rl cs, sn;
@@ -1174,15 +1179,18 @@ __device__ int jacobi_sweeps(C* A, C* V, int k, int max_sweeps, Rl tol2, int* s_
   return sweep;
 }
 
-__global__ void __launch_bounds__(512) k_svd(int real_path, const int* k_dev, int kmax, const zd* S2, double svd_tol,
+// C / Cf = zd / zf, or double / float for a real problem (its Ct^H C is real: real rotations, a
+// quarter of the complex FP64 work).
+template <class C, class Cf>
+__global__ void __launch_bounds__(512) k_svd(const int* k_dev, int kmax, const zd* S2, double svd_tol,
                                              zd* Nmat, zd* Mmat, double* sigma, int* p_dev, double* Dc_dev,
                                              int* status) {
-  extern __shared__ unsigned char smraw[];
-  zd* A = reinterpret_cast<zd*>(smraw);   // column-major k x k: A = S_norm, rotated to M Sigma
-  zd* V = A + KMAX * KMAX;                // accumulated right rotations (N)
-  zd* A0 = V + KMAX * KMAX;               // S_norm (kept for the FP64 restart)
-  zf* Af = reinterpret_cast<zf*>(A0 + KMAX * KMAX);
-  zf* Vf = Af + KMAX * KMAX;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* A = reinterpret_cast<C*>(smraw);     // column-major k x k: A = S_norm, rotated to M Sigma
+  C* V = A + KMAX * KMAX;                 // accumulated right rotations (N)
+  C* A0 = V + KMAX * KMAX;                // S_norm (kept for the FP64 restart)
+  Cf* Af = reinterpret_cast<Cf*>(A0 + KMAX * KMAX);
+  Cf* Vf = Af + KMAX * KMAX;
   __shared__ double dn[KMAX], dtn[KMAX], sg[KMAX];
   __shared__ int ord[KMAX], s_rot, s_p;
   const int k = min(*k_dev, kmax);
@@ -1199,49 +1207,48 @@ __global__ void __launch_bounds__(512) k_svd(int real_path, const int* k_dev, in
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int r = e % k, c = e / k;
     const double sr = dtn[r] > 0.0 ? 1.0 / dtn[r] : 0.0, scc = dn[c] > 0.0 ? 1.0 / dn[c] : 0.0;
-    zd a = S2[r * ld2 + c] * (sr * scc);
-    if (real_path) a.im = 0.0;
+    const C a = from_zd<C>(S2[r * ld2 + c] * (sr * scc));
     A0[r + c * k] = a;
-    Af[r + c * k] = zf((float)a.re, (float)a.im);   // entries <= 1 after the unit-norm scaling
-    Vf[r + c * k] = r == c ? zf(1.f) : zf(0.f);
+    Af[r + c * k] = cvt<Cf>(a);   // entries <= 1 after the unit-norm scaling
+    Vf[r + c * k] = r == c ? Cf(1.f) : Cf(0.f);
   }
   __syncthreads();
   // FP32 sweeps to about FP32 orthogonality, then A <- A0 Vf and V <- Vf in FP64 and FP64
   // sweeps from there (one or two: the convergence of cyclic Jacobi is quadratic).
-  jacobi_sweeps<zf, float>(Af, Vf, k, 30, (8e-8f * k) * (8e-8f * k), &s_rot);
+  jacobi_sweeps<Cf, float>(Af, Vf, k, 30, (8e-8f * k) * (8e-8f * k), &s_rot);
   // Vf is unitary only to FP32 rounding: two Newton-Schulz steps in FP64, V <- V (3 I - V^H V) / 2,
   // make it unitary to FP64 rounding (the error squares at each step); G = V^H V goes in A.
   for (int e = threadIdx.x; e < k * k; e += blockDim.x)
-    V[e] = zd((double)Vf[e].re, (double)Vf[e].im);
+    V[e] = cvt<C>(Vf[e]);
   __syncthreads();
   for (int ns = 0; ns < 2; ++ns) {
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
       const int r = e % k, c = e / k;
-      zd acc = zd();
+      C acc = C();
       for (int q = 0; q < k; ++q) acc += cmul(V[q + r * k], V[q + c * k]);
       A[r + c * k] = acc;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {   // A0's spare copy: Af/Vf area
       const int r = e % k, c = e / k;
-      zd acc = zd();
-      for (int q = 0; q < k; ++q) acc += V[r + q * k] * ((q == c ? zd(3.0) : zd()) - A[q + c * k]);
-      reinterpret_cast<zd*>(Af)[r + c * k] = acc * 0.5;
+      C acc = C();
+      for (int q = 0; q < k; ++q) acc += V[r + q * k] * ((q == c ? C(3.0) : C()) - A[q + c * k]);
+      reinterpret_cast<C*>(Af)[r + c * k] = acc * 0.5;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < k * k; e += blockDim.x) V[e] = reinterpret_cast<zd*>(Af)[e];
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) V[e] = reinterpret_cast<C*>(Af)[e];
     __syncthreads();
   }
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {   // A = A0 V
     const int r = e % k, c = e / k;
-    zd acc = zd();
+    C acc = C();
     for (int q = 0; q < k; ++q) acc += A0[r + q * k] * V[q + c * k];
     A[r + c * k] = acc;
   }
   __syncthreads();
   // converged pair: |a^H b| at the rounding floor of a k-term FP64 inner product (about
   // k eps ||a|| ||b||); a threshold below it never lets the sweeps stop
-  jacobi_sweeps<zd, double>(A, V, k, 10, (4e-16 * k) * (4e-16 * k), &s_rot);
+  jacobi_sweeps<C, double>(A, V, k, 10, (4e-16 * k) * (4e-16 * k), &s_rot);
   // singular values, order
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
     double s = 0.0;
@@ -1268,14 +1275,14 @@ __global__ void __launch_bounds__(512) k_svd(int real_path, const int* k_dev, in
   // Nmat[a, c] = (1/dn[a]) N[a, ord c]; Mmat[a, c] = (1/dtn[a]) M[a, ord c], M = A / sigma
   for (int e = threadIdx.x; e < kmax * KMAX; e += blockDim.x) {
     const int a = e / KMAX, c = e % KMAX;
-    zd nv = zd(), mv = zd();
+    C nv = C(), mv = C();
     if (a < k && c < p) {
       const int oc = ord[c];
       nv = V[a + oc * k] * (dn[a] > 0.0 ? 1.0 / dn[a] : 0.0);
       mv = A[a + oc * k] * ((dtn[a] > 0.0 ? 1.0 / dtn[a] : 0.0) / sg[oc]);
     }
-    Nmat[e] = nv;
-    Mmat[e] = mv;
+    Nmat[e] = to_zd(nv);
+    Mmat[e] = to_zd(mv);
   }
   for (int c = threadIdx.x; c < KMAX; c += blockDim.x) {
     const double sv = c < p ? sg[ord[c]] : 0.0;
@@ -1291,10 +1298,14 @@ void launch_dense_svd(int real_path, const int* k_dev, int kmax, const zd* S, co
   const size_t smem = 3 * KMAX * KMAX * sizeof(zd) + 2 * KMAX * KMAX * sizeof(zf);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_svd<zd, zf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_svd<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  k_svd<<<1, 512, smem, s>>>(real_path, k_dev, kmax, S, svd_tol, Nmat, Mmat, sigma, p_dev, Dc_dev, status_dev);
+  if (real_path)
+    k_svd<double, float><<<1, 512, smem, s>>>(k_dev, kmax, S, svd_tol, Nmat, Mmat, sigma, p_dev, Dc_dev, status_dev);
+  else
+    k_svd<zd, zf><<<1, 512, smem, s>>>(k_dev, kmax, S, svd_tol, Nmat, Mmat, sigma, p_dev, Dc_dev, status_dev);
 }
 
 template void launch_dense_refresh<double>(const RefreshInfo&, DevState*, const double*, zd*, zd*, zd*, int, double*,
