@@ -392,9 +392,12 @@ __device__ __forceinline__ void phase2_body(const OpArgs<V> op, const VecArgs<T>
                                             typename traits<T>::acc* part, Blk g) {
   typedef typename traits<T>::acc A;
   constexpr int KA = KT > 0 ? KT : 1;
-  __shared__ A red[(NTHREADS / 32) * 4];
+  constexpr int NW = NTHREADS / 32;
+  __shared__ A red[NW * 4];
   __shared__ A tot[3];
   __shared__ T ze[KA], zet[KA];   // zeta, zetat broadcast from shared memory (few registers)
+  // per warp: an 8-column slice of C (or Ct) for its 32 rows, row stride 9 (conflict-free reads)
+  __shared__ T stg[KT > 0 ? NW : 1][KT > 0 ? 32 * 9 : 1];
   pdl_wait();
   if (st->done) return;
   const int i = st->iter + 1;
@@ -405,21 +408,50 @@ __device__ __forceinline__ void phase2_body(const OpArgs<V> op, const VecArgs<T>
   }
   __syncthreads();
   const T* __restrict__ pt = (i & 1) ? v.pt[1] : v.pt[0];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   A pq = A(0.0), nq = A(0.0), npt = A(0.0);
   int r0, r1;
   block_rows(op.n, g, r0, r1);
-  for (int row = r0 + threadIdx.x; row < r1; row += NTHREADS) {
-    T q = v.z[row], qt = v.zt[row];
+  // warp w takes the 32-row chunks r0 + 32 w + 256 j, so thread t sees rows r0 + t + 256 j:
+  // the order in which phase 1 accumulates the same sums when it finishes alpha itself
+  for (int base = r0 + warp * 32; base < r1; base += NTHREADS) {
+    const int row = base + lane;
+    const bool live = row < r1;
+    T q = live ? v.z[row] : T(0), qt = live ? v.zt[row] : T(0);
     if (KT > 0) {
-      const T* __restrict__ crow = v.C + (int64_t)row * v.ldk;
-      const T* __restrict__ ctrow = v.Ct + (int64_t)row * v.ldk;
+      // q = z - C zeta, qt = zt - Ct zetat, columns in ascending order.  A slice's 8 entries of
+      // a row are 64 contiguous bytes, so each warp load reads 4 rows in whole sectors.
+      const int nvalid = r1 - base < 32 ? r1 - base : 32;
+      const int ldk = v.ldk;
+      T* sg = stg[warp];
+#pragma unroll 1
+      for (int c0 = 0; c0 < KA; c0 += 8) {
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+          const T* __restrict__ src = side == 0 ? v.C : v.Ct;
 #pragma unroll
-      for (int c = 0; c < KA; ++c)
-        if (c < k) { q -= crow[c] * ze[c]; qt -= ctrow[c] * zet[c]; }
-      v.z[row] = q;
-      v.zt[row] = qt;
+          for (int u = 0; u < 8; ++u) {
+            const int e = lane + 32 * u, rr = e >> 3, cc = c0 + (e & 7);
+            sg[rr * 9 + (e & 7)] = (rr < nvalid && cc < ldk) ? src[(int64_t)(base + rr) * ldk + cc] : T(0);
+          }
+          __syncwarp();
+          if (live) {
+            T acc = side == 0 ? q : qt;
+            const T* zz = side == 0 ? ze : zet;
+#pragma unroll
+            for (int cl = 0; cl < 8; ++cl)
+              if (c0 + cl < k) acc -= sg[lane * 9 + cl] * zz[c0 + cl];
+            if (side == 0) q = acc; else qt = acc;
+          }
+          __syncwarp();
+        }
+      }
+      if (live) {
+        v.z[row] = q;
+        v.zt[row] = qt;
+      }
     }
-    alpha_terms(pq, nq, npt, pt[row], q);
+    if (live) alpha_terms(pq, nq, npt, pt[row], q);
   }
   pdl_release();
   block_sum3(pq, nq, npt, red, tot);
@@ -493,7 +525,9 @@ __device__ __forceinline__ int batch_slot(const BatchArgs<V, T>* ba) {
   return r;
 }
 // MINB resident blocks per SM: the unrolled slab projection of phase 1 otherwise takes 128
-// registers a thread and halves the warps that hide the gather latency.
+// registers a thread and halves the warps that hide the gather latency.  Three blocks per SM is
+// the default grid's one wave (3 x SMs blocks); phase 2's staged slices need that many
+// registers to stay out of local memory.
 #define RB_PHASE_KERNELS(NAME, BODY, MINB, TPARAMS, TARGS)                                               \
   template <TPARAMS>                                                                                    \
   __global__ void __launch_bounds__(NTHREADS, MINB) NAME(OpArgs<V> op, VecArgs<T> v, DevState* st,     \
@@ -510,7 +544,7 @@ __device__ __forceinline__ int batch_slot(const BatchArgs<V, T>* ba) {
   }
 #define RB_COMMA ,
 RB_PHASE_KERNELS(k_phase1, phase1_body, 3, class V RB_COMMA class T RB_COMMA int LD, V RB_COMMA T RB_COMMA LD)
-RB_PHASE_KERNELS(k_phase2, phase2_body, 4, class V RB_COMMA class T RB_COMMA int KT, V RB_COMMA T RB_COMMA KT)
+RB_PHASE_KERNELS(k_phase2, phase2_body, 3, class V RB_COMMA class T RB_COMMA int KT, V RB_COMMA T RB_COMMA KT)
 RB_PHASE_KERNELS(k_phase3, phase3_body, 4, class V RB_COMMA class T, V RB_COMMA T)
 #undef RB_COMMA
 #undef RB_PHASE_KERNELS
