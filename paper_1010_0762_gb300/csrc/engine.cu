@@ -169,6 +169,11 @@ struct Solver : SolverBase {
   cudaStream_t gs = nullptr;                        // graph capture / launch stream
   cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr;
   bool ref_pending = false;
+  // solve() launches a cycle's refresh after the next cycle's iterations (one graph launch)
+  // instead of before them (about twenty launches): ev_cycle marks the cycle's end at once, the
+  // refresh kernels follow the graph launch
+  bool defer_refresh = false, ref_deferred = false;
+  int def_j = 0, def_kp = 0;
   void* gpart = nullptr;        // Gram partials of the refresh (part belongs to the iteration)
   int64_t* launches;
   // operator (values in V; A^H values owned here)
@@ -195,6 +200,7 @@ struct Solver : SolverBase {
   // device scratch
   DevState* st = nullptr;
   void* part = nullptr;
+  T *Cq = nullptr, *Ctq = nullptr;   // compact copies of C, Ct (row stride VecArgs::ldc)
   A* G = nullptr;
   zd* work = nullptr;
   zd *Wphi = nullptr, *Wphit = nullptr, *Nmat = nullptr, *Mmat = nullptr;
@@ -262,6 +268,7 @@ struct Solver : SolverBase {
     T* bufs[] = {ring, ringt, p[0], p[1], pt[0], pt[1], z, zt, U, Ut, C, Ct,
                  Uc[0], Uc[1], Utc[0], Utc[1], Cc[0], Cc[1], Ctc[0], Ctc[1]};
     for (T* b : bufs) cudaFree(b);
+    cudaFree(Cq); cudaFree(Ctq);
     cudaFree(st); cudaFree(part); cudaFree(gpart); cudaFree(G); cudaFree(work); cudaFree(Wphi); cudaFree(Wphit);
     cudaFree(Nmat); cudaFree(Mmat); cudaFree(sig); cudaFree(iflag);
     if (x_save) cudaFree(x_save);
@@ -348,7 +355,7 @@ struct Solver : SolverBase {
     v.ring = ring; v.ringt = ringt; v.ld = ring_ld; v.R = R;
     v.p[0] = p[0]; v.p[1] = p[1]; v.pt[0] = pt[0]; v.pt[1] = pt[1];
     v.z = z; v.zt = zt; v.x = x; v.xt = xt; v.b = b; v.bt = bt;
-    v.C = Cp; v.Ct = Ctp; v.U = Up; v.Ut = Utp; v.ldk = ldk;
+    v.C = Cp; v.Ct = Ctp; v.U = Up; v.Ut = Utp; v.ldk = ldk; v.ldc = ldk;
     return v;
   }
 
@@ -405,8 +412,8 @@ struct Solver : SolverBase {
   // ------------------------------------------------------------------ Section 4.1-4.3 refresh
   // Runs after iteration j*s.  kp = columns of U_{j-1}.  Returns nothing; results are read
   // at the next sync (st->pcyc, st->eig_status).
-  void refresh(int j, int kp, const T* /*unused*/) {
-    RB_CUDA(cudaEventRecord(ev_cycle, s));
+  void refresh(int j, int kp, bool cycle_end_recorded = false) {
+    if (!cycle_end_recorded) RB_CUDA(cudaEventRecord(ev_cycle, s));
     RB_CUDA(cudaStreamWaitEvent(s2, ev_cycle, 0));
     cudaStream_t q = s2;
     const bool first = kc == 0;
@@ -507,6 +514,8 @@ struct Solver : SolverBase {
   void begin(const T* b, const T* bt, T* x, T* xt, double tol, int max_itn, uint64_t seed) {
     Run& R_ = run;
     R_ = Run{};
+    defer_refresh = false;   // solve() turns it on after begin(); batched engine steps never do
+    ref_deferred = false;
     R_.b = b; R_.bt = bt; R_.x = x; R_.xt = xt; R_.tol = tol; R_.max_itn = max_itn; R_.seed = seed;
     R_.kU_in = prm.recycle ? kU : 0;
     if (pending_start) system_start();
@@ -517,6 +526,16 @@ struct Solver : SolverBase {
     set_field(&DevState::eig_status, 0);
     set_field(&DevState::pcyc, 0);
     R_.v = vec(b, bt, x, xt, C, Ct, U, Ut);
+    // compact copies of C, Ct for the iteration kernels: the projections then run over the
+    // kc columns the system start kept (rounded up to 4), not the k columns of storage
+    const int ldc = std::max(4, ((kc + 3) / 4) * 4);
+    if (kc > 0 && ldc < ldk) {
+      if (!Cq) { Cq = dmalloc<T>((size_t)n * ldk); Ctq = dmalloc<T>((size_t)n * ldk); }
+      launch_pack_cols<T>(C, ldk, Cq, ldc, kc, n, s);
+      launch_pack_cols<T>(Ct, ldk, Ctq, ldc, kc, n, s);
+      count(2);
+      R_.v.C = Cq; R_.v.Ct = Ctq; R_.v.ldc = ldc;
+    }
     const int pi = prof->begin(7, s);
     launch_init<V, T>(op, R_.v, st, part, R_.kt, grid, 0, s);
     prof->end(pi, 2, s);
@@ -663,9 +682,21 @@ struct Solver : SolverBase {
     }
     if (R_.recycle && !R_.broken && R_.iter == (R_.j + 1) * prm.s) {
       ++R_.j;
-      refresh(R_.j, R_.kp, nullptr);
+      if (defer_refresh) {
+        RB_CUDA(cudaEventRecord(ev_cycle, s));
+        ref_deferred = true;
+        def_j = R_.j;
+        def_kp = R_.kp;
+      } else {
+        refresh(R_.j, R_.kp);
+      }
       R_.last_refresh = R_.j;
     }
+  }
+  void launch_deferred_refresh() {
+    if (!ref_deferred) return;
+    ref_deferred = false;
+    refresh(def_j, def_kp, true);
   }
 
   PairOut end() {
@@ -721,11 +752,15 @@ struct Solver : SolverBase {
 
   PairOut solve(const T* b, const T* bt, T* x, T* xt, double tol, int max_itn, uint64_t seed) {
     begin(b, bt, x, xt, tol, max_itn, seed);
+    defer_refresh = true;
     while (!run.done) {
       launch_cycle(cycle_len());
+      launch_deferred_refresh();
       fetch();
       after_cycle();
     }
+    launch_deferred_refresh();
+    defer_refresh = false;
     return end();
   }
 
@@ -1303,7 +1338,7 @@ static void op_spmv_project_impl(const rbicg_csr* A, const void* r, const void* 
     RB_CUDA(cudaMemcpy2DAsync(Cp, sizeof(T) * ldp, C, sizeof(T) * ldc, sizeof(T) * k, A->n, cudaMemcpyDeviceToDevice, s));
     RB_CUDA(cudaMemcpy2DAsync(Ctp, sizeof(T) * ldp, Ct, sizeof(T) * ldc, sizeof(T) * k, A->n, cudaMemcpyDeviceToDevice, s));
   }
-  v.C = Cp; v.Ct = Ctp; v.ldk = ldp;
+  v.C = Cp; v.Ct = Ctp; v.ldk = ldp; v.ldc = ldp;
   launch_phase1<V, T>(op, v, st, part, kt_for(k), grid, s);
   RB_CUDA(cudaGetLastError());
   RB_CUDA(cudaMemcpyAsync(&hst, st, sizeof hst, cudaMemcpyDeviceToHost, s));
@@ -1544,7 +1579,7 @@ static void engine_step_kind(rbicg_engine e, int kind) {
   if (idx.empty()) return;
   std::vector<int> strides;
   for (int i : idx) {
-    const int l = as_solver<V, T>(e->active[i])->ldk;
+    const int l = as_solver<V, T>(e->active[i])->run.v.ldc;
     if (std::find(strides.begin(), strides.end(), l) == strides.end()) strides.push_back(l);
   }
   auto& pool = e->bufs[kind];
@@ -1567,7 +1602,7 @@ static void engine_step_kind(rbicg_engine e, int kind) {
     hb->start[0] = 0;
     for (int i : idx) {
       Solver<V, T>* q = as_solver<V, T>(e->active[i]);
-      if (q->ldk != strides[g]) continue;
+      if (q->run.v.ldc != strides[g]) continue;
       hb->op[nreq] = q->op;
       hb->v[nreq] = q->run.v;
       hb->st[nreq] = q->st;

@@ -90,7 +90,10 @@ struct VecArgs {
   T* z; T* zt;                                   // z_i (overwritten by q_i)
   T* x; T* xt;                                   // iterates (caller buffers)
   const T* b; const T* bt;
-  const T* C; const T* Ct; const T* U; const T* Ut; int ldk;   // n x ldk row-major bases
+  const T* C; const T* Ct; const T* U; const T* Ut; int ldk;   // n x ldk row-major bases U, Ut
+  int ldc;   // row stride of C, Ct as the iteration kernels see them: the system's kc columns
+             // rounded up to 4 (a compact copy when that is below ldk), so the projections
+             // skip the columns the Section 4.3 truncation dropped
 };
 
 // Per-request arguments of a batched iteration launch: request r owns the blocks
@@ -165,6 +168,8 @@ void launch_rotate(T* B, int ld, const zd* Nmat, const int* kin_dev, const int* 
                    int fp32, cudaStream_t s);
 template <class Tfrom, class Tto>
 void launch_convert(const Tfrom* a, Tto* b, int64_t n, cudaStream_t s);
+template <class T>
+void launch_pack_cols(const T* src, int lds, T* dst, int ldd, int kc, int64_t n, cudaStream_t s);   // dst[:, :ldd] = [src[:, :kc] 0]
 template <class T>
 void launch_axpy_inplace(T* y, const T* x, int64_t n, cudaStream_t s);   // y += x
 

@@ -422,7 +422,7 @@ __device__ __forceinline__ void phase2_body(const OpArgs<V> op, const VecArgs<T>
       // q = z - C zeta, qt = zt - Ct zetat, columns in ascending order.  A slice's 8 entries of
       // a row are 64 contiguous bytes, so each warp load reads 4 rows in whole sectors.
       const int nvalid = r1 - base < 32 ? r1 - base : 32;
-      const int ldk = v.ldk;
+      const int ldk = v.ldc;
       T* sg = stg[warp];
 #pragma unroll 1
       for (int c0 = 0; c0 < KA; c0 += 8) {
@@ -587,8 +587,8 @@ __global__ void __launch_bounds__(NTHREADS) k_init_a(OpArgs<V> op, VecArgs<T> v,
     rt[row] = rest;
     nbt += A((double)abs2(v.bt[row]));
     if (KT > 0) {
-      const T* __restrict__ crow = v.C + (int64_t)row * v.ldk;
-      const T* __restrict__ ctrow = v.Ct + (int64_t)row * v.ldk;
+      const T* __restrict__ crow = v.C + (int64_t)row * v.ldc;
+      const T* __restrict__ ctrow = v.Ct + (int64_t)row * v.ldc;
 #pragma unroll
       for (int c = 0; c < KA; ++c)
         if (c < k) { a1[c] += cmul(ctrow[c], res); a2[c] += cmul(crow[c], rest); }
@@ -634,14 +634,14 @@ __global__ void __launch_bounds__(NTHREADS) k_init_b(OpArgs<V> op, VecArgs<T> v,
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += stride) {
     T a = r[row], b = rt[row];
     if (KT > 0) {
-      const int64_t o = (int64_t)row * v.ldk;
+      const int64_t o = (int64_t)row * v.ldk, oc = (int64_t)row * v.ldc;
       T dx = T(0), dr = T(0), dxt = T(0), drt = T(0);
 #pragma unroll
       for (int c = 0; c < KA; ++c)
         if (c < k) {
-          if (!dual_only) { dx += v.U[o + c] * cf[c]; dr += v.C[o + c] * cf[c]; }
+          if (!dual_only) { dx += v.U[o + c] * cf[c]; dr += v.C[oc + c] * cf[c]; }
           dxt += v.Ut[o + c] * cft[c];
-          drt += v.Ct[o + c] * cft[c];
+          drt += v.Ct[oc + c] * cft[c];
         }
       if (!dual_only) { v.x[row] = v.x[row] + dx; a = a - dr; r[row] = a; }
       v.xt[row] = v.xt[row] + dxt;
@@ -868,6 +868,25 @@ __global__ void k_sort_rows(int n, const int* trp, int* tci, V* tva) {
   }
 }
 
+// dst row r = src row r's first kc entries, zero-padded to ldd (the compact projection bases)
+template <class T>
+__global__ void k_pack_cols(const T* __restrict__ src, int lds, T* __restrict__ dst, int ldd, int kc, int64_t n) {
+  const int64_t total = n * ldd;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / ldd;
+    const int c = (int)(e - r * ldd);
+    dst[e] = c < kc ? src[r * lds + c] : T(0);
+  }
+}
+template <class T>
+void launch_pack_cols(const T* src, int lds, T* dst, int ldd, int kc, int64_t n, cudaStream_t s) {
+  k_pack_cols<T><<<1024, 256, 0, s>>>(src, lds, dst, ldd, kc, n);
+}
+template void launch_pack_cols<double>(const double*, int, double*, int, int, int64_t, cudaStream_t);
+template void launch_pack_cols<float>(const float*, int, float*, int, int, int64_t, cudaStream_t);
+template void launch_pack_cols<zd>(const zd*, int, zd*, int, int, int64_t, cudaStream_t);
+template void launch_pack_cols<cplx<float>>(const cplx<float>*, int, cplx<float>*, int, int, int64_t, cudaStream_t);
+
 // ------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------
@@ -906,7 +925,7 @@ void launch_phase1(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void*
                    cudaStream_t s) {
   typedef typename traits<T>::acc A;
   // kt == 0: no recycle space (no projection); otherwise dispatch on the bases' row stride
-  const int ld = kt == 0 ? 0 : v.ldk;
+  const int ld = kt == 0 ? 0 : v.ldc;
 #define RB_CALL(L) launch_phase_kernel(k_phase1<V, T, L>, grid, s, op, v, st, (A*)part)
   switch (ld) {
     case 0: RB_CALL(0); break;
