@@ -91,6 +91,18 @@ template <class R> RB_HD cplx<R> cmul(cplx<R> a, cplx<R> b) {
   return {fmar(a.re, b.re, mul_rn(a.im, b.im)), fmar(a.re, b.im, -mul_rn(a.im, b.re))};
 }
 
+// 1 / z as conj(z) / |z|^2: one real division.  A dependent FP64 operation costs about 60
+// cycles on this part, a division about 570 and the scaled (Smith) complex quotient about
+// 2000, so the quotients on critical paths (pivots, reflector factors, the iteration scalars
+// alpha and beta) use this form; |z|^2 falls back to the scaled quotient when it would over- or
+// underflow.
+__device__ __forceinline__ cplx<double> crcp(cplx<double> z) {
+  const double n2 = fma(z.re, z.re, z.im * z.im);
+  if (!(n2 > 1e-290 && n2 < 1e290)) return cplx<double>(1.0) / z;
+  const double d = 1.0 / n2;
+  return cplx<double>(z.re * d, -z.im * d);
+}
+
 RB_HD bool finite_of(double a) { return isfinite(a); }
 template <class R> RB_HD bool finite_of(cplx<R> a) { return isfinite(a.re) && isfinite(a.im); }
 

@@ -218,16 +218,6 @@ __device__ __forceinline__ float cabs_(zf a) { return hypotf(a.re, a.im); }
 // sqrt(2) of the modulus).  FP64 hypot costs dozens of FP64 instructions on this part.
 __device__ __forceinline__ double cabs1_(zd a) { return fabs(a.re) + fabs(a.im); }
 __device__ __forceinline__ float cabs1_(zf a) { return fabsf(a.re) + fabsf(a.im); }
-// 1 / z as conj(z) / |z|^2: one real division.  A dependent FP64 operation costs about 60
-// cycles on this part, a division about 570 and the scaled (Smith) complex quotient about
-// 2000, so pivots and reflector factors on the dense kernels' critical paths use this form;
-// |z|^2 falls back to the scaled quotient when it would over- or underflow.
-__device__ __forceinline__ zd crcp(zd z) {
-  const double n2 = fma(z.re, z.re, z.im * z.im);
-  if (!(n2 > 1e-290 && n2 < 1e290)) return zd(1.0) / z;
-  const double d = 1.0 / n2;
-  return zd(z.re * d, -z.im * d);
-}
 
 // Selection of eigenvalue indices (reading: k closest to the origin; on a real problem a
 // conjugate pair is one unit of two columns, k-1 columns if it straddles the cut).

@@ -170,6 +170,25 @@ __device__ bool grid_reduce(A* tot, A* part, unsigned int* ctr, Blk g) {
   return true;
 }
 
+// Deterministic one-level grid reduction of three values per block (the iteration scalars):
+// every block writes its row, the last to arrive sums all rows -- thread t the rows t, t + 256,
+// ..., one round of independent loads -- and combines the threads' sums with block_sum3.  One
+// arrival instead of the two of grid_reduce: for three values the rows of all blocks are few
+// enough to read at once.  tot and red as in block_sum3; the grand totals land in tot.
+template <class A>
+__device__ bool grid_reduce3(A* tot, A* red, A* part, unsigned int* ctr, Blk g) {
+  if (threadIdx.x < 3) part[(int64_t)g.id * 3 + threadIdx.x] = tot[threadIdx.x];
+  if (!arrive_last(&ctr[GMAX], g.n)) return false;
+  A s0 = A(0.0), s1 = A(0.0), s2 = A(0.0);
+  for (int b = threadIdx.x; b < g.n; b += NTHREADS) {
+    s0 += ld_cg(part + (int64_t)b * 3);
+    s1 += ld_cg(part + (int64_t)b * 3 + 1);
+    s2 += ld_cg(part + (int64_t)b * 3 + 2);
+  }
+  block_sum3(s0, s1, s2, red, tot);
+  return true;
+}
+
 // The three sums of one row that decide alpha_i: (pt_i, q_i), ||q_i||^2, ||pt_i||^2.
 template <class A, class T>
 __device__ __forceinline__ void alpha_terms(A& pq, A& nq, A& npt, T ptr, T q) {
@@ -181,23 +200,28 @@ __device__ __forceinline__ void alpha_terms(A& pq, A& nq, A& npt, T ptr, T q) {
 // In the block that finished the (pt, q) reduction (tot = the three sums): alpha_i =
 // rho_{i-1} / (pt_i, q_i) with the finiteness and breakdown tests, then zeta_c += alpha zeta
 // and zetat_c += conj(alpha) zetat for the k recycle columns (Algorithm 2).
+// rho_prev: st->rho, read at the start of the kernel (it does not change during it).
 template <class A>
-__device__ void finish_alpha(DevState* st, const A* tot, int i, int k) {
+__device__ void finish_alpha(DevState* st, const A* tot, int i, int k, zd rho_prev) {
+  __shared__ int s_stop;
   if (threadIdx.x == 0) {
     const zd PQ = to_zd(tot[0]);
     const double NQ = real_of(tot[1]), NPT = real_of(tot[2]);
+    int stop = 0;
     if (!isfinite(PQ.re) || !isfinite(PQ.im) || !isfinite(NQ) || !isfinite(NPT)) {
-      st->done = DONE_NONFINITE;
-    } else if (absval(PQ) <= BREAKDOWN_EPS * sqrt(NQ) * sqrt(NPT)) {
-      st->done = DONE_BREAK_PQ;
+      stop = DONE_NONFINITE;
+    } else if (abs2(PQ) <= (BREAKDOWN_EPS * NQ) * (BREAKDOWN_EPS * NPT)) {   // |PQ| <= eps ||q|| ||pt||
+      stop = DONE_BREAK_PQ;
     } else {
-      const zd al = st->rho / PQ;
+      const zd al = rho_prev * crcp(PQ);
       st->alpha = al;
       st->h_alpha[i % HR] = al;
     }
+    if (stop) st->done = stop;
+    s_stop = stop;
   }
   __syncthreads();
-  if (st->done) return;
+  if (s_stop) return;
   if (threadIdx.x < k) {
     const zd al = st->alpha;
     const int c = threadIdx.x;
@@ -294,6 +318,7 @@ __device__ __forceinline__ void phase1_body(const OpArgs<V> op, const VecArgs<T>
   if (st->done) return;
   const int i = st->iter + 1;
   const T beta = from_zd<T>(st->beta), cbeta = conjg(beta);
+  const zd rho_prev = st->rho;   // for alpha when this launch finishes it
   const int64_t so = (int64_t)((i - 1) % v.R) * v.ld;
   const T* __restrict__ r = v.ring + so;
   const T* __restrict__ rt = v.ringt + so;
@@ -363,8 +388,8 @@ __device__ __forceinline__ void phase1_body(const OpArgs<V> op, const VecArgs<T>
   pdl_release();
   if (LD == 0) {
     block_sum3(pq, nq, npt, red, tot);
-    if (!grid_reduce<A, 3>(tot, part, st->gcnt, g)) return;
-    finish_alpha(st, tot, i, 0);
+    if (!grid_reduce3(tot, red, part, st->gcnt, g)) return;
+    finish_alpha(st, tot, i, 0, rho_prev);
     return;
   }
 #pragma unroll
@@ -402,6 +427,7 @@ __device__ __forceinline__ void phase2_body(const OpArgs<V> op, const VecArgs<T>
   if (st->done) return;
   const int i = st->iter + 1;
   const int k = KT > 0 ? st->kc : 0;
+  const zd rho_prev = st->rho;
   for (int c = threadIdx.x; c < KA; c += blockDim.x) {
     ze[c] = c < k ? from_zd<T>(st->zeta[c]) : T(0);
     zet[c] = c < k ? from_zd<T>(st->zetat[c]) : T(0);
@@ -455,8 +481,8 @@ __device__ __forceinline__ void phase2_body(const OpArgs<V> op, const VecArgs<T>
   }
   pdl_release();
   block_sum3(pq, nq, npt, red, tot);
-  if (!grid_reduce<A, 3>(tot, part, st->gcnt, g)) return;
-  finish_alpha(st, tot, i, k);
+  if (!grid_reduce3(tot, red, part, st->gcnt, g)) return;
+  finish_alpha(st, tot, i, k, rho_prev);
 }
 
 // ------------------------------------------------------------------------------------
@@ -472,6 +498,10 @@ __device__ __forceinline__ void phase3_body(const OpArgs<V> op, const VecArgs<T>
   if (st->done) return;
   const int i = st->iter + 1;
   const T al = from_zd<T>(st->alpha), cal = conjg(al);
+  // scalars of the finishing block, read up front (the kernel does not change them)
+  const zd rho_prev = st->rho;
+  const double tol = st->tol, bnorm = st->bnorm, btnorm = st->btnorm;
+  const int max_itn = st->max_itn;
   const int64_t so = (int64_t)((i - 1) % v.R) * v.ld, sn = (int64_t)(i % v.R) * v.ld;
   const T* __restrict__ ro = v.ring + so;
   const T* __restrict__ rto = v.ringt + so;
@@ -495,22 +525,22 @@ __device__ __forceinline__ void phase3_body(const OpArgs<V> op, const VecArgs<T>
   }
   pdl_release();
   block_sum3(rho, n1, n2, red, tot);
-  if (!grid_reduce<A, 3>(tot, part, st->gcnt, g)) return;
+  if (!grid_reduce3(tot, red, part, st->gcnt, g)) return;
   if (threadIdx.x == 0) {
     const zd RHO = to_zd(tot[0]);
     const double rr = sqrt(real_of(tot[1])), rtr = sqrt(real_of(tot[2]));
-    const zd beta = RHO / st->rho;
+    const zd beta = RHO * crcp(rho_prev);
     st->h_rnorm[i % HR] = rr;
     st->h_rho[i % HR] = RHO;
     st->h_beta[i % HR] = beta;
     st->rnorm = rr;
     st->rtnorm = rtr;
     st->iter = i;
-    const bool conv = rr <= st->tol * st->bnorm && (st->btnorm == 0.0 || rtr <= st->tol * st->btnorm);
+    const bool conv = rr <= tol * bnorm && (btnorm == 0.0 || rtr <= tol * btnorm);
     if (!isfinite(rr) || !isfinite(rtr) || !isfinite(RHO.re) || !isfinite(RHO.im)) st->done = DONE_NONFINITE;
     else if (conv) st->done = DONE_CONVERGED;
-    else if (absval(RHO) <= BREAKDOWN_EPS * rr * rtr) st->done = DONE_BREAK_RHO;
-    else if (i >= st->max_itn) st->done = DONE_MAXIT;
+    else if (abs2(RHO) <= (BREAKDOWN_EPS * rr * rtr) * (BREAKDOWN_EPS * rr * rtr)) st->done = DONE_BREAK_RHO;
+    else if (i >= max_itn) st->done = DONE_MAXIT;
     st->rho = RHO;
     st->beta = beta;
   }
