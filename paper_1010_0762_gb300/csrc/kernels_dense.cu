@@ -124,8 +124,8 @@ __device__ int phi_ycol(const Layout& L, int b) {
 constexpr int64_t W_HD = 0, W_HTD = W_HD + PSIMAX * MMAX, W_GH = W_HTD + PSIMAX * MMAX,
                   W_L = W_GH + PSIMAX * MMAX, W_R = W_L + MMAX * MMAX,
                   W_H = W_R + MMAX * MMAX, W_QV = W_H + MMAX * MMAX, W_QF = W_QV + MMAX * MMAX,
-                  W_RI = W_QF + MMAX,
-                  W_Y = W_RI + MMAX * MMAX, W_YL = W_Y + MMAX * (KMAX + 8), W_LAM = W_YL + MMAX * (KMAX + 8),
+                  W_RI = W_QF + MMAX, W_Q = W_RI + MMAX * MMAX,
+                  W_Y = W_Q + MMAX * MMAX, W_YL = W_Y + MMAX * (KMAX + 8), W_LAM = W_YL + MMAX * (KMAX + 8),
                   W_LAM2 = W_LAM + KMAX + 8, W_INT = W_LAM2 + KMAX + 8,
                   W_END = W_INT + (MMAX + 2 * KMAX + 8 + 3) / 4 + 1;
 static_assert(PSIMAX * MMAX >= 2 * MMAX * KMAX, "k_eig_c keeps the selected vectors in the GH area");
@@ -653,7 +653,34 @@ k_eig_cl(RefreshInfo f, DevState* st, zd* work, int has_R, int m) {
   }
   __threadfence();
   cl.sync();   // every CTA's writes are visible; no shared memory of another CTA is read after this
-  if (rank != 0) return;
+  if (rank != 0) {
+    // CTAs 1 .. ECL-1, while CTA 0 runs the QR: Q = P_0 P_1 ... P_{m-3} explicitly, column c =
+    // Q e_c with the reflectors applied last to first (P_j leaves e_c alone for j >= c), one
+    // warp per column in shared memory.  k_eig_h then back-transforms with one dense product
+    // instead of m - 2 dependent reflector applications.
+    if (failed) return;
+    const zd* QVg = work + W_QV;
+    const zd* QFg = work + W_QF;
+    zd* Qg = work + W_Q;
+    zd* yv = reinterpret_cast<zd*>(smraw) + warp * MMAX;   // the local columns are done with
+    for (int c = (rank - 1) * nwarp + warp; c < m; c += (ECL - 1) * nwarp) {
+      for (int i = lane; i < m; i += 32) yv[i] = i == c ? zd(1.0) : zd();
+      __syncwarp();
+      for (int j = min(m - 3, c - 1); j >= 0; --j) {
+        const zd fj = QFg[j];
+        if (fj.re == 0.0 && fj.im == 0.0) continue;
+        const int len = m - j - 1;
+        zd w = zd();
+        for (int i = lane; i < len; i += 32) w += cmul(QVg[i + j * MMAX], yv[j + 1 + i]);
+        w = bcast0(warp_sum(w)) * fj;
+        for (int i = lane; i < len; i += 32) yv[j + 1 + i] -= QVg[i + j * MMAX] * w;
+        __syncwarp();
+      }
+      for (int i = lane; i < m; i += 32) Qg[i + c * MMAX] = yv[i];
+      __syncwarp();
+    }
+    return;
+  }
   if (failed) {
     if (tid == 0) { st->eig_status = 1; st->kk = 0; *ei.ncand = 0; }
     return;
@@ -786,22 +813,6 @@ __device__ void hess_solve_adj_warp(const zd* A, int m, const int* sw, const zd*
   __syncwarp();
 }
 
-// One warp: y <- Q y, Q = P_0 P_1 ... P_{m-3} (P_j = I - f_j v_j v_j^H on rows j+1..m-1).
-__device__ void apply_q_warp(const zd* QV, const zd* QF, int m, zd* y) {
-  const int lane = threadIdx.x & 31;
-  for (int j = m - 3; j >= 0; --j) {
-    const zd fj = QF[j];
-    if (fj.re == 0.0 && fj.im == 0.0) continue;
-    const int len = m - j - 1;
-    zd w = zd();
-    for (int i = lane; i < len; i += 32) w += cmul(QV[i + j * MMAX], y[j + 1 + i]);
-    w = warp_sum(w);
-    w = zd(__shfl_sync(0xffffffffu, w.re, 0), __shfl_sync(0xffffffffu, w.im, 0)) * fj;
-    for (int i = lane; i < len; i += 32) y[j + 1 + i] -= QV[i + j * MMAX] * w;
-    __syncwarp();
-  }
-}
-
 // One warp: largest |re| + |im| scaled to 1 (t -> y)
 __device__ void normalise_warp(const zd* t, zd* y, int m) {
   const int lane = threadIdx.x & 31;
@@ -893,10 +904,17 @@ __global__ void __launch_bounds__(64) k_eig_h(zd* work, int m, int has_R) {
   }
   __syncthreads();
   // pencil vectors: y = Q z (warp 0); yl = R^{-H} Q zl (warp 1)
-  if (warp == 0) {
-    apply_q_warp(work + W_QV, work + W_QF, m, z);
-  } else {
-    apply_q_warp(work + W_QV, work + W_QF, m, zl);
+  {
+    // y = Q z (warp 0), Q zl (warp 1): dense products with the Q that k_eig_cl formed
+    zd* src = warp == 0 ? z : zl;
+    zd* tmp = warp == 0 ? t : tl;
+    const zd* Qg = work + W_Q;
+    for (int r = lane; r < m; r += 32) tmp[r] = dot4(0, m, [&](int c) { return Qg[r + c * MMAX] * src[c]; });
+    __syncwarp();
+    for (int r = lane; r < m; r += 32) src[r] = tmp[r];
+    __syncwarp();
+  }
+  if (warp == 1) {
     if (has_R) {
       const zd* RI = work + W_RI;
       for (int r = lane; r < m; r += 32) {
