@@ -113,57 +113,13 @@ template <> struct traits<float> { typedef float real; typedef double acc; stati
 template <> struct traits<cplx<double>> { typedef double real; typedef cplx<double> acc; static const bool cx = true; };
 template <> struct traits<cplx<float>> { typedef float real; typedef cplx<double> acc; static const bool cx = true; };
 
-// double <-> float on the integer pipes.  A conversion instruction runs on the FP64 unit (2
-// lanes per clock per SM on this part), which made the FP32-compute kernels that read FP64 data
-// conversion-bound.  Normal-range values and zeros take integer paths with the same result as
-// the conversion instruction (round to nearest even for double -> float; float -> double is
-// exact); everything else (float subnormals, overflow, inf, nan) uses the instruction.
-__device__ __forceinline__ float d2f(double x) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
-  const unsigned a = hi & 0x7fffffffu;
-  if (a - 0x38100000u < 0x47f00000u - 0x38100000u) {      // 2^-126 <= |x| < 2^128
-    unsigned m = ((a - 0x38000000u) << 3) | (lo >> 29);      // rebiased exponent, 23 mantissa bits
-    const unsigned rest = lo & 0x1fffffffu;                  // the 29 bits dropped
-    m += (unsigned)(rest > 0x10000000u) | ((unsigned)(rest == 0x10000000u) & m);   // to nearest even
-    return __uint_as_float(m | (hi & 0x80000000u));
-  }
-  if ((a | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
-  return __double2float_rn(x);
-}
-__device__ __forceinline__ double f2d(float f) {
-  const unsigned b = __float_as_uint(f), a = b & 0x7fffffffu;
-  if (a - 0x00800000u < 0x7f800000u - 0x00800000u)          // normal
-    return __hiloint2double((int)((b & 0x80000000u) | ((a >> 3) + 0x38000000u)), (int)(a << 29));
-  if (a == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
-  return (double)f;
-}
-RB_HD float to_f32(double x) {
-#ifdef __CUDA_ARCH__
-  return d2f(x);
-#else
-  return (float)x;
-#endif
-}
-RB_HD double to_f64(float x) {
-#ifdef __CUDA_ARCH__
-  return f2d(x);
-#else
-  return (double)x;
-#endif
-}
-
 // Conversions between storage, compute and accumulation types.
 template <class To, class From> struct conv;
 template <class From> struct conv<double, From> { static RB_HD double f(From a) { return (double)a; } };
 template <class From> struct conv<float, From> { static RB_HD float f(From a) { return (float)a; } };
-template <> struct conv<double, float> { static RB_HD double f(float a) { return to_f64(a); } };
-template <> struct conv<float, double> { static RB_HD float f(double a) { return to_f32(a); } };
-template <class R, class S> struct conv<cplx<R>, cplx<S>> {
-  static RB_HD cplx<R> f(cplx<S> a) { return cplx<R>(conv<R, S>::f(a.re), conv<R, S>::f(a.im)); }
-};
-template <class R> struct conv<cplx<R>, double> { static RB_HD cplx<R> f(double a) { return cplx<R>(conv<R, double>::f(a), (R)0); } };
-template <class R> struct conv<cplx<R>, float> { static RB_HD cplx<R> f(float a) { return cplx<R>(conv<R, float>::f(a), (R)0); } };
+template <class R, class S> struct conv<cplx<R>, cplx<S>> { static RB_HD cplx<R> f(cplx<S> a) { return cplx<R>((R)a.re, (R)a.im); } };
+template <class R> struct conv<cplx<R>, double> { static RB_HD cplx<R> f(double a) { return cplx<R>((R)a, (R)0); } };
+template <class R> struct conv<cplx<R>, float> { static RB_HD cplx<R> f(float a) { return cplx<R>((R)a, (R)0); } };
 template <class To, class From> RB_HD To cvt(From a) { return conv<To, From>::f(a); }
 
 // Value * vector-type product where the value may be real and the vector complex.
