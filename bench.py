@@ -251,11 +251,12 @@ def gpu_arm(a):
     hbm_frac = ach_gbs / hbm_peak
     bound = "alu" if alu_frac >= hbm_frac else "hbm"
     launches_phase1 = cnt_slots[0]
-    # DRAM traffic of one k_phase1<double, double, 20> launch on this operator (ncu
-    # dram__bytes_read.sum + dram__bytes_write.sum; summary kept with the profiles) against
-    # the algorithmic bytes of the same launch
-    traffic_k20 = 119.649792e6 + 6.948352e6
-    alg_k20 = algorithmic_phase1(n, nnz, 20)[1]
+    # DRAM traffic of one recycled k_phase1 launch on this operator, the compact bases four
+    # columns wide (k_phase1<double, double, 4>: ncu dram__bytes_read.sum +
+    # dram__bytes_write.sum; summary kept with the profiles), against the algorithmic bytes of
+    # the same launch
+    traffic_k4 = 52.440576e6 + 0.253952e6
+    alg_k4 = algorithmic_phase1(n, nnz, 4)[1]
     roofline = {
         "kernel": "k_phase1 (dual SpMV + p update + Ct^H z, C^H zt)",
         "bound": bound,
@@ -265,8 +266,9 @@ def gpu_arm(a):
         "frac": round(alu_frac if bound == "alu" else hbm_frac, 4),
         "peak_source": ("FP64 FMA units: 2 DFMA/clock/SM x %d SMs at the sampled %.0f MHz" % (sms, sm_mhz)
                         if bound == "alu" else "MEASURED_PEAKS.json hbm_gbs (of measured)"),
-        "traffic": traffic_k20 if n == 262144 and nnz == 1308672 else None,
-        "traffic_note": "bytes of one k=20 launch at 512^2 (ncu); algorithmic %.1f MB" % (alg_k20 / 1e6),
+        "traffic": traffic_k4 if n == 262144 and nnz == 1308672 else None,
+        "traffic_note": "bytes of one recycled launch (bases 4 columns wide) at 512^2 (ncu); "
+                        "algorithmic %.1f MB" % (alg_k4 / 1e6),
         "hbm_view": {"achieved_gbs": round(ach_gbs, 1), "peak_gbs": hbm_peak, "frac": round(hbm_frac, 4)},
         "alu_view": {"achieved_tflops": round(ach_tf, 4), "peak_tflops": round(fp64_peak, 4),
                      "frac": round(alu_frac, 4), "dgemm_tflops_measured": round(dgemm, 4)},
