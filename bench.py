@@ -295,7 +295,7 @@ def gpu_arm(a):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic (seeded convection-diffusion sequence; see DESIGN.md input recipe)",
+        "data": "synthetic (seeded convection-diffusion sequence, paper_1010_0762_gb300.inputs.convdiff_sequence)",
         "config": {"workload": WORKLOAD, "grid": a.grid, "n": n, "nnz": nnz, "pairs": a.pairs, "k": a.k,
                    "s": a.s, "tol": a.tol, "drift": 0.01, "form": "plain FP64 RBiCG",
                    "l2": "256 MB flush between steps; working set > L2", "parallelism": "replicas"},
