@@ -533,7 +533,9 @@ def reference_arm(a):
     cpu = {"value": round(value, 6), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
            "sample": "each step: oracle RBiCG on one pair for %d iterations; solves/s = 1 / (seconds per "
                      "iteration x %d, the oracle's own iteration count for a full solve of pair 0)" % (its, n_ref)}
-    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": 0,
+    # n_gpus: the launch's N (the oracle itself runs on rank 0's host cores, see cpu_baseline)
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s",
+           "n_gpus": int(os.environ.get("WORLD_SIZE", str(a.gpus))),
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(1e3 * tot / max(1, a.steps), 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": a.grid, "pairs": a.pairs, "k": a.k,

@@ -28,7 +28,7 @@
  *    the tolerance (x then holds the last iterate); a negative status for an error, in
  *    which case outputs are unspecified and rbicg_last_error() describes it.  No call
  *    traps, aborts or exits; device-side waits are bounded.
- *  - Environment switches (read once per process; none changes any result):
+ *  - Environment switches (read when first needed; none changes any result):
  *    RBICG_NO_GRAPHS: launch each cycle's iteration kernels one by one instead of as a CUDA
  *    graph (profilers then see and select the individual kernels); RBICG_NO_PDL: launch the
  *    iteration kernels without programmatic stream serialization; RBICG_DEBUG: print one
