@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--k", type=int, default=20)
     ap.add_argument("--s", type=int, default=40)
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--grid-blocks", type=int, default=0,
+                    help="blocks per iteration-phase launch (0: the library default)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32-refined, BiCG and e2e passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -214,7 +216,7 @@ def gpu_arm(a):
         return total_ms, results, ck, prof, launches
 
     # --- plain FP64 RBiCG (the configuration's own form) ---
-    S = R.Solver(n, k=a.k, s=a.s, tol=a.tol)
+    S = R.Solver(n, k=a.k, s=a.s, tol=a.tol, grid_blocks=a.grid_blocks)
     ms64, res64, clocks, prof, launches = timed(S, a.steps, a.warmup, profile=True)
     pairs_done = a.pairs * a.steps
     value = replica_value(world, pairs_done, ms64)
@@ -310,7 +312,8 @@ def gpu_arm(a):
 
     if not a.no_extras:
         # --- chosen form: FP64 iterative refinement around FP32 inner RBiCG ---
-        S32 = R.Solver(n, k=a.k, s=a.s, tol=a.tol, precision="fp32_refined", inner_tol=1e-5)
+        S32 = R.Solver(n, k=a.k, s=a.s, tol=a.tol, precision="fp32_refined", inner_tol=1e-5,
+                       grid_blocks=a.grid_blocks)
         ms32, res32, _, _, _ = timed(S32, a.steps, 1)
         out["chosen"] = {"form": "fp32_refined (FP32 inner RBiCG, FP64 residual refinement)",
                          "value": round(world * pairs_done / (ms32 * 1e-3), 4), "unit": "solves/s",
@@ -321,7 +324,7 @@ def gpu_arm(a):
                          "fp64_fallback_pairs": sum(1 for r in res32[:a.pairs] if r["fallback"] == 2),
                          "worst_true_relres": max(max(r["true_relres"], r["true_relres_dual"]) for r in res32)}
         # --- non-recycling BiCG on the same sequence ---
-        Sb = R.Solver(n, k=a.k, s=a.s, tol=a.tol, recycle=0)
+        Sb = R.Solver(n, k=a.k, s=a.s, tol=a.tol, recycle=0, grid_blocks=a.grid_blocks)
         msb, resb, _, _, _ = timed(Sb, 1, 1)
         out["bicg"] = {"value": round(world * a.pairs / (msb * 1e-3), 4), "unit": "solves/s",
                        "iters_per_pair": [r["iters"] for r in resb[:a.pairs]]}
@@ -335,7 +338,7 @@ def gpu_arm(a):
         hxt = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in seq]
         dvals = [torch.empty_like(o.val) for o in ops]
         drp, dci = torch.empty_like(rp), torch.empty_like(ci)
-        Se = R.Solver(n, k=a.k, s=a.s, tol=a.tol)
+        Se = R.Solver(n, k=a.k, s=a.s, tol=a.tol, grid_blocks=a.grid_blocks)
         e_steps = max(1, a.steps // 2)
         h2d = d2h = 0
         torch.cuda.synchronize()
