@@ -209,11 +209,9 @@ __global__ void k_t1(RefreshInfo f, const DevState* st, zd* work) {
 }
 
 // ------------------------------------------------------------------------------------
-// one-block dense eigen solver (complex FP64)
+// dense eigen pipeline: shared helpers and the eigenvalue selection
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ double cabs_(zd a) { return hypot(a.re, a.im); }
 typedef cplx<float> zf;
-__device__ __forceinline__ float cabs_(zf a) { return hypotf(a.re, a.im); }
 // |re| + |im|: the pivot and scale measure of complex LU (no square root; within a factor
 // sqrt(2) of the modulus).  FP64 hypot costs dozens of FP64 instructions on this part.
 __device__ __forceinline__ double cabs1_(zd a) { return fabs(a.re) + fabs(a.im); }
