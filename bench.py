@@ -225,6 +225,8 @@ def gpu_arm(a):
     ok = all(r["status"] in (R.OK, R.RECYCLE_EMPTY) for r in res64)
     worst_true = max(max(r["true_relres"], r["true_relres_dual"]) for r in res64)
     kcs = [r["recycle_dim"] for r in per_step]
+    # 1 where the stagnation guard dropped the recycle space mid-solve (recycle_dim then reads 0)
+    fbs = [r["fallback"] for r in per_step]
 
     # roofline of the dominant kernel (phase 1: dual SpMV + projections) from live CUDA events
     names = ["dual_spmv_project", "q_and_pq", "update_dots", "refresh_gram", "refresh_eig",
@@ -303,6 +305,7 @@ def gpu_arm(a):
                    "l2": "256 MB flush between steps; working set > L2", "parallelism": "replicas"},
         "iters_per_pair": iters,
         "recycle_dim_per_pair": kcs,
+        "guard_fallback_per_pair": fbs,
         "all_converged": ok,
         "worst_true_relres": worst_true,
         "roofline": roofline,
