@@ -2,8 +2,9 @@
 // of eq. (minusXR), the final correction of step 7, the true residual, the random restart of
 // step 3 and the construction of A^H.
 //
-// One iteration i = three grid-wide passes, each ending in a deterministic last-block
-// reduction that writes the scalars of the next pass into DevState:
+// One iteration i = three grid-wide passes (two without a recycle space, where phase 1 also
+// does phase 2's reduction), each ending in a deterministic grid reduction whose finishing block
+// writes the scalars of the next pass into DevState:
 //   phase 1: p_i = r_{i-1} + beta_{i-1} p_{i-1}, pt_i likewise (formed while gathering),
 //            z_i = Op p_i, zt_i = Op^H pt_i, and the projections
 //            zeta_i = D_c^{-1} Ct^H z_i, zetat_i = D_c^{-1} C^H zt_i        (eq. (CcheckChat))
