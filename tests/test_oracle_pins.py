@@ -363,3 +363,27 @@ def test_conjugate_shift_symmetry():
         out.append(r)
     np.testing.assert_allclose(out[1].x, np.conj(out[0].x), rtol=0, atol=1e-9 * np.linalg.norm(out[0].x))
     np.testing.assert_allclose(out[1].xt, np.conj(out[0].xt), rtol=0, atol=1e-9 * np.linalg.norm(out[0].xt))
+
+
+def test_exact_invariant_subspace_deflates():
+    # Section 3: with U spanning an exact invariant subspace of A (and Ut one of A^H), the
+    # augmented bi-Lanczos iteration works on the deflated operator, so Algorithm 2 needs fewer
+    # iterations than BiCG, and more deflated eigenvalues save more (k = 5, 10 at 48^2)
+    import scipy.sparse.linalg as ssla
+
+    pr = I.convdiff_sequence(48, [10.0, 10.0], 2, 0.01, 7, bt_kind="normal")[1]
+    A = O.as_scipy(pr["A"]).tocsc()
+    n = A.shape[0]
+    z = np.zeros(n)
+    base = O.bicg(A, pr["b"], pr["bt"], z, z, 1e-8, 5000)
+    its = []
+    for k in (5, 10):
+        _, V = ssla.eigs(A, k=k, sigma=0.0, which="LM", v0=np.ones(n))
+        _, W = ssla.eigs(A.T.conj().tocsc(), k=k, sigma=0.0, which="LM", v0=np.ones(n))
+        rec = O.biorth_recycle(A, np.real(V), np.real(W), 1e-6)
+        assert rec[0].shape[1] == k
+        r = O.rbicg_pair(A, pr["b"], pr["bt"], z, z, recycle=rec, k=k, s=40, tol=1e-8, max_itn=5000,
+                         refresh=False)
+        assert r.status == O.STATUS_OK
+        its.append(r.iters)
+    assert its[0] < 0.95 * base.iters and its[1] < its[0], (base.iters, its)
