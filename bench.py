@@ -25,7 +25,11 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "dual-pair solves/s at rel.res 1e-8, chosen vs plain FP64; HBM GB/s; p99 ms"
-WORKLOAD = "convdiff2d-512x512-seq20-k20"
+
+
+def workload_name(a):
+    """Name of the timed workload from its sizes (default: convdiff2d-512x512-seq20-k20)."""
+    return "convdiff2d-%dx%d-seq%d-k%d" % (a.grid, a.grid, a.pairs, a.k)
 
 
 def parse():
@@ -300,7 +304,7 @@ def gpu_arm(a):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded convection-diffusion sequence, paper_1010_0762_gb300.inputs.convdiff_sequence)",
-        "config": {"workload": WORKLOAD, "grid": a.grid, "n": n, "nnz": nnz, "pairs": a.pairs, "k": a.k,
+        "config": {"workload": workload_name(a), "grid": a.grid, "n": n, "nnz": nnz, "pairs": a.pairs, "k": a.k,
                    "s": a.s, "tol": a.tol, "drift": 0.01, "form": "plain FP64 RBiCG",
                    "l2": "256 MB flush between steps; working set > L2", "parallelism": "replicas"},
         "iters_per_pair": iters,
@@ -544,7 +548,7 @@ def reference_arm(a):
            "n_gpus": int(os.environ.get("WORLD_SIZE", str(a.gpus))),
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(1e3 * tot / max(1, a.steps), 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "grid": a.grid, "pairs": a.pairs, "k": a.k,
+           "data": "synthetic", "config": {"workload": workload_name(a), "grid": a.grid, "pairs": a.pairs, "k": a.k,
                                            "s": a.s, "tol": a.tol},
            "cpu_baseline": cpu, "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
