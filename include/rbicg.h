@@ -229,7 +229,8 @@ int64_t rbicg_launch_count(rbicg_handle h);
  * taken with CUDA events on the handle's stream.  enable = 1 starts collection (clearing the
  * accumulators), 0 stops it, -1 only reads.  ms_out / launches_out (host arrays of
  * RBICG_NPROF, may be NULL) receive the accumulated milliseconds and kernel launches per
- * slot: 0 dual SpMV + projections (Algorithm 2 step 5, lines 1-3), 1 q and (pt, q),
+ * slot: 0 dual SpMV + projections (Algorithm 2 step 5, lines 1-3; without a recycle space
+ * also (pt, q) and alpha), 1 q and (pt, q) (iterations with a recycle space only),
  * 2 x / r updates and (rt, r), 3 refresh Gram (Section 4.1), 4 refresh eigen solve
  * (eq. (finalGenEigValue)), 5 refresh basis update and SVD (Section 4.3), 6 system start
  * (Section 4.3 last paragraph), 7 initial projection / step 7 / A^H construction. */
