@@ -387,3 +387,129 @@ def test_exact_invariant_subspace_deflates():
         assert r.status == O.STATUS_OK
         its.append(r.iters)
     assert its[0] < 0.95 * base.iters and its[1] < its[0], (base.iters, its)
+
+
+# ---------------------------------------------------------------- refresh on iteration data
+def _pairs_of(lam):
+    """(first column, width) of each eigenvalue unit of eig_select's output: a complex value
+    followed by its conjugate is one real-arithmetic unit of two columns (reading R5)."""
+    out, i = [], 0
+    while i < len(lam):
+        if np.imag(lam[i]) != 0 and i + 1 < len(lam) and lam[i + 1] == np.conj(lam[i]):
+            out.append((i, 2)); i += 2
+        else:
+            out.append((i, 1)); i += 1
+    return out
+
+
+def _harmonic_residuals(As, Phi, Phit, W, Wt, lam):
+    """Largest relative residual of the harmonic-Ritz conditions, computed with explicit
+    sparse products instead of the H_j / Gamma_j / B_j recurrences:
+    primal (eq. (harmonic1)): (A u - lambda u) orthogonal to range(A^H Phit), u = Phi w;
+    dual (the same definition for A^H with test space A Phi): (A^H ut - conj(lambda) ut)
+    orthogonal to range(A Phi), ut = Phit wt.  A conjugate pair of a real problem is checked
+    as the 2 x 2 real block it stands for."""
+    AH = As.conj().T.tocsr()
+    AP, AtPt = As @ Phi, AH @ Phit
+    worst_p = worst_d = 0.0
+    for i, w in _pairs_of(lam):
+        l = lam[i]
+        if w == 1:
+            Lb, Lbd = np.array([[l]]), np.array([[np.conj(l)]])
+        else:
+            a, b = l.real, l.imag
+            Lb, Lbd = np.array([[a, b], [-b, a]]), np.array([[a, -b], [b, a]])
+        u, ut = Phi @ W[:, i:i + w], Phit @ Wt[:, i:i + w]
+        rp = AtPt.conj().T @ (As @ u - u @ Lb)
+        rd = AP.conj().T @ (AH @ ut - ut @ Lbd)
+        worst_p = max(worst_p, np.linalg.norm(rp) / (np.linalg.norm(AtPt) * np.linalg.norm(As @ u)))
+        worst_d = max(worst_d, np.linalg.norm(rd) / (np.linalg.norm(AP) * np.linalg.norm(AH @ ut)))
+    return worst_p, worst_d
+
+
+@pytest.mark.parametrize("N,c,seed", [(20, [10.0, 6.0], 1), (16, [3.0, 1.0], 2)])
+def test_refresh_satisfies_harmonic_ritz_definition_on_iteration_data(N, c, seed):
+    # Every refresh of a first system (Section 4.2, cycles j >= 2) and of a recycled system
+    # (first cycle with C, Section 4.2; general cycle, Section 4.1), on a nonsymmetric operator
+    # with an unrelated dual right-hand side, returns vectors that satisfy the harmonic-Ritz
+    # conditions written with A itself.  This pins the pencil's blocks built from the iteration
+    # scalars (T, Gamma, B and their duals) and the dual reading R4 (left eigenvectors of the
+    # pencil).  The wrong reading Wt = W fails the dual check by more than 1e-5 on these cases.
+    A = I.convdiff(N, c)
+    As = A.to_scipy()
+    n = A.n
+    b, bt = I.normal_vector(n, seed), I.normal_vector(n, seed + 50)
+    z = np.zeros(n)
+    rec, checked = None, 0
+    for _ in range(2):
+        r = O.rbicg_pair(A, b, bt, z, z, recycle=rec, k=6, s=20, tol=1e-10, record=True, max_itn=200)
+        assert r.status == O.STATUS_OK
+        for cy in r.hist["cycles"]:
+            blk = cy["blocks"]
+            if blk is None:
+                continue
+            wp, wd = _harmonic_residuals(As, blk["Phi"], blk["Phit"], cy["W"], cy["Wt"], cy["lam"])
+            assert wp < 1e-9 and wd < 1e-9, (cy["j"], wp, wd)
+            _, wrong = _harmonic_residuals(As, blk["Phi"], blk["Phit"], cy["W"], cy["W"], cy["lam"])
+            assert wrong > 1e-5
+            checked += 1
+        rec = O.biorth_recycle(A, r.U_next, r.Ut_next, 1e-6)
+    assert checked >= 4
+
+
+@pytest.mark.parametrize("dim,N", [(1, 200), (2, 24)])
+def test_symmetric_case_both_sides_coincide(dim, N):
+    # A symmetric (c = 0), bt = b and xt_{-1} = x_{-1}: the dual iteration repeats the primal
+    # one, so Phit = Phi, Ht = H and the pencil of eq. (finalGenEigValue) is symmetric, with
+    # R = Phi^T A Phi positive definite: it is the harmonic-Ritz problem of RMINRES that
+    # Section 4.1 starts from.  Then at every harmonic refresh the eigenvalues are real, the
+    # left eigenvectors span the right ones (Wt = W), and C_j = A Phi W, Ct_j = A Phit Wt are
+    # bi-orthogonal already before the SVD of Section 4.3 (eigenvectors of a symmetric-definite
+    # pencil are L-orthogonal), so the truncation keeps all k columns (p = k).  Recycling the
+    # space on the same pair saves iterations (Section 6.1 protocol).
+    A = I.convdiff(N, [0.0] * dim)
+    As = A.to_scipy()
+    n = A.n
+    b = I.normal_vector(n, 3)
+    z = np.zeros(n)
+    k, rec, its, checked = 8, None, [], 0
+    for _ in range(3):
+        r = O.rbicg_pair(A, b, b.copy(), z, z, recycle=rec, k=k, s=30, tol=1e-10, record=True)
+        assert r.status == O.STATUS_OK
+        its.append(r.iters)
+        for cy in r.hist["cycles"]:
+            W, Wt, lam = cy["W"], cy["Wt"], cy["lam"]
+            assert np.abs(np.imag(lam)).max() <= 1e-10 * np.abs(lam).max()
+            cos = sla.svdvals(np.linalg.qr(W)[0].T @ np.linalg.qr(Wt)[0])
+            assert cos.min() > 1 - 1e-10
+            assert cy["U"].shape[1] == k
+            blk = cy["blocks"]
+            if blk is None:
+                continue   # first cycle: Ritz (not harmonic) vectors of T_1
+            Cj = As @ (blk["Phi"] @ W)
+            Cjt = As.T @ (blk["Phit"] @ Wt)
+            G = (Cjt / np.linalg.norm(Cjt, axis=0)).T @ (Cj / np.linalg.norm(Cj, axis=0))
+            assert np.abs(G - np.diag(np.diag(G))).max() < (1e-4 if dim == 1 else 1e-8)
+            assert np.abs(np.diag(G)).min() > 1 - 1e-8
+            checked += 1
+        rec = O.biorth_recycle(A, r.U_next, r.Ut_next, 1e-6)
+        assert rec[0].shape[1] == k
+    assert checked >= 3
+    assert its[1] < 0.9 * its[0] and its[2] <= its[1], its
+
+
+def test_guard_baseline_does_not_shrink_after_a_fallback():
+    # The stagnation guard (not in the paper) measures recycled pairs against the full count of
+    # the last pair solved from its start without a recycle space.  On this sequence pair 3
+    # falls back; pair 4 keeps the same limit (a baseline taken from the continued leg alone
+    # would have dropped it to 40).
+    seq = I.convdiff_sequence(24, [20.0, 20.0], 5, 0.01, 4, bt_kind="normal")
+    rs = O.rbicg_sequence(seq, k=6, s=20, tol=1e-8, guard=1.5)
+    assert all(r.status == O.STATUS_OK for r in rs)
+    limit = -(-int(1.5 * rs[0].iters) // 20) * 20
+    fell = [j for j, r in enumerate(rs) if r.hist["fallback"]]
+    assert fell and fell[0] < len(rs) - 1, fell
+    for r in rs[1:]:
+        assert r.hist["guard_limit"] == limit
+        if r.hist["fallback"]:
+            assert r.iters > limit
