@@ -48,7 +48,8 @@ typedef enum {
   RBICG_NOT_CONVERGED = 1,   /* max_itn reached (Algorithm 2 step 5 bound) */
   RBICG_BREAKDOWN_RHO = 2,   /* |(rt_i, r_i)| <= 1e-14 ||rt_i|| ||r_i|| (Section 2, serious breakdown) */
   RBICG_BREAKDOWN_PQ = 3,    /* |(pt_i, q_i)| <= 1e-14 ||pt_i|| ||q_i|| (Section 2, second kind) */
-  RBICG_RECYCLE_EMPTY = 4,   /* solve converged, but Section 4.3 truncation left p = 0 columns */
+  RBICG_RECYCLE_EMPTY = 4,   /* solve converged, but the system start's Section 4.3 truncation
+                                left p = 0 columns of the recycle space carried in */
   RBICG_ERR_ARG = -1,        /* invalid argument (sizes, null pointers, malformed CSR) */
   RBICG_ERR_OOM = -2,        /* device allocation failed */
   RBICG_ERR_CUDA = -3,       /* a CUDA call failed */
@@ -94,7 +95,8 @@ typedef struct {
                               FP32 solver keeps only sigma >= max(svd_tol, inner_svd_tol) */
   double guard;            /* stagnation guard (not in the paper): a pair solved with a recycle
                               space that has not converged after guard x (iterations of the last
-                              pair this handle solved without one) iterations applies step 7 to
+                              pair this handle solved from its start without one, every leg
+                              counted) iterations applies step 7 to
                               its current iterate and continues from it as plain BiCG (Algorithm 2
                               with an empty recycle space); rbicg_result.fallback reports it.
                               0 disables the guard. */

@@ -585,7 +585,8 @@ def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, 
     recycle=False gives plain BiCG on every pair (RBiCG with an empty recycle space).
     guard > 0 reproduces the CUDA library's stagnation guard, which is NOT part of the paper:
     a pair solved with a recycle space that has not converged after guard x (iterations of
-    the last pair solved without one) iterations, rounded up to whole cycles of s, applies
+    the last pair solved from its start without one, all legs counted) iterations, rounded
+    up to whole cycles of s, applies
     step 7 to its iterate and continues from it as plain BiCG (Algorithm 2 with an empty
     recycle space).
     restarts > 0 reproduces the library's restart after a breakdown (also not in the paper): a
@@ -614,6 +615,7 @@ def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, 
         res = rbicg_pair(A, b, bt, x0, xt0, recycle=rec, k=k, s=s, tol=tol, max_itn=limit,
                          svd_tol=svd_tol, seed=seed + j, refresh=recycle)
         res.hist["fallback"] = False
+        res.hist["guard_limit"] = limit if limit < max_itn else None
         if limit < max_itn and res.status != STATUS_OK:
             first = res
             res = rbicg_pair(A, b, bt, first.x, first.xt, recycle=None, k=k, s=s, tol=tol,
@@ -621,20 +623,22 @@ def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, 
                              refresh=recycle)
             res.iters += first.iters
             res.hist["fallback"] = True
+            res.hist["guard_limit"] = limit
             res.recycle_dim = 0
-            last_plain = res.iters - first.iters
-        elif rec is None or rec[0].shape[1] == 0:
-            last_plain = res.iters
         used = 0
         while used < restarts and res.status in (STATUS_BREAKDOWN_RHO, STATUS_BREAKDOWN_PQ) and res.iters < max_itn:
             used += 1
             prev = res
             res = rbicg_pair(A, b, bt, prev.x, prev.xt, recycle=None, k=k, s=s, tol=tol,
                              max_itn=max_itn - prev.iters, svd_tol=svd_tol, seed=seed + j, refresh=recycle)
-            last_plain = res.iters
             res.iters += prev.iters
             res.hist["fallback"] = True
             res.recycle_dim = 0
+        # the guard's baseline is the full iteration count of the last pair solved from its
+        # start without a recycle space; a leg that continued a stalled or broken solve starts
+        # from a nearly converged iterate and would shrink it
+        if rec is None or rec[0].shape[1] == 0:
+            last_plain = res.iters
         if rec is not None and rec[0].shape[1] == 0 and res.status == STATUS_OK:
             res.status = STATUS_RECYCLE_EMPTY
         out.append(res)

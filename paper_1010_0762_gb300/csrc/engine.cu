@@ -488,7 +488,7 @@ struct Solver : SolverBase {
     double tol = 0;
     int max_itn = 0;
     uint64_t seed = 0;
-    int kU_in = 0, kt = 0;
+    int kU_in = 0, kc_start = 0, kt = 0;
     VecArgs<T> v{};
     PairOut out;
     bool recycle = false, broken = false;
@@ -519,6 +519,7 @@ struct Solver : SolverBase {
     R_.b = b; R_.bt = bt; R_.x = x; R_.xt = xt; R_.tol = tol; R_.max_itn = max_itn; R_.seed = seed;
     R_.kU_in = prm.recycle ? kU : 0;
     if (pending_start) system_start();
+    R_.kc_start = kc;
     R_.kt = kt_for(kc);
     set_field(&DevState::tol, tol);
     set_field(&DevState::max_itn, max_itn);
@@ -714,7 +715,10 @@ struct Solver : SolverBase {
     out.iters = R_.iter_before + hv->iter;
     out.cycles = R_.good_refresh;
     out.recycle_dim = out.fallback ? 0 : kc;
-    if (out.fallback || R_.kU_in == 0) last_plain_iters = hv->iter;
+    // the guard's baseline: the full count of the last pair solved from its start without a
+    // recycle space (a leg that continued a stalled or broken solve starts from a nearly
+    // converged iterate and would shrink it)
+    if (R_.kc_start == 0) last_plain_iters = out.iters;
     const double nb = hv->bnorm > 0 ? hv->bnorm : 1.0, nbt = hv->btnorm > 0 ? hv->btnorm : 1.0;
     out.relres = hv->rnorm / nb;
     out.relres_dual = hv->rtnorm / nbt;
@@ -746,7 +750,9 @@ struct Solver : SolverBase {
       }
     }
     pending_start = 1;   // the next solve re-derives C, Ct for the (possibly new) operator
-    if (R_.kU_in > 0 && kc == 0 && out.status == RBICG_OK) out.status = RBICG_RECYCLE_EMPTY;
+    // only the system start's truncation empties the space (a guard fallback is reported by
+    // out.fallback alone)
+    if (R_.kU_in > 0 && R_.kc_start == 0 && out.status == RBICG_OK) out.status = RBICG_RECYCLE_EMPTY;
     return out;
   }
 

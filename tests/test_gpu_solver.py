@@ -368,12 +368,18 @@ def test_stagnation_guard_matches_oracle_and_converges(R):
     ref = O.rbicg_sequence(seq, k=20, s=40, tol=1e-8, guard=1.5)
     S = R.Solver(n, k=20, s=40, tol=1e-8, guard=1.5, setup_fp32=0)
     fell = 0
+    status = {O.STATUS_OK: R.OK, O.STATUS_RECYCLE_EMPTY: R.RECYCLE_EMPTY}
+    first = None
     for j, pr in enumerate(seq):
         res, x, xt = _solve_gpu(R, S, pr["A"], pr["b"], pr["bt"])
-        assert res["status"] in (R.OK, R.RECYCLE_EMPTY), res
+        assert res["status"] == status[ref[j].status], (j, res, ref[j].status)
         assert res["true_relres"] < 2e-8 and res["true_relres_dual"] < 2e-8
-        assert ref[j].status in (O.STATUS_OK, O.STATUS_RECYCLE_EMPTY)
         assert _rel(x, ref[j].x) < 1e-5 and _rel(xt, ref[j].xt) < 1e-5
+        if j == 0:
+            first = res["iters"]
+        if res["fallback"]:
+            # the recycled leg ran to the guard limit, which stays 1.5 x the first pair's count
+            assert res["iters"] > 1.5 * first, (j, res["iters"], first)
         fell += res["fallback"]
     assert fell >= 1
 
