@@ -170,18 +170,27 @@ class Server:
                 in_flight -= 1
                 done += 1
         wall = clock() - t0
-        lat = np.array([(r.t_done - r.t_arrival) * 1e3 for r in requests])
+        # a solve counts only when it met the tolerance (status OK, or OK with an empty recycle
+        # space); breakdowns and exhausted iteration budgets are reported beside it
+        ok = [r for r in requests if r.result["status"] in (0, 4)]
+        lat_ok = np.array([(r.t_done - r.t_arrival) * 1e3 for r in ok]) if ok else np.zeros(1)
+        lat_all = np.array([(r.t_done - r.t_arrival) * 1e3 for r in requests])
         return {
             "requests": len(requests),
+            "converged": len(ok),
+            "failed": len(requests) - len(ok),
             "wall_s": wall,
-            "solves_per_s": len(requests) / wall if wall > 0 else None,
-            "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()),
+            "solves_per_s": len(ok) / wall if wall > 0 else None,
+            "requests_per_s": len(requests) / wall if wall > 0 else None,
+            "p50_ms": float(np.percentile(lat_ok, 50)),
+            "p99_ms": float(np.percentile(lat_ok, 99)),
+            "mean_ms": float(lat_ok.mean()),
+            "p99_ms_all_requests": float(np.percentile(lat_all, 99)),
             "evictions": self.evictions,
-            "all_converged": all(r.result["status"] in (0, 4) for r in requests),
+            "all_converged": len(ok) == len(requests),
             "statuses": dict(collections.Counter(int(r.result["status"]) for r in requests)),
             "fp64_fallbacks": sum(1 for r in requests if r.result.get("fallback") == 2),
+            "guard_fallbacks": sum(1 for r in requests if r.result.get("fallback") == 1),
             "mean_iters": float(np.mean([r.result["iters"] for r in requests])),
         }
 
