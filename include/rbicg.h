@@ -75,7 +75,8 @@ typedef enum {
 
 /* Solver parameters.  Defaults (rbicg_default_params): k = 10, s = 40, max_itn = 20000,
  * tol = 1e-8, svd_tol = 1e-6, inner_tol = 1e-5, refine_max = 12, precision = FP64,
- * seed = 0, setup_fp32 = 1, recycle = 1, inner_svd_tol = 1e-3, guard = 1.5. */
+ * seed = 0, setup_fp32 = 1, recycle = 1, inner_svd_tol = 1e-3, guard = 1.5, restarts = 0,
+ * grid_blocks = 0, refresh = 1. */
 typedef struct {
   int k;                   /* recycle dimension: columns kept in U, Ut (Section 3, 4.1); 1..32 */
   int s;                   /* cycle length (Section 4.1); 2..64, k + s <= 80 */
@@ -108,6 +109,12 @@ typedef struct {
                               min(ceil(n / 256), 3 x SMs)); rbicg_autotune picks one by timed
                               trials.  Reductions follow the block partition, so results are
                               reproducible for a given value. */
+  int refresh;             /* 1 (default): refresh the recycle space every s iterations and hand the
+                              last one to the next pair (Section 4); 0: solve with the current
+                              recycle space and carry it to the next pair unchanged (Section 6.2:
+                              the recycle space may be recomputed only for some systems of a
+                              sequence, e.g. every fifth IRKA step).  Changeable between pairs
+                              with rbicg_set_refresh. */
 } rbicg_params;
 
 /* A sparse operator.  Operator = A when has_shift == 0, (shift I - A) otherwise. */
@@ -216,6 +223,10 @@ rbicg_status rbicg_import_recycle(rbicg_handle h, const void *U, const void *Ut,
 /* Drop the recycle space: the next pair is solved as a first system (Algorithm 2 step 1). */
 rbicg_status rbicg_reset(rbicg_handle h);
 
+/* Set rbicg_params.refresh (0 or 1) for the handle's next solves (Section 6.2: recompute the
+ * recycle space only for selected systems of a sequence). */
+rbicg_status rbicg_set_refresh(rbicg_handle h, int refresh);
+
 /* Free the handle and its device workspace. */
 rbicg_status rbicg_destroy(rbicg_handle h);
 
@@ -299,6 +310,76 @@ rbicg_status rbicg_op_svd(rbicg_dtype dtype, int k, const void *S_host, void *M_
  * once the work is queued; synchronise `stream` before reading G. */
 rbicg_status rbicg_op_gram_noalloc(rbicg_dtype dtype, int64_t n, const void *X, int mx, int ldx,
                                    const void *Y, int my, int ldy, int fp32, void *G, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Applications built on solved dual pairs.
+ * ------------------------------------------------------------------------------------- */
+
+/* Bilinear form u^H Op^{-1} w from a solved dual pair (Section 1: bilinear forms u^* A^{-1} w,
+ * e.g. in QMC, are evaluated from the primal and the dual system, with an error bound that is
+ * quadratic in the residuals).  x solves Op x = w and xt solves Op^H xt = u (for example
+ * rbicg_solve_pair with b = w, bt = u); Op = A or (shift I - A) as in rbicg_csr.  u, w, x, xt:
+ * n device values of the dtype.  out_host receives three complex values (re, im interleaved; the
+ * imaginary parts are 0 for R64): u^H x, xt^H w, and the corrected estimate
+ * u^H x + xt^H (w - Op x), whose error u^H Op^{-1} w - estimate equals
+ * (u - Op^H xt)^H Op^{-1} (w - Op x).  Sums are taken in FP64 in a fixed order (reproducible).
+ * Synchronous on `stream`; allocates a small device buffer for the block partial sums. */
+rbicg_status rbicg_bilinear_form(const rbicg_csr *A, rbicg_dtype dtype, const void *u, const void *w,
+                                 const void *x, const void *xt, double *out_host, void *stream);
+
+/* IRKA (Algorithm 3, Section 5) for the SISO system G(s) = c^H (s I - A)^{-1} b with E = I:
+ * dual shifted systems (sigma_i I - A) v_i = b, (sigma_i I - A)^H w_i = c solved with RBiCG,
+ * reduced model E_r = W^H V, A_r = W^H A V, b_r = W^H b, c_r = V^H c (eq. (red_projection); the
+ * algorithm's listing prints W^H A V for E_r and V^H c_r for c_r), new shifts
+ * sigma_i <- -lambda_i(A_r, E_r) until they stop moving.  Shifts are kept in ascending modulus
+ * (the larger imaginary part first among equal moduli), and for real A, b, c the new set is made
+ * exactly closed under conjugation (rounding removed).  Recycling (Section 5.3): */
+typedef struct {
+  int r;               /* reduced order = number of shifts, 1..32 */
+  int max_steps;       /* bound on IRKA steps (reduced models formed) */
+  double shift_tol;    /* converged when max_i |sigma_i' - sigma_i| / |sigma_i| < shift_tol (the
+                          paper's experiments: 1e-6) */
+  int strategy;        /* 0: no recycling (BiCG); 1: shift index i recycles from index i of the
+                          previous step; 2: each solve recycles from the previous shift's solve
+                          (within a step, and from the last shift of a step to the first of the
+                          next); 3: the space of the pooled system (previous step's shifts and this
+                          step's earlier ones) with the smallest relative shift change, if below
+                          pool_tol, else none */
+  int recycle_count;   /* recycle only for the recycle_count shifts of smallest modulus (0: all;
+                          Section 6.2 recycles for the small shifts only) */
+  int refresh_every;   /* compute new recycle spaces only on steps m with m % refresh_every == 0,
+                          else solve with the carried spaces (Section 6.2: every fifth step) */
+  double pool_tol;     /* strategy 3 threshold on the relative shift change */
+  int batched;         /* strategies 0 and 1: the r solves of a step in one rbicg_solve_batch */
+} rbicg_irka_params;
+
+typedef struct {
+  int steps;               /* reduced models formed */
+  int converged;           /* 1 if the shift change fell below shift_tol */
+  double last_change;      /* max relative shift change of the last step */
+  int64_t iters;           /* iterations summed over all solves (primal and dual pair counted once) */
+  int failed_solves;       /* solves that ended with a status other than OK / RECYCLE_EMPTY */
+  double model_shifts[64]; /* the r shifts (re, im) the returned reduced model interpolates at */
+} rbicg_irka_result;
+
+/* Fill *p with the defaults: r = 8, max_steps = 10, shift_tol = 1e-6, strategy = 1,
+ * recycle_count = 0, refresh_every = 1, pool_tol = 0.5, batched = 1. */
+void rbicg_irka_default_params(rbicg_irka_params *p);
+
+/* Run IRKA.  sp: the RBiCG parameters of every solve (complex double vectors, C128).  A: the real
+ * system matrix (val_complex = 0, has_shift = 0), device CSR.  b, c: n doubles each (device).
+ * shifts_in: r initial shifts (re, im) on the host.  On return: shifts_out (host, r complex) the
+ * shifts after the last step; Ar_out, Er_out (host, r x r complex, column-major) and br_out,
+ * cr_out (host, r complex) the reduced model of the last step, which interpolates G at
+ * res->model_shifts; iters_out (host, max_steps x r ints, may be NULL) the iterations of every
+ * solve, step-major.  The output pointers other than shifts_out may be NULL.  Work runs on
+ * `stream`; device memory for V, W, A V and the recycle pools is allocated and freed inside.
+ * Returns a negative status on error (a failed solve is not an error: res->failed_solves counts
+ * them), RBICG_ERR_EIG if the reduced pencil's eigenvalues could not be computed. */
+rbicg_status rbicg_irka(const rbicg_params *sp, const rbicg_irka_params *ip, const rbicg_csr *A,
+                        const double *b, const double *c, const double *shifts_in, void *stream,
+                        double *shifts_out, double *Ar_out, double *Er_out, double *br_out, double *cr_out,
+                        int *iters_out, rbicg_irka_result *res);
 
 #ifdef __cplusplus
 }

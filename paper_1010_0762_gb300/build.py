@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "librbicg.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["kernels_iter.cu", "kernels_basis.cu", "kernels_dense.cu", "engine.cu", "noalloc.cu"]
+SOURCES = ["kernels_iter.cu", "kernels_basis.cu", "kernels_dense.cu", "engine.cu", "noalloc.cu", "apps.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "--extended-lambda", "-lineinfo", "-Xcompiler", "-fPIC",
          "-diag-suppress", "128,186", "-I", os.path.join(HERE, "..", "include")]

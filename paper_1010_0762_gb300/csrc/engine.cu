@@ -681,7 +681,7 @@ struct Solver : SolverBase {
       R_.done = hv->done;
       return;
     }
-    if (R_.recycle && !R_.broken && R_.iter == (R_.j + 1) * prm.s) {
+    if (R_.recycle && prm.refresh && !R_.broken && R_.iter == (R_.j + 1) * prm.s) {
       ++R_.j;
       if (defer_refresh) {
         RB_CUDA(cudaEventRecord(ev_cycle, s));
@@ -829,6 +829,7 @@ struct Impl {
   virtual void reset() = 0;
   virtual void export_recycle(void* U, void* Ut, int* p) = 0;
   virtual void import_recycle(const void* U, const void* Ut, int p) = 0;
+  virtual void set_refresh(int v) = 0;
   // FP64 handles: the solver that a batch drives directly, and the kind of its (V, T)
   virtual void* batch_solver(int* kind) = 0;
 };
@@ -1017,6 +1018,12 @@ struct ImplT : Impl {
     fp64_only = false;
   }
 
+  void set_refresh(int v) override {
+    prm.refresh = v;
+    hi->prm.refresh = v;
+    if (lo) lo->prm.refresh = v;
+  }
+
   void export_recycle(void* Uo, void* Uto, int* p) override {
     if (lo && !fp64_only) {
       // the recycle space lives in the FP32 inner solver; export it widened to FP64
@@ -1114,6 +1121,7 @@ extern "C" void rbicg_default_params(rbicg_params* p) {
   p->guard = 1.5;
   p->restarts = 0;
   p->grid_blocks = 0;
+  p->refresh = 1;
 }
 
 static std::string check_params(const rbicg_params* p, int64_t n) {
@@ -1128,6 +1136,7 @@ static std::string check_params(const rbicg_params* p, int64_t n) {
   if (!(p->guard >= 0.0)) return "guard must be >= 0";
   if (p->grid_blocks < 0 || p->grid_blocks > (1 << 20)) return "grid_blocks must be in 0..2^20";
   if (p->restarts < 0 || p->restarts > 1000) return "restarts must be in 0..1000";
+  if (p->refresh != 0 && p->refresh != 1) return "refresh must be 0 or 1";
   if (p->precision == RBICG_FP32_REFINED && !(p->inner_tol > 0.0 && p->inner_tol < 1.0))
     return "inner_tol must be in (0, 1)";
   if (p->precision != RBICG_FP64 && p->precision != RBICG_FP32_REFINED) return "unknown precision";
@@ -1251,6 +1260,14 @@ extern "C" rbicg_status rbicg_import_recycle(rbicg_handle h, const void* U, cons
 extern "C" rbicg_status rbicg_reset(rbicg_handle h) {
   if (!h) return fail(nullptr, RBICG_ERR_ARG, "handle is NULL");
   if (h->impl) h->impl->reset();
+  return RBICG_OK;
+}
+
+extern "C" rbicg_status rbicg_set_refresh(rbicg_handle h, int refresh) {
+  if (!h) return fail(nullptr, RBICG_ERR_ARG, "handle is NULL");
+  if (refresh != 0 && refresh != 1) return fail(h, RBICG_ERR_ARG, "refresh must be 0 or 1");
+  h->prm.refresh = refresh;
+  if (h->impl) h->impl->set_refresh(refresh);
   return RBICG_OK;
 }
 

@@ -30,7 +30,7 @@ class Params(C.Structure):
                 ("svd_tol", C.c_double), ("inner_tol", C.c_double), ("refine_max", C.c_int),
                 ("precision", C.c_int), ("seed", C.c_uint64), ("setup_fp32", C.c_int),
                 ("recycle", C.c_int), ("inner_svd_tol", C.c_double), ("guard", C.c_double),
-                ("restarts", C.c_int), ("grid_blocks", C.c_int)]
+                ("restarts", C.c_int), ("grid_blocks", C.c_int), ("refresh", C.c_int)]
 
 
 class CSRStruct(C.Structure):
@@ -46,6 +46,17 @@ class Result(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class IrkaParams(C.Structure):
+    _fields_ = [("r", C.c_int), ("max_steps", C.c_int), ("shift_tol", C.c_double), ("strategy", C.c_int),
+                ("recycle_count", C.c_int), ("refresh_every", C.c_int), ("pool_tol", C.c_double),
+                ("batched", C.c_int)]
+
+
+class IrkaResult(C.Structure):
+    _fields_ = [("steps", C.c_int), ("converged", C.c_int), ("last_change", C.c_double), ("iters", C.c_int64),
+                ("failed_solves", C.c_int), ("model_shifts", C.c_double * 64)]
 
 
 class RBiCGError(RuntimeError):
@@ -70,6 +81,7 @@ def _load():
         "rbicg_export_recycle": (ci, [vp, vp, vp, C.POINTER(ci)]),
         "rbicg_import_recycle": (ci, [vp, vp, vp, ci]),
         "rbicg_reset": (ci, [vp]),
+        "rbicg_set_refresh": (ci, [vp, ci]),
         "rbicg_destroy": (ci, [vp]),
         "rbicg_last_error": (C.c_char_p, [vp]),
         "rbicg_launch_count": (i64, [vp]),
@@ -86,6 +98,10 @@ def _load():
         "rbicg_engine_step": (ci, [vp, C.POINTER(ci)]),
         "rbicg_engine_poll": (ci, [vp, C.POINTER(i64), C.POINTER(Result), ci, C.POINTER(ci)]),
         "rbicg_engine_destroy": (ci, [vp]),
+        "rbicg_bilinear_form": (ci, [C.POINTER(CSRStruct), ci, vp, vp, vp, vp, vp, vp]),
+        "rbicg_irka_default_params": (None, [C.POINTER(IrkaParams)]),
+        "rbicg_irka": (ci, [C.POINTER(Params), C.POINTER(IrkaParams), C.POINTER(CSRStruct), vp, vp, vp, vp,
+                            vp, vp, vp, vp, vp, vp, C.POINTER(IrkaResult)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -203,6 +219,10 @@ class Solver:
 
     def reset(self):
         _check(lib.rbicg_reset(self.h), self.h)
+
+    def set_refresh(self, refresh):
+        _check(lib.rbicg_set_refresh(self.h, int(refresh)), self.h)
+        self.params.refresh = int(refresh)
 
     def launch_count(self):
         return int(lib.rbicg_launch_count(self.h))
@@ -356,3 +376,51 @@ def op_svd(S, stream=None):
                           sig.ctypes.data_as(C.c_void_p), N.ctypes.data_as(C.c_void_p), _stream(stream))
     _check(st)
     return M, sig, N
+
+
+# ------------------------------------------------------------------ applications
+def bilinear_form(op: Operator, u, w, x, xt, stream=None):
+    """u^H Op^{-1} w from a solved pair Op x = w, Op^H xt = u (rbicg_bilinear_form): returns the
+    primal estimate u^H x, the dual estimate xt^H w and the corrected u^H x + xt^H (w - Op x)."""
+    dtype = C128 if x.dtype == torch.complex128 else R64
+    out = np.zeros(6)
+    _check(lib.rbicg_bilinear_form(C.byref(op.struct), dtype, _ptr(u), _ptr(w), _ptr(x), _ptr(xt),
+                                   out.ctypes.data_as(C.c_void_p), _stream(stream)))
+    z = out[0::2] + 1j * out[1::2]
+    return (z if dtype == C128 else z.real)
+
+
+def irka(op: Operator, b, c, shifts, stream=None, **kw):
+    """IRKA (Algorithm 3) for G(s) = c^H (s I - A)^{-1} b with the library's RBiCG solves
+    (rbicg_irka).  op: the real matrix A (no shift); b, c: real device vectors; shifts: the r
+    initial shifts.  Keyword arguments set rbicg_irka_params fields (r is len(shifts)) and, with a
+    solver_ prefix, rbicg_params fields of the solves (e.g. solver_k=16).  Returns a dict with the
+    final shifts, the reduced model (Ar, Er, br, cr) of the last step, the shifts it interpolates at,
+    per-solve iteration counts (steps x r) and the run's counters."""
+    ip = IrkaParams()
+    lib.rbicg_irka_default_params(C.byref(ip))
+    sp = {}
+    for k_, v in kw.items():
+        if k_.startswith("solver_"):
+            sp[k_[len("solver_"):]] = v
+        else:
+            setattr(ip, k_, v)
+    r = len(shifts)
+    ip.r = r
+    p = default_params(**sp)
+    sh = np.zeros(2 * r)
+    sh[0::2] = np.real(shifts)
+    sh[1::2] = np.imag(shifts)
+    out = np.zeros(2 * r)
+    Ar = np.zeros(2 * r * r); Er = np.zeros(2 * r * r); br = np.zeros(2 * r); cr = np.zeros(2 * r)
+    its = np.zeros(ip.max_steps * r, dtype=np.int32)
+    res = IrkaResult()
+    f = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(lib.rbicg_irka(C.byref(p), C.byref(ip), C.byref(op.struct), _ptr(b), _ptr(c), f(sh), _stream(stream),
+                          f(out), f(Ar), f(Er), f(br), f(cr), f(its), C.byref(res)))
+    cx = lambda a: a[0::2] + 1j * a[1::2]
+    ms = np.array(res.model_shifts[:2 * r])
+    return {"shifts": cx(out), "Ar": cx(Ar).reshape(r, r, order="F"), "Er": cx(Er).reshape(r, r, order="F"),
+            "br": cx(br), "cr": cx(cr), "model_shifts": cx(ms), "iters": its.reshape(ip.max_steps, r)[:res.steps],
+            "steps": res.steps, "converged": bool(res.converged), "last_change": res.last_change,
+            "total_iters": int(res.iters), "failed_solves": res.failed_solves}

@@ -29,7 +29,7 @@ def test_header_declares_the_boundary():
     names = _declared()
     for n in ["rbicg_create", "rbicg_update_recycle", "rbicg_solve_pair", "rbicg_destroy",
               "rbicg_solve_batch", "rbicg_op_dual_spmv_project", "rbicg_op_gram", "rbicg_op_eig_select",
-              "rbicg_op_svd"]:
+              "rbicg_op_svd", "rbicg_bilinear_form", "rbicg_irka", "rbicg_set_refresh"]:
         assert n in names
 
 
@@ -62,3 +62,27 @@ def test_default_params_and_argument_errors(lib):
     assert R.lib.rbicg_destroy(h) == R.OK
     assert R.lib.rbicg_op_gram(R.R64, 10, None, 1, 1, None, 1, 1, 0, None, None) == R.ERR_ARG
     assert R.lib.rbicg_op_eig_select(R.R64, 100, None, None, 4, None, None, None, None, None) == R.ERR_ARG
+    assert R.lib.rbicg_bilinear_form(None, R.R64, None, None, None, None, None, None) == R.ERR_ARG
+    ip = R.IrkaParams()
+    R.lib.rbicg_irka_default_params(C.byref(ip))
+    assert (ip.r, ip.max_steps, ip.shift_tol, ip.strategy, ip.refresh_every, ip.batched) == (8, 10, 1e-6, 1, 1, 1)
+    res = R.IrkaResult()
+    assert R.lib.rbicg_irka(C.byref(p), C.byref(ip), None, None, None, None, None, None, None, None, None,
+                            None, None, C.byref(res)) == R.ERR_ARG
+    one = C.c_void_p(1)
+    csr = R.CSRStruct()
+    csr.n, csr.nnz, csr.row_ptr, csr.col_idx, csr.val = 4, 4, 1, 1, 1
+    ip.strategy = 7
+    sh = (C.c_double * 16)()
+    assert R.lib.rbicg_irka(C.byref(p), C.byref(ip), C.byref(csr), one, one, sh, None, sh, None, None, None,
+                            None, None, C.byref(res)) == R.ERR_ARG
+    assert b"strategy" in R.lib.rbicg_last_error(None)
+    ip.strategy = 1
+    csr.has_shift = 1
+    assert R.lib.rbicg_irka(C.byref(p), C.byref(ip), C.byref(csr), one, one, sh, None, sh, None, None, None,
+                            None, None, C.byref(res)) == R.ERR_ARG
+    h2 = C.c_void_p()
+    assert R.lib.rbicg_create(C.byref(p), 100, R.R64, None, C.byref(h2)) == R.OK
+    assert R.lib.rbicg_set_refresh(h2, 2) == R.ERR_ARG
+    assert R.lib.rbicg_set_refresh(h2, 0) == R.OK
+    assert R.lib.rbicg_destroy(h2) == R.OK
