@@ -44,6 +44,9 @@ def test_gram_noalloc_matches_allocating_gram_on_two_calls():
             assert st == R.OK
             err = (abs(G.cpu().numpy() - ref) / scale).max()
             assert err < tol, err
+            # and against X^H Y formed on the host
+            err = (abs(G.cpu().numpy() - X.conj().T @ Y) / scale).max()
+            assert err < tol, err
 
 
 def test_gram_noalloc_rejects_sizes_beyond_its_scratch():
