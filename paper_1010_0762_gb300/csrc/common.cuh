@@ -134,6 +134,97 @@ template <class R> RB_HD cplx<R> vcmul(R v, cplx<R> x) { return {v * x.re, v * x
 template <class R> RB_HD cplx<R> vcmul(cplx<R> v, cplx<R> x) { return cmul(v, x); }
 
 // ------------------------------------------------------------------------------------
+// Sparse row sums sum_e a_e x_e.  In FP32 the 5-/7-point stencil rows cancel almost completely
+// on the smooth vectors that decide BiCG's convergence (the diagonal and the neighbour sum agree
+// to about log10(cond) digits), and a plain FP32 sum keeps only the few digits left: FP32 BiCG
+// then stalls near ||r|| ~ ||b|| on a 128 x 128 grid, while the same recurrences with the row
+// sums exact to FP32 rounding converge like FP64 BiCG.  So the FP32 types accumulate with a
+// compensated dot product (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005): each
+// product is split into its rounded value and its exact error by a fused multiply-add, each
+// running-sum addition into its rounded value and its exact error by Knuth's two-sum, and the
+// errors are summed in a second FP32 accumulator; the result is as accurate as a sum in twice
+// the working precision, rounded once.  The FP64 types keep a plain sum.
+// ------------------------------------------------------------------------------------
+struct Dot2f {
+  float s, c;
+  RB_HD Dot2f() : s(0.f), c(0.f) {}
+  RB_HD void two_sum_into(float p) {
+#ifdef __CUDA_ARCH__
+    const float t = __fadd_rn(s, p);
+    const float bb = __fadd_rn(t, -s);
+    const float err = __fadd_rn(__fadd_rn(s, -__fadd_rn(t, -bb)), __fadd_rn(p, -bb));
+#else
+    const float t = s + p, bb = t - s, err = (s - (t - bb)) + (p - bb);
+#endif
+    s = t;
+    c += err;
+  }
+  RB_HD void add_prod(float a, float x) {
+#ifdef __CUDA_ARCH__
+    const float p = __fmul_rn(a, x);
+#else
+    const float p = a * x;
+#endif
+    const float e = fmaf(a, x, -p);
+    two_sum_into(p);
+    c += e;
+  }
+  RB_HD float value() const { return s + c; }
+};
+
+// Type of an operator value in a sum over vectors of compute type Cm: real operators stay real
+// (a real-by-complex product is two real products), complex ones take Cm.
+template <class V, class Cm> struct val_of { typedef Cm type; };
+template <class Cm> struct val_of<double, Cm> { typedef typename traits<Cm>::real type; };
+template <class Cm> struct val_of<float, Cm> { typedef typename traits<Cm>::real type; };
+
+template <class T> struct SpAcc;
+// FP64: a plain sum, so that the FP64 kernels keep their arithmetic
+template <> struct SpAcc<double> {
+  double acc = 0.0;
+  RB_HD void add(double a, double x) { acc += a * x; }
+  RB_HD double value() const { return acc; }
+  RB_HD double shifted(double sh, double prow) const { return sh * prow - acc; }
+};
+template <> struct SpAcc<cplx<double>> {
+  cplx<double> acc = cplx<double>(0.0);
+  RB_HD void add(double a, cplx<double> x) { acc += vmul(a, x); }
+  RB_HD void add(cplx<double> a, cplx<double> x) { acc += vmul(a, x); }
+  RB_HD cplx<double> value() const { return acc; }
+  RB_HD cplx<double> shifted(cplx<double> sh, cplx<double> prow) const { return sh * prow - acc; }
+};
+// FP32: compensated
+template <> struct SpAcc<float> {
+  Dot2f d;
+  RB_HD void add(float a, float x) { d.add_prod(a, x); }
+  RB_HD float value() const { return d.value(); }
+  RB_HD float shifted(float sh, float prow) const {   // sh prow - sum, one compensated sum
+    Dot2f q;
+    q.add_prod(sh, prow);
+    q.two_sum_into(-d.s);
+    q.c -= d.c;
+    return q.value();
+  }
+};
+template <> struct SpAcc<cplx<float>> {
+  Dot2f re, im;
+  RB_HD void add(float a, cplx<float> x) { re.add_prod(a, x.re); im.add_prod(a, x.im); }
+  RB_HD void add(cplx<float> a, cplx<float> x) {
+    re.add_prod(a.re, x.re); re.add_prod(-a.im, x.im);
+    im.add_prod(a.re, x.im); im.add_prod(a.im, x.re);
+  }
+  RB_HD cplx<float> value() const { return cplx<float>(re.value(), im.value()); }
+  RB_HD cplx<float> shifted(cplx<float> sh, cplx<float> prow) const {
+    Dot2f qr, qi;
+    qr.add_prod(sh.re, prow.re); qr.add_prod(-sh.im, prow.im);
+    qi.add_prod(sh.re, prow.im); qi.add_prod(sh.im, prow.re);
+    qr.two_sum_into(-re.s); qr.c -= re.c;
+    qi.two_sum_into(-im.s); qi.c -= im.c;
+    return cplx<float>(qr.value(), qi.value());
+  }
+};
+
+// ------------------------------------------------------------------------------------
 // Warp / block reductions with a fixed order (deterministic for a given launch shape).
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }

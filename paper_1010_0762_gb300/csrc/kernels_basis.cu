@@ -216,24 +216,22 @@ __global__ void __launch_bounds__(256) k_spmm(OpArgs<V> op, int adjoint, const T
   const int* ci = adjoint ? op.tci : op.ci;
   const V* va = adjoint ? op.tva : op.va;
   Cm sh = from_zd<Cm>(zd(op.sh_re, adjoint ? -op.sh_im : op.sh_im));
+  typedef typename val_of<V, Cm>::type Va;
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += gridDim.x * blockDim.x) {
-    Cm acc[KC];
-#pragma unroll
-    for (int c = 0; c < KC; ++c) acc[c] = Cm(0);
+    SpAcc<Cm> acc[KC];   // compensated for FP32 compute types (see SpAcc)
     for (int e = rp[row]; e < rp[row + 1]; ++e) {
-      const Cm a = cvt<Cm>(va[e]);
+      const Va a = cvt<Va>(va[e]);
       const T* u = U + (int64_t)ci[e] * ldu;
 #pragma unroll
       for (int c = 0; c < KC; ++c)
-        if (c < nc) acc[c] += a * cvt<Cm>(u[c]);
+        if (c < nc) acc[c].add(a, cvt<Cm>(u[c]));
     }
     T* o = out + (int64_t)row * ldu;
     const T* ur = U + (int64_t)row * ldu;
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       if (c >= ldu) break;
-      Cm v = acc[c];
-      if (op.has_shift) v = sh * cvt<Cm>(ur[c]) - v;
+      const Cm v = op.has_shift ? acc[c].shifted(sh, cvt<Cm>(ur[c])) : acc[c].value();
       o[c] = c < nc ? cvt<T>(v) : T(0);
     }
   }

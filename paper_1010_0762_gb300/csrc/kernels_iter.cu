@@ -243,11 +243,11 @@ template <class R> struct shift_of<cplx<R>> {
 
 // Op p at one row (Op = A or shift I - A).  `g(j)` returns the gathered vector entry.
 template <class V, class T, class G>
-__device__ __forceinline__ T row_apply(const int* __restrict__ rp, const int* __restrict__ ci,
-                                       const V* __restrict__ va, int row, G g) {
-  T acc = T(0);
+__device__ __forceinline__ SpAcc<T> row_apply(const int* __restrict__ rp, const int* __restrict__ ci,
+                                              const V* __restrict__ va, int row, G g) {
+  SpAcc<T> acc;
   const int e0 = rp[row], e1 = rp[row + 1];
-  for (int e = e0; e < e1; ++e) acc += vmul(va[e], g(ci[e]));
+  for (int e = e0; e < e1; ++e) acc.add(va[e], g(ci[e]));
   return acc;
 }
 
@@ -340,29 +340,31 @@ __device__ __forceinline__ void phase1_body(const OpArgs<V> op, const VecArgs<T>
     const int row = base + lane;
     T z = T(0), zt = T(0);
     if (row < r1) {
+      SpAcc<T> za, zta;
       const int e0 = op.rp[row], e1 = op.rp[row + 1];
       if (op.shared) {
         for (int e = e0; e < e1; ++e) {
           const int j = op.ci[e];
-          z += vmul(op.va[e], r[j] + beta * po[j]);
-          zt += vmul(op.tva[e], rt[j] + cbeta * pto[j]);
+          za.add(op.va[e], r[j] + beta * po[j]);
+          zta.add(op.tva[e], rt[j] + cbeta * pto[j]);
         }
       } else {
         for (int e = e0; e < e1; ++e) {
           const int j = op.ci[e];
-          z += vmul(op.va[e], r[j] + beta * po[j]);
+          za.add(op.va[e], r[j] + beta * po[j]);
         }
         const int f0 = op.trp[row], f1 = op.trp[row + 1];
         for (int e = f0; e < f1; ++e) {
           const int j = op.tci[e];
-          zt += vmul(op.tva[e], rt[j] + cbeta * pto[j]);
+          zta.add(op.tva[e], rt[j] + cbeta * pto[j]);
         }
       }
       const T prow = r[row] + beta * po[row];
       const T ptrow = rt[row] + cbeta * pto[row];
       pn[row] = prow;
       ptn[row] = ptrow;
-      if (op.has_shift) { z = sh * prow - z; zt = shc * ptrow - zt; }
+      if (op.has_shift) { z = za.shifted(sh, prow); zt = zta.shifted(shc, ptrow); }
+      else { z = za.value(); zt = zta.value(); }
       v.z[row] = z;
       v.zt[row] = zt;
       if (LD == 0) alpha_terms(pq, nq, npt, ptrow, z);
@@ -606,14 +608,14 @@ __global__ void __launch_bounds__(NTHREADS) k_init_a(OpArgs<V> op, VecArgs<T> v,
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += stride) {
     T res = T(0), rest = T(0);
     if (!dual_only) {
-      T ax = row_apply<V, T>(op.rp, op.ci, op.va, row, [&](int j) { return x[j]; });
-      if (op.has_shift) ax = sh * x[row] - ax;
+      const SpAcc<T> aa = row_apply<V, T>(op.rp, op.ci, op.va, row, [&](int j) { return x[j]; });
+      const T ax = op.has_shift ? aa.shifted(sh, x[row]) : aa.value();
       res = v.b[row] - ax;
       r[row] = res;
       nb += A((double)abs2(v.b[row]));
     }
-    T atx = row_apply<V, T>(op.trp, op.tci, op.tva, row, [&](int j) { return xt[j]; });
-    if (op.has_shift) atx = shc * xt[row] - atx;
+    const SpAcc<T> ta = row_apply<V, T>(op.trp, op.tci, op.tva, row, [&](int j) { return xt[j]; });
+    const T atx = op.has_shift ? ta.shifted(shc, xt[row]) : ta.value();
     rest = v.bt[row] - atx;
     rt[row] = rest;
     nbt += A((double)abs2(v.bt[row]));
@@ -747,10 +749,10 @@ __global__ void __launch_bounds__(NTHREADS) k_fin_b(OpArgs<V> op, VecArgs<T> v, 
   A n1 = A(0.0), n2 = A(0.0);
   const int stride = gridDim.x * blockDim.x;
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < op.n; row += stride) {
-    T ax = row_apply<V, T>(op.rp, op.ci, op.va, row, [&](int j) { return x[j]; });
-    if (op.has_shift) ax = sh * x[row] - ax;
-    T atx = row_apply<V, T>(op.trp, op.tci, op.tva, row, [&](int j) { return xt[j]; });
-    if (op.has_shift) atx = shc * xt[row] - atx;
+    const SpAcc<T> aa = row_apply<V, T>(op.rp, op.ci, op.va, row, [&](int j) { return x[j]; });
+    const T ax = op.has_shift ? aa.shifted(sh, x[row]) : aa.value();
+    const SpAcc<T> ta = row_apply<V, T>(op.trp, op.tci, op.tva, row, [&](int j) { return xt[j]; });
+    const T atx = op.has_shift ? ta.shifted(shc, xt[row]) : ta.value();
     n1 += A((double)abs2(v.b[row] - ax));
     n2 += A((double)abs2(v.bt[row] - atx));
   }
