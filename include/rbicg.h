@@ -227,6 +227,13 @@ rbicg_status rbicg_reset(rbicg_handle h);
  * recycle space only for selected systems of a sequence). */
 rbicg_status rbicg_set_refresh(rbicg_handle h, int refresh);
 
+/* Measurement hook (no counterpart in the paper): the recurrence residual norms ||r_m|| of the last
+ * FP64 solve on this handle (Algorithm 2 step 5; m = 0 is the norm after eq. (minusXR)), for its
+ * last *count = min(max, 132, iterations + 1) iterations in iteration order, out[*count - 1] being
+ * the last iteration's.  The values come from the device's ring of scalar histories; a pair that
+ * restarted (guard, restarts) reports its last leg. */
+rbicg_status rbicg_residual_history(rbicg_handle h, double *out, int max, int *count);
+
 /* Free the handle and its device workspace. */
 rbicg_status rbicg_destroy(rbicg_handle h);
 
@@ -344,13 +351,16 @@ typedef struct {
                           (within a step, and from the last shift of a step to the first of the
                           next); 3: the space of the pooled system (previous step's shifts and this
                           step's earlier ones) with the smallest relative shift change, if below
-                          pool_tol, else none */
+                          pool_tol, else none; 4: one recycle space shared by all shifts (E = I:
+                          sigma I - A has A's eigenvectors, Section 5.3), computed by the solve of
+                          the smallest shift and used by every shift in the next step, so one
+                          refresh chain runs per step instead of r */
   int recycle_count;   /* recycle only for the recycle_count shifts of smallest modulus (0: all;
                           Section 6.2 recycles for the small shifts only) */
   int refresh_every;   /* compute new recycle spaces only on steps m with m % refresh_every == 0,
                           else solve with the carried spaces (Section 6.2: every fifth step) */
   double pool_tol;     /* strategy 3 threshold on the relative shift change */
-  int batched;         /* strategies 0 and 1: the r solves of a step in one rbicg_solve_batch */
+  int batched;         /* strategies 0, 1 and 4: the r solves of a step in one rbicg_solve_batch */
 } rbicg_irka_params;
 
 typedef struct {

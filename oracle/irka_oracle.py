@@ -125,7 +125,10 @@ def rbicg_solver(A, b, c, k=10, s=40, tol=1e-10, max_itn=20000, svd_tol=1e-6, st
 
     strategy 0: no recycling (BiCG); 1: the space of shift index i carries to index i of the next
     step; 2: within a step each solve passes its space to the next shift index (and the last to
-    the first index of the next step); 3: pooled (reading R17).  Only the recycle_count shift
+    the first index of the next step); 3: pooled (reading R17); 4: one space shared by all shifts
+    (E = I, Section 5.3: sigma_i I - A share A's eigenvectors, so approximate invariant subspaces of
+    one shifted operator serve every shift): the solve of shift index 0 (smallest modulus) computes
+    the space, every shift of the next step uses it, the others compute none.  Only the recycle_count shift
     indices of smallest modulus recycle (0: all).  New spaces are computed only on steps m with
     m % refresh_every == 0 (Section 6.2); on other steps a space is used and carried unchanged.
     Each solve starts from the previous step's solution for the same index (Section 6.2)."""
@@ -134,7 +137,7 @@ def rbicg_solver(A, b, c, k=10, s=40, tol=1e-10, max_itn=20000, svd_tol=1e-6, st
     Id = sp.identity(n, format="csr")
     state = {"spaces": {}, "prev_x": {}, "prev_xt": {}, "pool": [], "chain": None}
 
-    def one(i, sg, step, rec_in):
+    def one(i, sg, step, rec_in, refresh_ok=True):
         M = (sg * Id - A).tocsr()
         x0 = state["prev_x"].get(i, np.zeros(n, complex))
         xt0 = state["prev_xt"].get(i, np.zeros(n, complex))
@@ -144,16 +147,11 @@ def rbicg_solver(A, b, c, k=10, s=40, tol=1e-10, max_itn=20000, svd_tol=1e-6, st
             rec = O.biorth_recycle(M, rec_in[0], rec_in[1], svd_tol)
             if rec[0].shape[1] == 0:
                 rec = None
-        refresh = use and step % refresh_every == 0
+        refresh = use and refresh_ok and step % refresh_every == 0
         res = O.rbicg_pair(M, b.astype(complex), c.astype(complex), x0, xt0, recycle=rec, k=k, s=s, tol=tol,
                            max_itn=max_itn, svd_tol=svd_tol, seed=1000 * step + i, refresh=refresh)
         state["prev_x"][i], state["prev_xt"][i] = res.x, res.xt
-        out_space = None
-        if use:
-            if res.U_next is not None:
-                out_space = (res.U_next, res.Ut_next)
-            elif rec_in is not None:
-                out_space = rec_in
+        out_space = (res.U_next, res.Ut_next) if use and res.U_next is not None else None
         return res, out_space
 
     def solve(shifts, step):
@@ -167,6 +165,8 @@ def rbicg_solver(A, b, c, k=10, s=40, tol=1e-10, max_itn=20000, svd_tol=1e-6, st
                 rec_in = state["spaces"].get(i)
             elif strategy == 2:
                 rec_in = state["chain"]
+            elif strategy == 4:
+                rec_in = state["spaces"].get("shared")
             elif strategy == 3:
                 cands = [(abs(sg - s2) / abs(sg), sp_) for (s2, sp_) in state["pool"] + new_pool if sp_ is not None]
                 rec_in = None
@@ -176,11 +176,13 @@ def rbicg_solver(A, b, c, k=10, s=40, tol=1e-10, max_itn=20000, svd_tol=1e-6, st
                         rec_in = cands[best][1]
             else:
                 rec_in = None
-            res, sp_out = one(i, sg, step, rec_in)
+            res, sp_out = one(i, sg, step, rec_in, refresh_ok=(strategy != 4 or i == 0))
             V[:, i], W[:, i] = res.x, res.xt
             its.append(res.iters)
             if strategy == 1:
                 state["spaces"][i] = sp_out
+            elif strategy == 4 and i == 0:
+                new_shared = sp_out
             elif strategy == 2:
                 if sp_out is not None:
                     state["chain"] = sp_out
@@ -188,6 +190,8 @@ def rbicg_solver(A, b, c, k=10, s=40, tol=1e-10, max_itn=20000, svd_tol=1e-6, st
                 new_pool.append((sg, sp_out))
         if strategy == 3:
             state["pool"] = new_pool
+        if strategy == 4 and r > 0:
+            state["spaces"]["shared"] = new_shared
         return V, W, its
     return solve
 

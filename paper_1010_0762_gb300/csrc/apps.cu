@@ -268,9 +268,9 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
     return RBICG_ERR_ARG;
   }
   const int r = ip->r;
-  if (r < 1 || r > KMAX || ip->max_steps < 1 || !(ip->shift_tol > 0.0) || ip->strategy < 0 || ip->strategy > 3 ||
+  if (r < 1 || r > KMAX || ip->max_steps < 1 || !(ip->shift_tol > 0.0) || ip->strategy < 0 || ip->strategy > 4 ||
       ip->recycle_count < 0 || ip->refresh_every < 1 || !(ip->pool_tol > 0.0)) {
-    set_global_error("rbicg_irka: need 1 <= r <= 32, max_steps >= 1, shift_tol > 0, strategy 0..3, "
+    set_global_error("rbicg_irka: need 1 <= r <= 32, max_steps >= 1, shift_tol > 0, strategy 0..4, "
                      "recycle_count >= 0, refresh_every >= 1, pool_tol > 0");
     return RBICG_ERR_ARG;
   }
@@ -306,9 +306,9 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
     double* lam = run.alloc<double>(2 * KMAX + 2);
     zd* brc = run.alloc<zd>(2 * KMAX);
 
-    // handles: strategy 0/1 one per shift index; strategy 2/3 one that carries (or receives) the
-    // recycle space from solve to solve, plus one without recycling for the shift indices
-    // beyond recycle_count
+    // handles: strategies 0, 1 and 4 one per shift index; strategies 2 and 3 one that carries (or
+    // receives) the recycle space from solve to solve, plus one without recycling for the shift
+    // indices beyond recycle_count
     rbicg_params pr = *sp;
     rbicg_params pp = *sp;
     pp.recycle = 0;
@@ -321,8 +321,9 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
     };
     std::vector<rbicg_handle> hidx(r, nullptr);
     rbicg_handle hrec = nullptr, hplain = nullptr;
-    if (ip->strategy <= 1) {
-      for (int i = 0; i < r; ++i) hidx[i] = make(ip->strategy == 1 && i < nrec ? pr : pp);
+    const bool per_index = ip->strategy <= 1 || ip->strategy == 4;
+    if (per_index) {
+      for (int i = 0; i < r; ++i) hidx[i] = make((ip->strategy == 1 || ip->strategy == 4) && i < nrec ? pr : pp);
     } else {
       hrec = make(pr);
       if (nrec < r) hplain = make(pp);
@@ -336,9 +337,13 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
     zd* tmpUt = nullptr;
     if (ip->strategy == 3) {
       for (int i = 0; i < 2 * r; ++i) slot_bufs.push_back(run.alloc<zd>((size_t)n * kk * 2));
+    }
+    if (ip->strategy == 3 || ip->strategy == 4) {
       tmpU = run.alloc<zd>((size_t)n * kk);
       tmpUt = run.alloc<zd>((size_t)n * kk);
     }
+    zd* shU = ip->strategy == 4 ? run.alloc<zd>((size_t)n * kk) : nullptr;
+    zd* shUt = ip->strategy == 4 ? run.alloc<zd>((size_t)n * kk) : nullptr;
 
     std::vector<cd> sig(r);
     for (int i = 0; i < r; ++i) sig[i] = cd(shifts_in[2 * i], shifts_in[2 * i + 1]);
@@ -357,6 +362,25 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
     for (int step = 0; step < ip->max_steps; ++step) {
       const int refresh = step % ip->refresh_every == 0 ? 1 : 0;
       for (rbicg_handle h : run.handles) IR_CALL(rbicg_set_refresh(h, refresh), h);
+      if (ip->strategy == 4) {
+        // one recycle space shared by all shifts (E = I: sigma I - A has A's eigenvectors): the
+        // solve of shift index 0 computes it, the other shifts use the one it computed last step
+        for (int i = 1; i < nrec; ++i) IR_CALL(rbicg_set_refresh(hidx[i], 0), hidx[i]);
+        if (step > 0 && nrec > 1) {
+          int p = 0;
+          IR_CALL(rbicg_export_recycle(hidx[0], shU, shUt, &p), hidx[0]);
+          if (p > 0) {
+            IR_CUDA(cudaMemcpy2DAsync(tmpU, sizeof(zd) * p, shU, sizeof(zd) * kk, sizeof(zd) * p, n,
+                                      cudaMemcpyDeviceToDevice, s));
+            IR_CUDA(cudaMemcpy2DAsync(tmpUt, sizeof(zd) * p, shUt, sizeof(zd) * kk, sizeof(zd) * p, n,
+                                      cudaMemcpyDeviceToDevice, s));
+          }
+          for (int i = 1; i < nrec; ++i) {
+            if (p > 0) IR_CALL(rbicg_import_recycle(hidx[i], tmpU, tmpUt, p), hidx[i]);
+            else IR_CALL(rbicg_reset(hidx[i]), hidx[i]);
+          }
+        }
+      }
       for (int i = 0; i < r; ++i) {
         ops[i] = *A;
         ops[i].has_shift = 1;
@@ -365,7 +389,7 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
       }
       // Algorithm 3 steps 2-3 (and the loop's solves): v_i = (sigma_i I - A)^{-1} b,
       // w_i = (sigma_i I - A)^{-H} c, each from the previous step's solution for index i
-      if (ip->strategy <= 1 && ip->batched && r > 1) {
+      if (per_index && ip->batched && r > 1) {
         std::vector<const rbicg_csr*> pa(r);
         std::vector<const void*> pb(r), pc(r);
         std::vector<void*> px(r), pxt(r);
@@ -378,7 +402,7 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
       } else {
         pool_cur.clear();
         for (int i = 0; i < r; ++i) {
-          rbicg_handle h = ip->strategy <= 1 ? hidx[i] : (i < nrec ? hrec : hplain);
+          rbicg_handle h = per_index ? hidx[i] : (i < nrec ? hrec : hplain);
           if (ip->strategy == 3 && i < nrec) {
             // reading of strategy 3: the pooled space with the smallest relative shift change,
             // if below pool_tol; otherwise none

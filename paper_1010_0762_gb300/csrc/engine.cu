@@ -205,6 +205,7 @@ struct Solver : SolverBase {
   zd* work = nullptr;
   zd *Wphi = nullptr, *Wphit = nullptr, *Nmat = nullptr, *Mmat = nullptr;
   double* sig = nullptr;
+  zd* s2in = nullptr;           // input of the Section 4.3 SVD (Ct^H C and column norms)
   int* iflag = nullptr;
   HostView* hv = nullptr;       // pinned
 
@@ -255,6 +256,7 @@ struct Solver : SolverBase {
     Wphi = dmalloc<zd>(MMAX * KMAX); Wphit = dmalloc<zd>(MMAX * KMAX);
     Nmat = dmalloc<zd>(KMAX * KMAX); Mmat = dmalloc<zd>(KMAX * KMAX);
     sig = dmalloc<double>(KMAX);
+    s2in = dmalloc<zd>((size_t)4 * KMAX * KMAX);
     iflag = dmalloc<int>(4);
     RB_CUDA(cudaMallocHost(&hv, sizeof(HostView)));
   }
@@ -270,10 +272,9 @@ struct Solver : SolverBase {
     for (T* b : bufs) cudaFree(b);
     cudaFree(Cq); cudaFree(Ctq);
     cudaFree(st); cudaFree(part); cudaFree(gpart); cudaFree(G); cudaFree(work); cudaFree(Wphi); cudaFree(Wphit);
-    cudaFree(Nmat); cudaFree(Mmat); cudaFree(sig); cudaFree(iflag);
+    cudaFree(Nmat); cudaFree(Mmat); cudaFree(sig); cudaFree(s2in); cudaFree(iflag);
     if (x_save) cudaFree(x_save);
     if (xt_save) cudaFree(xt_save);
-    if (gz) cudaFree(gz);
     free_op();
     if (hv) cudaFreeHost(hv);
     if (ev_cycle) cudaEventDestroy(ev_cycle);
@@ -383,30 +384,17 @@ struct Solver : SolverBase {
     const int pi = prof->begin(6, s);
     launch_spmm<V, T>(op, 0, U, ldk, kdev, KMAX, C, 0, s);
     launch_spmm<V, T>(op, 1, Ut, ldk, kdev, KMAX, Ct, 0, s);
-    ColList<T> X{}, Y{};
-    append_block(X, Ct, prm.k); append_block(X, C, prm.k);
-    append_block(Y, C, prm.k); append_block(Y, Ct, prm.k);
-    launch_gram<T>(X, Y, n, 0, part, gram_grid, G, s);
-    launch_dense_svd(!traits<T>::cx, kdev, prm.k, reinterpret_cast<const zd*>(as_zd_gram(s)), nullptr, nullptr,
-                     prm.svd_tol, Nmat, Mmat, sig, &st->kc, st->Dc, iflag + 2, s);
+    launch_svd_input<T>(C, Ct, ldk, prm.k, prm.k, n, part, gram_grid, G, s2in, s);
+    launch_dense_svd(!traits<T>::cx, kdev, prm.k, s2in, nullptr, nullptr, prm.svd_tol, Nmat, Mmat, sig, &st->kc,
+                     st->Dc, iflag + 2, s);
     launch_rotate<T>(U, ldk, Nmat, kdev, &st->kc, prm.k, n, 0, s);
     launch_rotate<T>(C, ldk, Nmat, kdev, &st->kc, prm.k, n, 0, s);
     launch_rotate<T>(Ut, ldk, Mmat, kdev, &st->kc, prm.k, n, 0, s);
     launch_rotate<T>(Ct, ldk, Mmat, kdev, &st->kc, prm.k, n, 0, s);
-    prof->end(pi, 10, s);
-    count(10);
+    prof->end(pi, 11, s);
+    count(11);
     fetch();
     kc = hv->kc;
-  }
-
-  // The Gram output is A (double for real problems); the dense SVD reads complex entries.
-  zd* gz = nullptr;
-  const zd* as_zd_gram(cudaStream_t st_) {
-    if (traits<T>::cx) return reinterpret_cast<const zd*>(G);
-    if (!gz) gz = dmalloc<zd>((size_t)GRAM_MAXCOLS * GRAM_MAXCOLS);
-    launch_real_to_zd(reinterpret_cast<const double*>(G), gz, (int64_t)GRAM_MAXCOLS * GRAM_MAXCOLS, st_);
-    count(1);
-    return gz;
   }
 
   // ------------------------------------------------------------------ Section 4.1-4.3 refresh
@@ -457,18 +445,15 @@ struct Solver : SolverBase {
     launch_combine<T>(Pht, Wphit, KMAX, kk, prm.k, Utc[jc], ldk, n, prm.setup_fp32, q);
     launch_spmm<V, T>(op, 0, Uc[jc], ldk, kk, prm.k, Cc[jc], prm.setup_fp32, q);
     launch_spmm<V, T>(op, 1, Utc[jc], ldk, kk, prm.k, Ctc[jc], prm.setup_fp32, q);
-    ColList<T> X2{}, Y2{};
-    append_block(X2, Ctc[jc], prm.k); append_block(X2, Cc[jc], prm.k);
-    append_block(Y2, Cc[jc], prm.k); append_block(Y2, Ctc[jc], prm.k);
-    launch_gram<T>(X2, Y2, n, prm.setup_fp32, gpart, gram_grid, G, q);
-    launch_dense_svd(!traits<T>::cx, kk, prm.k, as_zd_gram(q), nullptr, nullptr, prm.svd_tol, Nmat, Mmat, sig,
-                     &st->pcyc, nullptr, iflag + 3, q);
+    launch_svd_input<T>(Cc[jc], Ctc[jc], ldk, prm.k, prm.k, n, gpart, gram_grid, G, s2in, q);
+    launch_dense_svd(!traits<T>::cx, kk, prm.k, s2in, nullptr, nullptr, prm.svd_tol, Nmat, Mmat, sig, &st->pcyc,
+                     nullptr, iflag + 3, q);
     launch_rotate<T>(Uc[jc], ldk, Nmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, q);
     launch_rotate<T>(Cc[jc], ldk, Nmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, q);
     launch_rotate<T>(Utc[jc], ldk, Mmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, q);
     launch_rotate<T>(Ctc[jc], ldk, Mmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, q);
-    prof->end(pb, 11, q);
-    count(11);
+    prof->end(pb, 13, q);
+    count(13);
     RB_CUDA(cudaEventRecord(ev_ref, q));
     ref_pending = true;
   }
@@ -770,18 +755,8 @@ struct Solver : SolverBase {
     return end();
   }
 
-  void launch_real_to_zd(const double* a, zd* b, int64_t m, cudaStream_t st_) { launch_convert_rz(a, b, m, st_); }
-  static void launch_convert_rz(const double* a, zd* b, int64_t m, cudaStream_t st_);
 };
 
-__global__ void k_real_to_zd(const double* a, zd* b, int64_t m) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = zd(a[i], 0.0);
-}
-template <class V, class T>
-void Solver<V, T>::launch_convert_rz(const double* a, zd* b, int64_t m, cudaStream_t st_) {
-  k_real_to_zd<<<64, 256, 0, st_>>>(a, b, m);
-}
 
 // residual kernel for the refinement loop: r = b - Op x (FP64), norms via a small reduction
 template <class V, class T>
@@ -830,6 +805,7 @@ struct Impl {
   virtual void export_recycle(void* U, void* Ut, int* p) = 0;
   virtual void import_recycle(const void* U, const void* Ut, int p) = 0;
   virtual void set_refresh(int v) = 0;
+  virtual void history(double* out, int max, int* count) = 0;
   // FP64 handles: the solver that a batch drives directly, and the kind of its (V, T)
   virtual void* batch_solver(int* kind) = 0;
 };
@@ -1022,6 +998,17 @@ struct ImplT : Impl {
     prm.refresh = v;
     hi->prm.refresh = v;
     if (lo) lo->prm.refresh = v;
+  }
+
+  // ||r_m|| of the FP64 solver's last solve for its last min(max, HR) iterations (device ring)
+  void history(double* out, int max, int* count) override {
+    DevState h;
+    RB_CUDA(cudaMemcpyAsync(&h, hi->st, sizeof h, cudaMemcpyDeviceToHost, s));
+    RB_CUDA(cudaStreamSynchronize(s));
+    const int last = h.iter;
+    const int cnt = std::min(std::min(max, HR), last + 1);
+    for (int q = 0; q < cnt; ++q) out[q] = h.h_rnorm[(last - cnt + 1 + q) % HR];
+    *count = cnt;
   }
 
   void export_recycle(void* Uo, void* Uto, int* p) override {
@@ -1261,6 +1248,12 @@ extern "C" rbicg_status rbicg_reset(rbicg_handle h) {
   if (!h) return fail(nullptr, RBICG_ERR_ARG, "handle is NULL");
   if (h->impl) h->impl->reset();
   return RBICG_OK;
+}
+
+extern "C" rbicg_status rbicg_residual_history(rbicg_handle h, double* out, int max, int* count) {
+  if (!h || !out || !count || max < 1) return fail(h, RBICG_ERR_ARG, "null argument or max < 1");
+  if (!h->impl) return fail(h, RBICG_ERR_ARG, "no solve on this handle yet");
+  RB_GUARD(h, { h->impl->history(out, max, count); return RBICG_OK; })
 }
 
 extern "C" rbicg_status rbicg_set_refresh(rbicg_handle h, int refresh) {

@@ -161,11 +161,14 @@ template <class V, class T>
 void launch_spmm(const OpArgs<V>& op, int adjoint, const T* U, int ldu, const int* ncols_dev, int ncols_max,
                  T* out, int fp32, cudaStream_t s);
 template <class T>
-void launch_colnorm_gram(const T* Ct, const T* C, int ld, const int* k_dev, int kmax, int64_t n, int fp32,
-                         void* part, int grid, zd* S, double* nC, double* nCt, cudaStream_t s);
-template <class T>
 void launch_rotate(T* B, int ld, const zd* Nmat, const int* kin_dev, const int* kout_dev, int kmax, int64_t n,
                    int fp32, cudaStream_t s);
+// SVD input of Section 4.3: S = Ct^H C (k x k, FP64) and the column norms of C and Ct, packed into
+// the 2 kmax x 2 kmax array the dense SVD reads.  part: Gram partials (grid x 32 x 32 accumulators)
+// followed by 64 x grid doubles.
+template <class T>
+void launch_svd_input(const T* C, const T* Ct, int ld, int k, int kmax, int64_t n, void* part, int grid,
+                      typename traits<T>::acc* G, zd* S2, cudaStream_t s);
 template <class Tfrom, class Tto>
 void launch_convert(const Tfrom* a, Tto* b, int64_t n, cudaStream_t s);
 template <class T>

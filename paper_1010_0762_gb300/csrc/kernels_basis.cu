@@ -16,26 +16,35 @@ template <class T, bool F32> struct comp_of { typedef T type; };
 template <> struct comp_of<double, true> { typedef float type; };
 template <> struct comp_of<cplx<double>, true> { typedef cplx<float> type; };
 
-constexpr int GT = 64;        // Gram tile (columns of X and of Y per block)
+constexpr int GT = 32;        // Gram tile (columns of X and of Y per block)
 constexpr int GROWS = 16;     // rows staged per step
 constexpr int GFLUSH = 16;    // steps accumulated in the compute type before an FP64 flush
 
+// Block: one GT x GT tile of G for a contiguous range of rows.  Warp w computes the 8 x 16
+// sub-tile (rows 8 (w & 3) .., columns 16 (w >> 2) ..), each lane a 2 x 2 block of it.  A warp
+// whose sub-tile lies beyond the last column of X or Y skips the products (warp-uniform), so the
+// FP64 work follows the actual column counts (the pencil's Grams are 40..110 columns wide, far
+// from multiples of a large tile); every entry is accumulated over the rows in the same order
+// whichever warp holds it.
 template <class T, class Cm>
 __global__ void __launch_bounds__(256) k_gram(ColList<T> X, ColList<T> Y, int64_t n, int64_t rows_per_block,
                                               typename traits<T>::acc* part) {
   typedef typename traits<T>::acc A;
   __shared__ Cm xs[GROWS][GT];
   __shared__ Cm ys[GROWS][GT];
-  const int ta = threadIdx.x & 15, tb = threadIdx.x >> 4;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ra = 8 * (warp & 3) + 2 * (lane & 3);      // tile rows ra, ra + 1
+  const int cb = 16 * (warp >> 2) + 2 * (lane >> 2);   // tile columns cb, cb + 1
   const int ax0 = blockIdx.y * GT, by0 = blockIdx.z * GT;
+  const bool active = ax0 + 8 * (warp & 3) < X.m && by0 + 16 * (warp >> 2) < Y.m;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
   const int64_t r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
-  A acc[4][4];
-  Cm loc[4][4];
+  A acc[2][2];
+  Cm loc[2][2];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { acc[i][j] = A(0.0); loc[i][j] = Cm(0); }
+    for (int j = 0; j < 2; ++j) { acc[i][j] = A(0.0); loc[i][j] = Cm(0); }
   int step = 0;
   for (int64_t rb0 = r0; rb0 < r1; rb0 += GROWS) {
     __syncthreads();
@@ -52,31 +61,32 @@ __global__ void __launch_bounds__(256) k_gram(ColList<T> X, ColList<T> Y, int64_
       ys[rr][cc] = yv;
     }
     __syncthreads();
+    if (active) {
 #pragma unroll 4
-    for (int rr = 0; rr < GROWS; ++rr) {
-      Cm xa[4], yb[4];
+      for (int rr = 0; rr < GROWS; ++rr) {
+        const Cm xa[2] = {xs[rr][ra], xs[rr][ra + 1]};
+        const Cm yb[2] = {ys[rr][cb], ys[rr][cb + 1]};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) { xa[i] = xs[rr][ta + 16 * i]; yb[i] = ys[rr][tb + 16 * i]; }
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) loc[i][j] += cmul(xa[i], yb[j]);
+          for (int j = 0; j < 2; ++j) loc[i][j] += cmul(xa[i], yb[j]);
+      }
     }
     if (++step == GFLUSH) {
       step = 0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { acc[i][j] += cvt<A>(loc[i][j]); loc[i][j] = Cm(0); }
+        for (int j = 0; j < 2; ++j) { acc[i][j] += cvt<A>(loc[i][j]); loc[i][j] = Cm(0); }
     }
   }
   const int ntile = gridDim.y * gridDim.z;
   const int tile = blockIdx.y * gridDim.z + blockIdx.z;
   A* out = part + ((int64_t)blockIdx.x * ntile + tile) * (GT * GT);
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) out[(ta + 16 * i) * GT + (tb + 16 * j)] = acc[i][j] + cvt<A>(loc[i][j]);
+    for (int j = 0; j < 2; ++j) out[(ra + i) * GT + (cb + j)] = acc[i][j] + cvt<A>(loc[i][j]);
 }
 
 template <class A>
@@ -110,8 +120,64 @@ void launch_gram(const ColList<T>& X, const ColList<T>& Y, int64_t n, int fp32, 
                                                                                      tz, X.m, Y.m, G);
 }
 
+// ------------------------------------------------------------------------------------
+// Input of the Section 4.3 SVD: S = Ct^H C (k x k) and the column norms of C and Ct, packed
+// where the SVD kernel reads them in a 2 kmax x 2 kmax row-major array (S top-left, ||C e_c||^2
+// on the diagonal of the bottom-left block, ||Ct e_c||^2 on that of the top-right block).  The
+// norms are column sums of squares of the row-major n x ld blocks: thread (t % 64) holds one
+// column (C's k, then Ct's k), thread t / 64 one of four row lanes; blocks write per-column
+// partials, one block adds them in block order.
+// ------------------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) k_colnorms(const T* __restrict__ C, const T* __restrict__ Ct, int ld, int k,
+                                                  int64_t n, int64_t rows_per_block, double* part) {
+  __shared__ double red[4][64];
+  const int c = threadIdx.x & 63, lanes = 4, l = threadIdx.x >> 6;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
+  double acc = 0.0;
+  if (c < 2 * k) {
+    const T* B = c < k ? C : Ct;
+    const int cc = c < k ? c : c - k;
+    for (int64_t row = r0 + l; row < r1; row += lanes) acc += (double)abs2(B[row * ld + cc]);
+  }
+  red[l][c] = acc;
+  __syncthreads();
+  if (threadIdx.x < 64) part[(int64_t)blockIdx.x * 64 + c] = red[0][c] + red[1][c] + red[2][c] + red[3][c];
+}
+
+template <class A>
+__global__ void k_svd_pack(const double* part, int nblk, const A* G, int k, int kmax, zd* S2) {
+  const int ld2 = 2 * kmax;
+  for (int e = threadIdx.x; e < ld2 * ld2; e += blockDim.x) S2[e] = zd(0.0);
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) S2[(e / k) * ld2 + e % k] = to_zd(G[e]);
+  for (int c = threadIdx.x; c < 2 * k; c += blockDim.x) {
+    double sacc = 0.0;
+    for (int b = 0; b < nblk; ++b) sacc += part[(int64_t)b * 64 + c];
+    if (c < k) S2[(kmax + c) * ld2 + c] = zd(sacc);              // ||C e_c||^2
+    else S2[(c - k) * ld2 + kmax + (c - k)] = zd(sacc);            // ||Ct e_c||^2
+  }
+}
+
+template <class T>
+void launch_svd_input(const T* C, const T* Ct, int ld, int k, int kmax, int64_t n, void* part, int grid,
+                      typename traits<T>::acc* G, zd* S2, cudaStream_t s) {
+  typedef typename traits<T>::acc A;
+  ColList<T> X{}, Y{};
+  for (int c = 0; c < k; ++c) { X.c[c].p = Ct + c; X.c[c].ld = ld; Y.c[c].p = C + c; Y.c[c].ld = ld; }
+  X.m = Y.m = k;
+  launch_gram<T>(X, Y, n, 0, part, grid, G, s);
+  // the norms' partials go after the Gram's (the Gram uses at most grid x GT^2 entries)
+  double* np = reinterpret_cast<double*>(reinterpret_cast<A*>(part) + (size_t)grid * GT * GT);
+  const int nb = std::max(1, std::min(grid, (int)((n + 255) / 256)));
+  const int64_t rpb = (n + nb - 1) / nb;
+  k_colnorms<T><<<nb, 256, 0, s>>>(C, Ct, ld, k, n, rpb, np);
+  k_svd_pack<A><<<1, 256, 0, s>>>(np, nb, G, k, kmax, S2);
+}
+
 // out[row, c] = sum_a src_a[row] * W[a, c]   (c < ncols, read on the device)
-// KC: accumulators per row, a multiple of 8 >= ncols_max (the recycle dimension)
+// KC: accumulators per row, one of 8, 12, 16, 20, 24, 32, >= ncols_max (the recycle dimension)
 template <class T, class Cm, int KC>
 __global__ void __launch_bounds__(256) k_combine(ColList<T> src, const zd* W, int ldw, const int* ncols_dev,
                                                  int ncols_max, T* out, int ldo, int64_t n) {
@@ -157,8 +223,12 @@ void launch_combine(const ColList<T>& src, const zd* W, int ldw, const int* ncol
     cudaFuncSetAttribute(k_combine<T, T, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);            \
     k_combine<T, T, KC><<<grid, 256, src.m * KC * sizeof(T), s>>>(src, W, ldw, ncols_dev, ncols_max, out, ldo, n); \
   }
+  // accumulators per row: the recycle dimension rounded up to 4 (k = 10, 16, 20 are common), so
+  // the FP64 products follow k instead of a coarser multiple
   if (ncols_max <= 8) { RB_COMB(8) }
+  else if (ncols_max <= 12) { RB_COMB(12) }
   else if (ncols_max <= 16) { RB_COMB(16) }
+  else if (ncols_max <= 20) { RB_COMB(20) }
   else if (ncols_max <= 24) { RB_COMB(24) }
   else { RB_COMB(32) }
 #undef RB_COMB
@@ -201,7 +271,9 @@ void launch_rotate(T* B, int ld, const zd* Nmat, const int* kin_dev, const int* 
   else                                                                                                     \
     k_rotate<T, T, KC><<<grid, 256, 0, s>>>(B, ld, Nmat, kin_dev, kout_dev, kmax, n);
   if (kmax <= 8) { RB_ROT(8) }
+  else if (kmax <= 12) { RB_ROT(12) }
   else if (kmax <= 16) { RB_ROT(16) }
+  else if (kmax <= 20) { RB_ROT(20) }
   else if (kmax <= 24) { RB_ROT(24) }
   else { RB_ROT(32) }
 #undef RB_ROT
@@ -284,7 +356,9 @@ void launch_axpy_inplace(T* y, const T* x, int64_t n, cudaStream_t s) {
   template void launch_combine<T>(const ColList<T>&, const zd*, int, const int*, int, T*, int, int64_t, int,  \
                                   cudaStream_t);                                                             \
   template void launch_rotate<T>(T*, int, const zd*, const int*, const int*, int, int64_t, int, cudaStream_t); \
-  template void launch_axpy_inplace<T>(T*, const T*, int64_t, cudaStream_t);
+  template void launch_axpy_inplace<T>(T*, const T*, int64_t, cudaStream_t);                                 \
+  template void launch_svd_input<T>(const T*, const T*, int, int, int, int64_t, void*, int,                   \
+                                    typename traits<T>::acc*, zd*, cudaStream_t);
 
 RB_INST_T(double)
 RB_INST_T(float)

@@ -14,8 +14,9 @@
 
 namespace rb {
 
-// Scratch: RB_NOALLOC_CHUNKS partial tiles of 64 x 64 complex doubles (8 MiB).  Every GPU that
-// loads this library holds this array until the process exits.
+// Scratch: room for RB_NOALLOC_CHUNKS x 64 x 64 complex doubles of partial sums (8 MiB): for
+// mx, my <= 64 the Gram kernel writes at most that many (its row chunks times the tiles of X^H Y).
+// Every GPU that loads this library holds this array until the process exits.
 constexpr int RB_NOALLOC_TILE = 64;
 constexpr int RB_NOALLOC_CHUNKS = 128;
 constexpr size_t RB_NOALLOC_BYTES = (size_t)RB_NOALLOC_CHUNKS * RB_NOALLOC_TILE * RB_NOALLOC_TILE * sizeof(zd);
@@ -72,8 +73,8 @@ extern "C" rbicg_status rbicg_op_gram_noalloc(rbicg_dtype dtype, int64_t n, cons
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // Every partial tile that the reduction reads is first written by the Gram kernel of the
-  // same call (one full 64 x 64 tile per row chunk, zero-padded), so no part of the shared
-  // scratch has to start at zero; the previous call's contents are simply overwritten.
+  // same call (whole tiles per row chunk, zero-padded), so no part of the shared scratch has to
+  // start at zero; the previous call's contents are simply overwritten.
   if (dtype == RBICG_R64) {
     ColList<double> xl{}, yl{};
     for (int c = 0; c < mx; ++c) { xl.c[c].p = reinterpret_cast<const double*>(X) + c; xl.c[c].ld = ldx; }

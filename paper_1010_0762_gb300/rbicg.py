@@ -82,6 +82,7 @@ def _load():
         "rbicg_import_recycle": (ci, [vp, vp, vp, ci]),
         "rbicg_reset": (ci, [vp]),
         "rbicg_set_refresh": (ci, [vp, ci]),
+        "rbicg_residual_history": (ci, [vp, vp, ci, C.POINTER(ci)]),
         "rbicg_destroy": (ci, [vp]),
         "rbicg_last_error": (C.c_char_p, [vp]),
         "rbicg_launch_count": (i64, [vp]),
@@ -219,6 +220,13 @@ class Solver:
 
     def reset(self):
         _check(lib.rbicg_reset(self.h), self.h)
+
+    def residual_history(self, max_count=132):
+        """||r_m|| of the last solve's last iterations (oldest first)."""
+        out = np.zeros(max_count)
+        cnt = C.c_int(0)
+        _check(lib.rbicg_residual_history(self.h, out.ctypes.data_as(C.c_void_p), max_count, C.byref(cnt)), self.h)
+        return out[:cnt.value].copy()
 
     def set_refresh(self, refresh):
         _check(lib.rbicg_set_refresh(self.h, int(refresh)), self.h)

@@ -65,7 +65,7 @@ def _irka_problem(N=12, c=10.0, r=4):
     return A, b, cvec, I.irka_shifts(r, 3001)
 
 
-@pytest.mark.parametrize("strategy,batched", [(1, 1), (1, 0), (0, 1), (2, 0), (3, 0)])
+@pytest.mark.parametrize("strategy,batched", [(1, 1), (1, 0), (0, 1), (2, 0), (3, 0), (4, 1)])
 def test_irka_matches_oracle(R, strategy, batched):
     # Algorithm 3 with the library's RBiCG solves (tol 1e-12) against the oracle's Algorithm 3
     # with direct solves: the shifts after every step and the last reduced model agree
@@ -84,12 +84,13 @@ def test_irka_matches_oracle(R, strategy, batched):
 
 
 def test_irka_recycling_counts_match_oracle_and_save_iterations(R):
-    # strategy 1 (Section 5.3) through the batched launch: per-solve iteration counts follow the
-    # oracle's Algorithm 2 with the same strategy, and recycling needs fewer iterations than BiCG
+    # strategies 1 and 4 (Section 5.3; 4: one space shared by the shifts) through the batched
+    # launch: per-solve iteration counts follow the oracle's Algorithm 2 with the same strategy, and
+    # recycling needs fewer iterations than BiCG
     A, b, c, sh = _irka_problem(r=8)
     op = R.Operator.from_csr(A)
     tot = {}
-    for strategy in (0, 1):
+    for strategy in (0, 1, 4):
         got = R.irka(op, _dev(b), _dev(c), sh, max_steps=5, shift_tol=1e-14, strategy=strategy,
                      solver_k=8, solver_s=20, solver_tol=1e-10, solver_setup_fp32=0)
         ref = IR.irka(A, b, c, sh, IR.rbicg_solver(A, b, c, k=8, s=20, tol=1e-10, strategy=strategy),
@@ -98,7 +99,7 @@ def test_irka_recycling_counts_match_oracle_and_save_iterations(R):
         assert its.shape == rits.shape
         assert np.all(np.abs(its - rits) <= np.maximum(3, 0.05 * rits)), (its, rits)
         tot[strategy] = its[1:].sum()
-    assert tot[1] < 0.9 * tot[0], tot
+    assert tot[1] < 0.9 * tot[0] and tot[4] < 0.9 * tot[0], tot
 
 
 def test_irka_refresh_every_keeps_spaces_between_refreshes(R):

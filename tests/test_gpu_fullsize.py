@@ -164,3 +164,63 @@ def test_largest_recycle_space_and_cycle(R):
             assert res["cycles"] >= 0
     U, Ut = S.export_recycle()
     assert U.shape[1] <= 32
+
+
+def _import_and_solve(R, S, A, b, bt, U, Ut, n):
+    op = R.Operator.from_csr(A)
+    S.update_recycle(op)
+    S.import_recycle(_dev(np.ascontiguousarray(U)), _dev(np.ascontiguousarray(Ut)))
+    x = _dev(np.zeros(n)); xt = _dev(np.zeros(n))
+    res = S.solve_pair(op, _dev(b), _dev(bt), x, xt)
+    return res, x.cpu().numpy(), xt.cpu().numpy()
+
+
+def test_config2_recycled_pair_two_cycles_match_oracle(R):
+    # 512 x 512, k = 20, s = 40, all-FP64 refresh: pair 1 solved with the oracle's recycle space
+    # (from two cycles of pair 0) on both sides, so that the recycled iteration itself is compared
+    # at full size: the system start keeps the same columns (Section 4.3), the recurrence residual
+    # norms of the first two cycles agree element by element and so do the iterates after them
+    # (Algorithm 2 step 7 applied)
+    seq = I.convdiff_sequence(512, [10.0, 10.0], 2, 0.01, 2000, bt_kind="normal")
+    n = seq[0]["A"].n
+    z = np.zeros(n)
+    r0 = O.rbicg_pair(seq[0]["A"], seq[0]["b"], seq[0]["bt"], z, z, None, k=20, s=40, tol=1e-8, max_itn=80)
+    rec = O.biorth_recycle(seq[1]["A"], r0.U_next, r0.Ut_next, 1e-6)
+    ref = O.rbicg_pair(seq[1]["A"], seq[1]["b"], seq[1]["bt"], z, z, rec, k=20, s=40, tol=1e-8, max_itn=80)
+    S = R.Solver(n, k=20, s=40, tol=1e-8, max_itn=80, setup_fp32=0, guard=0.0)
+    res, x, xt = _import_and_solve(R, S, seq[1]["A"], seq[1]["b"], seq[1]["bt"], r0.U_next, r0.Ut_next, n)
+    assert res["recycle_dim"] == rec[0].shape[1] == ref.recycle_dim
+    assert res["iters"] == ref.iters == 80
+    hist = S.residual_history()
+    rh = np.array(ref.hist["rnorm"])
+    assert len(hist) == len(rh) == 81
+    np.testing.assert_allclose(hist, rh, rtol=1e-8, atol=0)
+    for a, b_ in ((x, ref.x), (xt, ref.xt)):
+        assert np.abs(a - b_).max() <= 1e-6 * np.abs(b_).max()
+
+
+def test_config1_recycled_pairs_match_oracle(R):
+    # 32 x 32, c0 = (10, 10), 1 % drift, bt = ones, k = 10, all-FP64 refresh.  For pairs 1..4
+    # the oracle's incoming recycle space is imported, so each recycled pair is compared on its
+    # own (the full sequence is rounding-chaotic, see above): columns kept by the system start,
+    # the first two cycles' residual norms element by element, and at tol 1e-12 the solutions
+    # element by element.
+    seq = I.convdiff_sequence(32, [10.0, 10.0], 5, 0.01, 1000, bt_kind="ones")
+    n = seq[0]["A"].n
+    z = np.zeros(n)
+    refs = O.rbicg_sequence(seq, k=10, s=40, tol=1e-12)
+    for j in range(1, 5):
+        U, Ut = refs[j - 1].U_next, refs[j - 1].Ut_next
+        pr = seq[j]
+        rec = O.biorth_recycle(pr["A"], U, Ut, 1e-6)
+        two = O.rbicg_pair(pr["A"], pr["b"], pr["bt"], z, z, rec, k=10, s=40, tol=1e-12, max_itn=80)
+        S = R.Solver(n, k=10, s=40, tol=1e-12, max_itn=80, setup_fp32=0, guard=0.0)
+        res, _, _ = _import_and_solve(R, S, pr["A"], pr["b"], pr["bt"], U, Ut, n)
+        assert res["recycle_dim"] == rec[0].shape[1], (j, res)
+        h, rh = S.residual_history(), np.array(two.hist["rnorm"][-len(S.residual_history()):])
+        np.testing.assert_allclose(h, rh, rtol=1e-8, atol=0, err_msg="pair %d" % j)
+        S2 = R.Solver(n, k=10, s=40, tol=1e-12, setup_fp32=0, guard=0.0)
+        res2, x, xt = _import_and_solve(R, S2, pr["A"], pr["b"], pr["bt"], U, Ut, n)
+        assert res2["status"] in (R.OK, R.RECYCLE_EMPTY) and refs[j].status in (O.STATUS_OK, O.STATUS_RECYCLE_EMPTY)
+        for a, b_ in ((x, refs[j].x), (xt, refs[j].xt)):
+            assert np.abs(a - b_).max() <= 1e-6 * np.abs(b_).max(), j
