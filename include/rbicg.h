@@ -76,7 +76,7 @@ typedef enum {
 /* Solver parameters.  Defaults (rbicg_default_params): k = 10, s = 40, max_itn = 20000,
  * tol = 1e-8, svd_tol = 1e-6, inner_tol = 1e-5, refine_max = 12, precision = FP64,
  * seed = 0, setup_fp32 = 1, recycle = 1, inner_svd_tol = 1e-3, guard = 1.5, restarts = 0,
- * grid_blocks = 0, refresh = 1. */
+ * grid_blocks = 0, refresh = 1, setup_blocks = 0, graphs = 1. */
 typedef struct {
   int k;                   /* recycle dimension: columns kept in U, Ut (Section 3, 4.1); 1..32 */
   int s;                   /* cycle length (Section 4.1); 2..64, k + s <= 80 */
@@ -115,6 +115,10 @@ typedef struct {
                               the recycle space may be recomputed only for some systems of a
                               sequence, e.g. every fifth IRKA step).  Changeable between pairs
                               with rbicg_set_refresh. */
+  int setup_blocks;        /* blocks of the refresh's Gram products (0: the default, 2 x SMs);
+                              rbicg_autotune_params picks one by timed trials */
+  int graphs;              /* 1 (default): each cycle's iteration launches run as one CUDA graph;
+                              0: launched one by one */
 } rbicg_params;
 
 /* A sparse operator.  Operator = A when has_shift == 0, (shift I - A) otherwise. */
@@ -211,6 +215,15 @@ rbicg_status rbicg_engine_destroy(rbicg_engine e);
  * shape is returned without new trials.  Set params->grid_blocks to use it. */
 rbicg_status rbicg_autotune(const rbicg_params *params, rbicg_dtype dtype, const rbicg_csr *A, int trial_iters,
                             int *grid_blocks, double *us_per_iter);
+
+/* Autotuner over three launch knobs (no counterpart in the paper): grid_blocks as rbicg_autotune
+ * does; then, with that grid, setup_blocks in {1, 2, 4} x SMs and graphs in {1, 0}, each by timing
+ * three cycles of recycled iterations with their refreshes (k, s from params, tolerance 0, on a
+ * private stream, from a random start).  *out = *params with the three fields set to the fastest
+ * (the grid from the cache when rbicg_autotune already tuned this shape); *us_per_iter (may be
+ * NULL) the time per recycled iteration, refresh included. */
+rbicg_status rbicg_autotune_params(const rbicg_params *params, rbicg_dtype dtype, const rbicg_csr *A,
+                                   int trial_iters, rbicg_params *out, double *us_per_iter);
 
 /* Copy the recycle space for the next pair into caller buffers U, Ut (device, n x k row-major,
  * k = params->k columns, unused columns zero); *p receives the number of valid columns. */

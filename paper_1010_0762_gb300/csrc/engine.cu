@@ -196,6 +196,13 @@ struct Solver : SolverBase {
   int stall_window = 0;       // > 0: stop once ||r|| has not reached a new minimum for this
                               // many iterations (inner FP32 solves)
   T *x_save = nullptr, *xt_save = nullptr;   // initial guesses kept while the guard is armed
+  // inner FP32 solves (stall_window > 0): the iterate with the smallest residual seen at a cycle
+  // end, with its zeta_c, is kept and returned when the solve ends without converging (a BiCG
+  // iterate after a residual spike can be far worse than one a cycle earlier)
+  T *x_best = nullptr, *xt_best = nullptr;
+  zd* zc_best = nullptr;
+  double best_metric = 0.0;
+  bool have_best = false;
   int pending_start = 0;
   // device scratch
   DevState* st = nullptr;
@@ -231,7 +238,8 @@ struct Solver : SolverBase {
     grid = prm.grid_blocks > 0
                ? (int)std::min<int64_t>(prm.grid_blocks, std::max<int64_t>(1, (n + NTHREADS - 1) / NTHREADS))
                : (int)std::max<int64_t>(1, std::min<int64_t>((n + NTHREADS - 1) / NTHREADS, (int64_t)sms * 3));
-    gram_grid = 2 * sms;
+    // blocks of the refresh's Gram products (rbicg_params.setup_blocks; default 2 x SMs)
+    gram_grid = prm.setup_blocks > 0 ? prm.setup_blocks : 2 * sms;
     const int64_t ldv = ((n + 31) / 32) * 32;   // padded vector stride (256-byte aligned slots)
     ring = dmalloc<T>(ldv * R);
     ringt = dmalloc<T>(ldv * R);
@@ -248,9 +256,12 @@ struct Solver : SolverBase {
     ring_ld = ldv;
     st = dmalloc<DevState>(1);
     RB_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
-    const size_t part_elems = std::max<size_t>(part_elems_for(grid), (size_t)gram_grid * 64 * 64);
+    // Gram partials: one 32 x 32 tile per (row chunk, tile) with at most max(grid, tiles) of them
+    // (36 tiles at 176 x 176 columns), then the SVD input's column-norm partials
+    const size_t gelems = (size_t)std::max(gram_grid, 64) * 64 * 64;
+    const size_t part_elems = std::max<size_t>(part_elems_for(grid), gelems);
     part = dmalloc<A>(part_elems);
-    gpart = dmalloc<A>((size_t)gram_grid * 64 * 64);
+    gpart = dmalloc<A>(gelems);
     G = dmalloc<A>((size_t)GRAM_MAXCOLS * GRAM_MAXCOLS);
     work = dmalloc<zd>(dense_work_elems_fwd());
     Wphi = dmalloc<zd>(MMAX * KMAX); Wphit = dmalloc<zd>(MMAX * KMAX);
@@ -275,6 +286,9 @@ struct Solver : SolverBase {
     cudaFree(Nmat); cudaFree(Mmat); cudaFree(sig); cudaFree(s2in); cudaFree(iflag);
     if (x_save) cudaFree(x_save);
     if (xt_save) cudaFree(xt_save);
+    if (x_best) cudaFree(x_best);
+    if (xt_best) cudaFree(xt_best);
+    if (zc_best) cudaFree(zc_best);
     free_op();
     if (hv) cudaFreeHost(hv);
     if (ev_cycle) cudaEventDestroy(ev_cycle);
@@ -488,7 +502,9 @@ struct Solver : SolverBase {
   int cyc_todo = -1, cyc_kt = -1;
   VecArgs<T> cyc_v{};
   OpArgs<V> cyc_op{};
-  bool use_graphs = getenv("RBICG_NO_GRAPHS") == nullptr;   // profilers see plain launches
+  // cycles as CUDA graphs unless rbicg_params.graphs = 0 or RBICG_NO_GRAPHS is set (profilers
+  // then see plain launches)
+  bool use_graphs = prm.graphs != 0 && getenv("RBICG_NO_GRAPHS") == nullptr;
 
   void drop_graph() {
     if (cyc_exec) cudaGraphExecDestroy(cyc_exec);
@@ -537,6 +553,8 @@ struct Solver : SolverBase {
     R_.recycle = prm.recycle != 0;
     R_.done = hv->done;
     R_.best_r = hv->rnorm;
+    have_best = false;
+    best_metric = 1e300;
     // stagnation guard (not in the paper): see rbicg_params.guard
     R_.guard_limit = (kc > 0 && prm.guard > 0.0 && last_plain_iters > 0)
                          ? (int)std::min<double>(2e9, prm.guard * last_plain_iters) : 0x7fffffff;
@@ -623,6 +641,22 @@ struct Solver : SolverBase {
     if (!R_.done && diverge > 0.0 && hv->rnorm > diverge * (hv->bnorm > 0 ? hv->bnorm : 1.0)) R_.done = DONE_MAXIT;
     if (hv->rnorm < R_.best_r) { R_.best_r = hv->rnorm; R_.best_at = total; }
     if (!R_.done && stall_window > 0 && total - R_.best_at > stall_window) R_.done = DONE_MAXIT;
+    if (stall_window > 0 && R_.done != DONE_NONFINITE) {
+      const double m = std::max(hv->rnorm / (hv->bnorm > 0 ? hv->bnorm : 1.0),
+                                hv->btnorm > 0 ? hv->rtnorm / hv->btnorm : 0.0);
+      if (m < best_metric) {
+        best_metric = m;
+        if (!x_best) {
+          x_best = dmalloc<T>(n); xt_best = dmalloc<T>(n);
+          zc_best = dmalloc<zd>(2 * KMAX);
+        }
+        RB_CUDA(cudaMemcpyAsync(x_best, R_.x, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+        RB_CUDA(cudaMemcpyAsync(xt_best, R_.xt, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+        RB_CUDA(cudaMemcpyAsync(zc_best, st->zeta_c, sizeof(zd) * KMAX, cudaMemcpyDeviceToDevice, s));
+        RB_CUDA(cudaMemcpyAsync(zc_best + KMAX, st->zetat_c, sizeof(zd) * KMAX, cudaMemcpyDeviceToDevice, s));
+        have_best = true;
+      }
+    }
     const bool breakdown = R_.done == DONE_BREAK_RHO || R_.done == DONE_BREAK_PQ;
     const bool bad_end = breakdown || R_.done == DONE_NONFINITE;
     const bool stalled = !R_.done && R_.iter >= R_.guard_limit;
@@ -649,6 +683,8 @@ struct Solver : SolverBase {
       set_field(&DevState::max_itn, std::max(1, R_.max_itn - R_.iter_before));
       R_.out.fallback = 1;
       R_.guard_limit = 0x7fffffff;
+      have_best = false;   // the kept iterate belongs to the abandoned leg
+      best_metric = 1e300;
       const int pi2 = prof->begin(7, s);
       launch_init<V, T>(op, R_.v, st, part, 0, grid, 0, s);
       prof->end(pi2, 2, s);
@@ -688,6 +724,13 @@ struct Solver : SolverBase {
   PairOut end() {
     Run& R_ = run;
     PairOut out = R_.out;
+    if (stall_window > 0 && have_best && R_.done != DONE_CONVERGED) {
+      // an inner solve that did not converge returns the best iterate it reached at a cycle end
+      RB_CUDA(cudaMemcpyAsync(R_.x, x_best, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+      RB_CUDA(cudaMemcpyAsync(R_.xt, xt_best, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+      RB_CUDA(cudaMemcpyAsync(st->zeta_c, zc_best, sizeof(zd) * KMAX, cudaMemcpyDeviceToDevice, s));
+      RB_CUDA(cudaMemcpyAsync(st->zetat_c, zc_best + KMAX, sizeof(zd) * KMAX, cudaMemcpyDeviceToDevice, s));
+    }
     const int pf = prof->begin(7, s);
     launch_finish<V, T>(op, R_.v, st, part, R_.kt, grid, s);
     prof->end(pf, 2, s);
@@ -743,6 +786,10 @@ struct Solver : SolverBase {
 
   PairOut solve(const T* b, const T* bt, T* x, T* xt, double tol, int max_itn, uint64_t seed) {
     begin(b, bt, x, xt, tol, max_itn, seed);
+    return run_to_end();
+  }
+  // the cycles of a begun solve, then step 7 (a solve that begin() finished goes straight to end)
+  PairOut run_to_end() {
     defer_refresh = true;
     while (!run.done) {
       launch_cycle(cycle_len());
@@ -806,6 +853,14 @@ struct Impl {
   virtual void import_recycle(const void* U, const void* Ut, int p) = 0;
   virtual void set_refresh(int v) = 0;
   virtual void history(double* out, int max, int* count) = 0;
+  // FP32-refined handles in the engine: begin the refinement / continue it after the solver that
+  // the engine stepped (kind) finished its cycles; both return 1 with the next solver to step
+  // (*solver, *kind) or 0 when refine_result() holds the result
+  virtual int refine_begin(const void* b, const void* bt, void* x, void* xt, void** solver, int* kind) = 0;
+  virtual int refine_after(int kind, void** solver, int* kindout) = 0;
+  virtual rbicg_result refine_result() = 0;
+  // run this handle's work (refinement kernels and both solvers) on st; returns the previous stream
+  virtual cudaStream_t swap_stream(cudaStream_t st) = 0;
   // FP64 handles: the solver that a batch drives directly, and the kind of its (V, T)
   virtual void* batch_solver(int* kind) = 0;
 };
@@ -881,91 +936,176 @@ struct ImplT : Impl {
     return sqrt(t);
   }
 
-  rbicg_result solve(const void* bv, const void* btv, void* xv, void* xtv) override {
-    const T* b = reinterpret_cast<const T*>(bv);
-    const T* bt = reinterpret_cast<const T*>(btv);
-    T* x = reinterpret_cast<T*>(xv);
-    T* xt = reinterpret_cast<T*>(xtv);
+  // ---- FP64 iterative refinement around FP32 inner RBiCG solves, as a resumable state machine:
+  // refine_begin() / refine_after() return what runs next (REF_DONE, REF_INNER: the FP32 solver
+  // lo has begun an inner solve, REF_FP64: the FP64 solver hi has begun the fallback solve).
+  // solve() drives it to the end on the handle's stream; the batching engine drives the same
+  // states one cycle at a time, so a served FP32-refined request overlaps the others.
+  enum { REF_DONE = 0, REF_INNER = 1, REF_FP64 = 2 };
+  struct RefState {
+    const T* b = nullptr; const T* bt = nullptr; T* x = nullptr; T* xt = nullptr;
+    double nb = 0, nbt = 0, rr = 0, rtr = 0;
+    int step = 0, total_iters = 0, cycles = 0, rdim = 0, first_inner = -1, inner_cap = 0, status = 0;
+    bool retried_plain = false, pc = false, dc = false;
     rbicg_result res{};
-    if (!lo || fp64_only) return solve_fp64(b, bt, x, xt, 0, 0);
-    // FP64 iterative refinement around FP32 inner RBiCG solves
-    const int grid = std::max(1, std::min((int)((n + 255) / 256), num_sms() * 8));
-    const double nb = norm(b), nbt = norm(bt);
-    int status = RBICG_NOT_CONVERGED;
-    double rr = 0, rtr = 0;
-    int step = 0, total_iters = 0, cycles = 0, rdim = 0;
-    int first_inner = -1, inner_cap = prm.max_itn;
-    bool retried_plain = false;
-    for (;; ++step) {
-      k_residual<V, T><<<grid, 256, 0, s>>>(hi->op, b, x, r64, 0);
-      k_residual<V, T><<<grid, 256, 0, s>>>(hi->op, bt, xt, rt64, 1);
-      *launches += 2;
-      rr = norm(r64);
-      rtr = norm(rt64);
-      if (debug_on()) fprintf(stderr, "[rbicg] refine step %d relres %.3e dual %.3e\n", step, rr / (nb > 0 ? nb : 1.0),
-                              rtr / (nbt > 0 ? nbt : 1.0));
-      const bool pc = rr <= prm.tol * (nb > 0 ? nb : 1.0) || (nb == 0 && rr == 0);
-      const bool dc = nbt == 0.0 || rtr <= prm.tol * nbt;
-      if (pc && dc) { status = RBICG_OK; break; }
-      if (step >= prm.refine_max) break;
-      launch_convert<T, T32>(r64, r32, n, s);
-      launch_convert<T, T32>(rt64, rt32, n, s);
-      RB_CUDA(cudaMemsetAsync(d32, 0, sizeof(T32) * n, s));
-      RB_CUDA(cudaMemsetAsync(dt32, 0, sizeof(T32) * n, s));
-      *launches += 2;
-      auto o = lo->solve(r32, rt32, d32, dt32, prm.inner_tol, inner_cap, prm.seed + step);
-      total_iters += o.iters;
-      cycles += o.cycles;
-      rdim = o.recycle_dim;
-      // a non-finite inner solve is treated like an unusable correction (retried as plain BiCG)
-      if (o.status < 0 && o.status != RBICG_ERR_NONFINITE) { status = o.status; break; }
-      if (first_inner < 0) {
-        first_inner = o.iters;
-        inner_cap = std::min(prm.max_itn, std::max(200, 4 * first_inner + 100));
-      }
-      // A correction is used only if the inner solve reduced its own residual; otherwise the
-      // inner recycle space is dropped and the step is retried once as plain FP32 BiCG.
-      const bool usable = o.status != RBICG_ERR_NONFINITE &&
-                          (o.status == RBICG_OK || o.status == RBICG_RECYCLE_EMPTY ||
-                           (o.true_relres < 0.5 && (dc || o.true_relres_dual < 0.5)));
-      if (debug_on())
-        fprintf(stderr, "[rbicg] inner step %d status %d iters %d relres %.3e/%.3e usable %d\n", step, o.status,
-                o.iters, o.true_relres, o.true_relres_dual, (int)usable);
-      if (!usable) {
-        if (retried_plain) {
-          // the FP32 recurrence does not converge on this problem even without a recycle
-          // space: this handle continues in FP64 RBiCG from the refined iterate
-          fp64_only = true;
-          return solve_fp64(b, bt, x, xt, total_iters, step);
-        }
-        retried_plain = true;
-        lo->kU = 0;
-        lo->pending_start = 1;
-        --step;
-        continue;
-      }
-      retried_plain = false;
-      if (!pc) {
-        launch_convert<T32, T>(d32, d64, n, s);
-        launch_axpy_inplace<T>(x, d64, n, s);
-        *launches += 2;
-      }
-      if (!dc) {
-        launch_convert<T32, T>(dt32, d64, n, s);
-        launch_axpy_inplace<T>(xt, d64, n, s);
-        *launches += 2;
-      }
+  } rs;
+
+  rbicg_result solve(const void* bv, const void* btv, void* xv, void* xtv) override {
+    if (!lo || fp64_only) {
+      return solve_fp64(reinterpret_cast<const T*>(bv), reinterpret_cast<const T*>(btv), reinterpret_cast<T*>(xv),
+                        reinterpret_cast<T*>(xtv), 0, 0);
     }
-    res.iters = total_iters;
-    res.cycles = cycles;
-    res.recycle_dim = rdim;
-    res.refine_steps = step;
-    res.relres = rr / (nb > 0 ? nb : 1.0);
-    res.relres_dual = rtr / (nbt > 0 ? nbt : 1.0);
+    int what = refine_begin_t(reinterpret_cast<const T*>(bv), reinterpret_cast<const T*>(btv),
+                              reinterpret_cast<T*>(xv), reinterpret_cast<T*>(xtv));
+    while (what != REF_DONE) {
+      if (what == REF_INNER) what = after_inner(lo->run_to_end());
+      else what = after_fp64(hi->run_to_end());
+    }
+    return rs.res;
+  }
+
+  int refine_begin_t(const T* b, const T* bt, T* x, T* xt) {
+    rs = RefState{};
+    rs.b = b; rs.bt = bt; rs.x = x; rs.xt = xt;
+    rs.nb = norm(b);
+    rs.nbt = norm(bt);
+    rs.status = RBICG_NOT_CONVERGED;
+    rs.inner_cap = prm.max_itn;
+    return advance();
+  }
+
+  // residual of the refined iterate; converged, out of steps, or the next inner solve
+  int advance() {
+    const int grid = std::max(1, std::min((int)((n + 255) / 256), num_sms() * 8));
+    k_residual<V, T><<<grid, 256, 0, s>>>(hi->op, rs.b, rs.x, r64, 0);
+    k_residual<V, T><<<grid, 256, 0, s>>>(hi->op, rs.bt, rs.xt, rt64, 1);
+    *launches += 2;
+    rs.rr = norm(r64);
+    rs.rtr = norm(rt64);
+    if (debug_on())
+      fprintf(stderr, "[rbicg] refine step %d relres %.3e dual %.3e\n", rs.step, rs.rr / (rs.nb > 0 ? rs.nb : 1.0),
+              rs.rtr / (rs.nbt > 0 ? rs.nbt : 1.0));
+    rs.pc = rs.rr <= prm.tol * (rs.nb > 0 ? rs.nb : 1.0) || (rs.nb == 0 && rs.rr == 0);
+    rs.dc = rs.nbt == 0.0 || rs.rtr <= prm.tol * rs.nbt;
+    if (rs.pc && rs.dc) { rs.status = RBICG_OK; return finish_refined(); }
+    if (rs.step >= prm.refine_max) return finish_refined();
+    launch_convert<T, T32>(r64, r32, n, s);
+    launch_convert<T, T32>(rt64, rt32, n, s);
+    RB_CUDA(cudaMemsetAsync(d32, 0, sizeof(T32) * n, s));
+    RB_CUDA(cudaMemsetAsync(dt32, 0, sizeof(T32) * n, s));
+    *launches += 2;
+    lo->begin(r32, rt32, d32, dt32, prm.inner_tol, rs.inner_cap, prm.seed + rs.step);
+    if (!lo->run.done) return REF_INNER;
+    return after_inner(lo->run_to_end());
+  }
+
+  // an inner solve ended (its step 7 applied): use its correction or retry / fall back
+  int after_inner(const typename Solver<V32, T32>::PairOut& o) {
+    rs.total_iters += o.iters;
+    rs.cycles += o.cycles;
+    rs.rdim = o.recycle_dim;
+    // a non-finite inner solve is treated like an unusable correction (retried as plain BiCG)
+    if (o.status < 0 && o.status != RBICG_ERR_NONFINITE) { rs.status = o.status; return finish_refined(); }
+    if (rs.first_inner < 0) {
+      rs.first_inner = o.iters;
+      rs.inner_cap = std::min(prm.max_itn, std::max(200, 4 * rs.first_inner + 100));
+    }
+    // A correction is used only if the inner solve reduced its own residual; otherwise the
+    // inner recycle space is dropped and the step is retried once as plain FP32 BiCG.
+    const bool usable = o.status != RBICG_ERR_NONFINITE &&
+                        (o.status == RBICG_OK || o.status == RBICG_RECYCLE_EMPTY ||
+                         (o.true_relres < 0.5 && (rs.dc || o.true_relres_dual < 0.5)));
+    if (debug_on())
+      fprintf(stderr, "[rbicg] inner step %d status %d iters %d relres %.3e/%.3e usable %d\n", rs.step, o.status,
+              o.iters, o.true_relres, o.true_relres_dual, (int)usable);
+    if (!usable) {
+      if (rs.retried_plain) {
+        // the FP32 recurrence does not converge on this problem even without a recycle space:
+        // this handle continues in FP64 RBiCG from the refined iterate
+        fp64_only = true;
+        hi->begin(rs.b, rs.bt, rs.x, rs.xt, prm.tol, prm.max_itn, prm.seed);
+        if (!hi->run.done) return REF_FP64;
+        return after_fp64(hi->run_to_end());
+      }
+      rs.retried_plain = true;
+      lo->kU = 0;
+      lo->pending_start = 1;
+      return advance();   // the same step again (the residual is unchanged)
+    }
+    rs.retried_plain = false;
+    if (!rs.pc) {
+      launch_convert<T32, T>(d32, d64, n, s);
+      launch_axpy_inplace<T>(rs.x, d64, n, s);
+      *launches += 2;
+    }
+    if (!rs.dc) {
+      launch_convert<T32, T>(dt32, d64, n, s);
+      launch_axpy_inplace<T>(rs.xt, d64, n, s);
+      *launches += 2;
+    }
+    ++rs.step;
+    return advance();
+  }
+
+  int after_fp64(const typename Solver<V, T>::PairOut& o) {
+    rbicg_result& res = rs.res;
+    res = rbicg_result{};
+    res.iters = rs.total_iters + o.iters; res.cycles = o.cycles; res.recycle_dim = o.recycle_dim;
+    res.refine_steps = rs.step;
+    res.relres = o.relres; res.relres_dual = o.relres_dual;
+    res.true_relres = o.true_relres; res.true_relres_dual = o.true_relres_dual;
+    res.status = o.status;
+    res.fallback = 2;
+    return REF_DONE;
+  }
+
+  int finish_refined() {
+    rbicg_result& res = rs.res;
+    res = rbicg_result{};
+    res.iters = rs.total_iters;
+    res.cycles = rs.cycles;
+    res.recycle_dim = rs.rdim;
+    res.refine_steps = rs.step;
+    res.relres = rs.rr / (rs.nb > 0 ? rs.nb : 1.0);
+    res.relres_dual = rs.rtr / (rs.nbt > 0 ? rs.nbt : 1.0);
     res.true_relres = res.relres;
     res.true_relres_dual = res.relres_dual;
-    res.status = status;
-    return res;
+    res.status = rs.status;
+    return REF_DONE;
+  }
+
+  // engine entry points: kinds 0..2 are the FP64 solvers, 3..5 the FP32 ones
+  static int kind_of_hi() { return traits<T>::cx ? (traits<V>::cx ? 2 : 1) : 0; }
+  static int kind_of_lo() { return traits<T>::cx ? (traits<V>::cx ? 5 : 4) : 3; }
+  int refine_begin(const void* b, const void* bt, void* x, void* xt, void** solver, int* kind) override {
+    int w;
+    if (!lo || fp64_only) {
+      rs = RefState{};
+      hi->begin(reinterpret_cast<const T*>(b), reinterpret_cast<const T*>(bt), reinterpret_cast<T*>(x),
+                reinterpret_cast<T*>(xt), prm.tol, prm.max_itn, prm.seed);
+      w = hi->run.done ? after_fp64(hi->run_to_end()) : REF_FP64;
+    } else {
+      w = refine_begin_t(reinterpret_cast<const T*>(b), reinterpret_cast<const T*>(bt), reinterpret_cast<T*>(x),
+                         reinterpret_cast<T*>(xt));
+    }
+    return route(w, solver, kind);
+  }
+  int refine_after(int kind, void** solver, int* kindout) override {
+    const int w = kind >= 3 ? after_inner(lo->end()) : after_fp64(hi->end());
+    return route(w, solver, kindout);
+  }
+  int route(int w, void** solver, int* kind) {
+    if (w == REF_INNER) { *solver = lo.get(); *kind = kind_of_lo(); return 1; }
+    if (w == REF_FP64) { *solver = hi.get(); *kind = kind_of_hi(); return 1; }
+    return 0;
+  }
+  rbicg_result refine_result() override { return rs.res; }
+  cudaStream_t swap_stream(cudaStream_t st) override {
+    const cudaStream_t old = s;
+    s = st;
+    hi->s = st;
+    if (lo) lo->s = st;
+    return old;
   }
 
   bool fp64_only = false;   // FP32_REFINED handle that fell back to FP64 (until rbicg_reset)
@@ -1109,6 +1249,8 @@ extern "C" void rbicg_default_params(rbicg_params* p) {
   p->restarts = 0;
   p->grid_blocks = 0;
   p->refresh = 1;
+  p->setup_blocks = 0;
+  p->graphs = 1;
 }
 
 static std::string check_params(const rbicg_params* p, int64_t n) {
@@ -1124,6 +1266,8 @@ static std::string check_params(const rbicg_params* p, int64_t n) {
   if (p->grid_blocks < 0 || p->grid_blocks > (1 << 20)) return "grid_blocks must be in 0..2^20";
   if (p->restarts < 0 || p->restarts > 1000) return "restarts must be in 0..1000";
   if (p->refresh != 0 && p->refresh != 1) return "refresh must be 0 or 1";
+  if (p->setup_blocks < 0 || p->setup_blocks > 8192) return "setup_blocks must be in 0..8192";
+  if (p->graphs != 0 && p->graphs != 1) return "graphs must be 0 or 1";
   if (p->precision == RBICG_FP32_REFINED && !(p->inner_tol > 0.0 && p->inner_tol < 1.0))
     return "inner_tol must be in (0, 1)";
   if (p->precision != RBICG_FP64 && p->precision != RBICG_FP32_REFINED) return "unknown precision";
@@ -1550,21 +1694,43 @@ extern "C" rbicg_status rbicg_op_svd(rbicg_dtype dtype, int k, const void* S_hos
 // sums and reduction order), whatever else is in flight.
 struct EngineReq {
   rbicg_handle h = nullptr;
-  int kind = -1;
-  void* solver = nullptr;
+  int kind = -1;             // 0..2 FP64 solvers, 3..5 FP32 (inner solves of FP32-refined requests)
+  void* solver = nullptr;    // the solver the engine steps
   cudaStream_t saved = nullptr;
+  int refine = 0;            // FP32-refined request: its refinement state machine picks the solvers
   int64_t tag = 0;
+};
+
+// A cycle's batched launches (todo iterations x 2 or 3 phases) captured as a CUDA graph and
+// replayed while the launch shape stays the same: the kernels read the requests' arguments from
+// the stride group's device BatchArgs, which is refreshed before every replay, so a graph depends
+// only on (kind, stride group, blocks, ld, kt, todo).
+struct EngineGraph {
+  int kind = -1, g = -1, blocks = 0, ld = 0, kt = 0, todo = 0;
+  cudaGraphExec_t exec = nullptr;
+  int64_t last_use = 0;
 };
 
 struct rbicg_engine_s {
   cudaStream_t s = nullptr;
   std::vector<EngineReq> active;
   std::vector<std::pair<int64_t, rbicg_result>> finished;
-  std::vector<std::pair<void*, void*>> bufs[3];   // per kind: (device BatchArgs, pinned staging)
+  std::vector<std::pair<void*, void*>> bufs[6];   // per kind: (device BatchArgs, pinned staging)
   std::string err;
   int64_t steps = 0;
+  // graph capture and replay (a private stream: the engine's may be the legacy default stream)
+  cudaStream_t gs = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<EngineGraph> graphs;
+  bool use_graphs = getenv("RBICG_NO_GRAPHS") == nullptr;
   ~rbicg_engine_s() {
     if (s) cudaStreamSynchronize(s);
+    if (gs) cudaStreamSynchronize(gs);
+    for (auto& gr : graphs)
+      if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (gs) cudaStreamDestroy(gs);
     for (auto& pool : bufs)
       for (auto& b : pool) {
         cudaFree(b.first);
@@ -1573,16 +1739,86 @@ struct rbicg_engine_s {
   }
 };
 
+// Launch one stride group's cycle: replay a cached graph of the same shape, capture a new one,
+// or (graphs off, or capture refused) launch the kernels one by one on the engine's stream.
+template <class V, class T>
+static void engine_launch_cycle(rbicg_engine e, int kind, int g, BatchArgs<V, T>* dba, int blocks, int ld, int kt,
+                                int todo) {
+  auto launch_all = [&](cudaStream_t st) {
+    for (int t = 0; t < todo; ++t) {
+      launch_phase1_batch<V, T>(dba, blocks, ld, st);
+      if (kt > 0) launch_phase2_batch<V, T>(dba, blocks, kt, st);
+      launch_phase3_batch<V, T>(dba, blocks, st);
+    }
+  };
+  if (!e->use_graphs || todo <= 0) { launch_all(e->s); return; }
+  if (!e->gs) {
+    RB_CUDA(cudaStreamCreateWithFlags(&e->gs, cudaStreamNonBlocking));
+    RB_CUDA(cudaEventCreateWithFlags(&e->ev0, cudaEventDisableTiming));
+    RB_CUDA(cudaEventCreateWithFlags(&e->ev1, cudaEventDisableTiming));
+  }
+  EngineGraph* gr = nullptr;
+  for (auto& x : e->graphs)
+    if (x.kind == kind && x.g == g && x.blocks == blocks && x.ld == ld && x.kt == kt && x.todo == todo) gr = &x;
+  if (!gr) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(e->gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      e->use_graphs = false;
+      launch_all(e->s);
+      return;
+    }
+    launch_all(e->gs);
+    const cudaError_t ec = cudaStreamEndCapture(e->gs, &graph);
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = ec == cudaSuccess ? cudaGraphInstantiate(&exec, graph, 0) : ec;
+    if (graph) cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      cudaGetLastError();
+      e->use_graphs = false;
+      launch_all(e->s);
+      return;
+    }
+    if (e->graphs.size() >= 16) {   // keep the 16 most recently used shapes
+      auto old = std::min_element(e->graphs.begin(), e->graphs.end(),
+                                  [](const EngineGraph& a, const EngineGraph& b) { return a.last_use < b.last_use; });
+      cudaGraphExecDestroy(old->exec);
+      e->graphs.erase(old);
+    }
+    EngineGraph ng;
+    ng.kind = kind; ng.g = g; ng.blocks = blocks; ng.ld = ld; ng.kt = kt; ng.todo = todo; ng.exec = exec;
+    e->graphs.push_back(ng);
+    gr = &e->graphs.back();
+  }
+  gr->last_use = e->steps;
+  RB_CUDA(cudaEventRecord(e->ev0, e->s));
+  RB_CUDA(cudaStreamWaitEvent(e->gs, e->ev0, 0));
+  RB_CUDA(cudaGraphLaunch(gr->exec, e->gs));
+  RB_CUDA(cudaEventRecord(e->ev1, e->gs));
+  RB_CUDA(cudaStreamWaitEvent(e->s, e->ev1, 0));
+}
+
 template <class V, class T>
 static Solver<V, T>* as_solver(const EngineReq& q) { return static_cast<Solver<V, T>*>(q.solver); }
 
+// A request whose solver finished its cycles: an FP64 request ends (step 7, result); an
+// FP32-refined one continues its refinement and may go on with another solver (returns true:
+// keep it in flight).
 template <class V, class T>
-static void engine_finish(rbicg_engine e, EngineReq& q) {
+static bool engine_finish(rbicg_engine e, EngineReq& q) {
+  if (q.refine) {
+    if (q.h->impl->refine_after(q.kind, &q.solver, &q.kind)) return true;
+    q.h->impl->swap_stream(q.saved);
+    q.h->err.clear();
+    e->finished.push_back({q.tag, q.h->impl->refine_result()});
+    return false;
+  }
   Solver<V, T>* sv = as_solver<V, T>(q);
   const rbicg_result r = to_result(sv->end());
   sv->s = q.saved;
   q.h->err.clear();
   e->finished.push_back({q.tag, r});
+  return false;
 }
 
 // one cycle for every in-flight request of kind (V, T): one batched launch sequence per
@@ -1632,11 +1868,7 @@ static void engine_step_kind(rbicg_engine e, int kind) {
     hb->nreq = nreq;
     const int ld = kt == 0 ? 0 : strides[g];
     RB_CUDA(cudaMemcpyAsync(dba, hb, sizeof(BatchArgs<V, T>), cudaMemcpyHostToDevice, e->s));
-    for (int t = 0; t < todo; ++t) {
-      launch_phase1_batch<V, T>(dba, blocks, ld, e->s);
-      if (kt > 0) launch_phase2_batch<V, T>(dba, blocks, kt, e->s);
-      launch_phase3_batch<V, T>(dba, blocks, e->s);
-    }
+    engine_launch_cycle<V, T>(e, kind, (int)g, dba, blocks, ld, kt, todo);
     launched += (kt > 0 ? 3 : 2) * todo;
   }
   as_solver<V, T>(e->active[idx[0]])->count(launched);
@@ -1650,8 +1882,11 @@ static void engine_step_kind(rbicg_engine e, int kind) {
   std::vector<EngineReq> keep;
   for (size_t i = 0; i < e->active.size(); ++i) {
     EngineReq& q = e->active[i];
-    if (q.kind == kind && as_solver<V, T>(q)->run.done) engine_finish<V, T>(e, q);
-    else keep.push_back(q);
+    if (q.kind == kind && as_solver<V, T>(q)->run.done) {
+      if (engine_finish<V, T>(e, q)) keep.push_back(q);
+    } else {
+      keep.push_back(q);
+    }
   }
   e->active.swap(keep);
 }
@@ -1687,10 +1922,16 @@ extern "C" rbicg_status rbicg_engine_submit(rbicg_engine e, rbicg_handle h, cons
     q.tag = tag;
     q.solver = h->impl->batch_solver(&q.kind);
     if (!q.solver) {
-      // FP32-refined requests run their refinement loop whole, on the engine's stream order
-      RB_CUDA(cudaStreamSynchronize(e->s));
-      const rbicg_result r = h->impl->solve(b, bt, x, xt);
-      e->finished.push_back({tag, r});
+      // FP32-refined request: its refinement steps run on the engine's stream; the engine steps
+      // its inner FP32 solves (and a FP64 fallback solve) one cycle at a time with the others
+      q.refine = 1;
+      q.saved = h->impl->swap_stream(e->s);
+      if (!h->impl->refine_begin(b, bt, x, xt, &q.solver, &q.kind)) {
+        h->impl->swap_stream(q.saved);
+        e->finished.push_back({tag, h->impl->refine_result()});
+        return RBICG_OK;
+      }
+      e->active.push_back(q);
       return RBICG_OK;
     }
     const rbicg_params& p = h->prm;
@@ -1728,6 +1969,9 @@ extern "C" rbicg_status rbicg_engine_step(rbicg_engine e, int* in_flight) {
     engine_step_kind<double, double>(e, 0);
     engine_step_kind<double, cplx<double>>(e, 1);
     engine_step_kind<cplx<double>, cplx<double>>(e, 2);
+    engine_step_kind<float, float>(e, 3);
+    engine_step_kind<float, cplx<float>>(e, 4);
+    engine_step_kind<cplx<float>, cplx<float>>(e, 5);
   } catch (const Err& x) {
     e->err = x.msg;
     return fail(nullptr, x.st, x.msg);
@@ -1911,6 +2155,87 @@ extern "C" rbicg_status rbicg_autotune(const rbicg_params* params, rbicg_dtype d
     g_tune[key] = {best, best_us};
   }
   *grid_blocks = best;
+  if (us_per_iter) *us_per_iter = best_us;
+  return RBICG_OK;
+}
+
+extern "C" rbicg_status rbicg_autotune_params(const rbicg_params* params, rbicg_dtype dtype, const rbicg_csr* A,
+                                              int trial_iters, rbicg_params* out, double* us_per_iter) {
+  if (!params || !A || !out) return fail(nullptr, RBICG_ERR_ARG, "null argument");
+  if (dtype != RBICG_R64 && dtype != RBICG_C128) return fail(nullptr, RBICG_ERR_ARG, "unknown dtype");
+  const std::string m = check_params(params, A->n);
+  if (!m.empty()) return fail(nullptr, RBICG_ERR_ARG, m);
+  int g = 0;
+  double us = 0.0;
+  rbicg_status st = rbicg_autotune(params, dtype, A, std::max(4, trial_iters), &g, &us);
+  if (st < 0) return st;
+  rbicg_params best = *params;
+  best.grid_blocks = g;
+  const int64_t n = A->n;
+  const size_t w = dtype == RBICG_C128 ? sizeof(zd) : sizeof(double);
+  cudaStream_t s = nullptr;
+  void* buf = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(nullptr, RBICG_ERR_CUDA, "autotune stream");
+  if (cudaMalloc(&buf, 4 * w * (size_t)n) != cudaSuccess) {
+    cudaStreamDestroy(s);
+    return fail(nullptr, RBICG_ERR_OOM, "autotune vectors");
+  }
+  char* b = static_cast<char*>(buf);
+  char* bt = b + w * n;
+  char* x = bt + w * n;
+  char* xt = x + w * n;
+  if (dtype == RBICG_C128) {
+    launch_philox<cplx<double>>(reinterpret_cast<zd*>(b), n, 1, s);
+    launch_philox<cplx<double>>(reinterpret_cast<zd*>(bt), n, 2, s);
+  } else {
+    launch_philox<double>(reinterpret_cast<double*>(b), n, 1, s);
+    launch_philox<double>(reinterpret_cast<double*>(bt), n, 2, s);
+  }
+  const int sms = num_sms();
+  double best_us = 1e300;
+  rbicg_status err = RBICG_OK;
+  for (int f : {2, 1, 4}) {
+    for (int gr : {1, 0}) {
+      rbicg_params q = best;
+      q.setup_blocks = f * sms;
+      q.graphs = gr;
+      q.recycle = 1;
+      q.refresh = 1;
+      q.guard = 0.0;
+      q.tol = 1e-300;            // never met: exactly three cycles per solve
+      q.max_itn = 3 * q.s;
+      q.precision = RBICG_FP64;
+      rbicg_handle h = nullptr;
+      st = rbicg_create(&q, n, dtype, s, &h);
+      if (st != RBICG_OK) { err = st; break; }
+      double t = 0.0;
+      // the first solve builds A^H and a recycle space; the second runs recycled iterations and
+      // their refreshes, and is timed
+      for (int rep = 0; rep < 2 && st >= 0; ++rep) {
+        cudaMemsetAsync(x, 0, 2 * w * (size_t)n, s);
+        cudaStreamSynchronize(s);
+        const auto t0 = std::chrono::steady_clock::now();
+        rbicg_result r{};
+        st = rbicg_solve_pair(h, A, b, bt, x, xt, &r);
+        cudaStreamSynchronize(s);
+        t = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count() /
+            std::max(1, r.iters);
+      }
+      rbicg_destroy(h);
+      if (st < 0) { err = st; break; }
+      if (t < best_us) {
+        best_us = t;
+        best.setup_blocks = q.setup_blocks;
+        best.graphs = gr;
+      }
+    }
+    if (err < 0) break;
+  }
+  cudaFree(buf);
+  cudaStreamDestroy(s);
+  if (err < 0) return err;
+  *out = best;
   if (us_per_iter) *us_per_iter = best_us;
   return RBICG_OK;
 }

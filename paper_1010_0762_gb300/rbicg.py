@@ -30,7 +30,8 @@ class Params(C.Structure):
                 ("svd_tol", C.c_double), ("inner_tol", C.c_double), ("refine_max", C.c_int),
                 ("precision", C.c_int), ("seed", C.c_uint64), ("setup_fp32", C.c_int),
                 ("recycle", C.c_int), ("inner_svd_tol", C.c_double), ("guard", C.c_double),
-                ("restarts", C.c_int), ("grid_blocks", C.c_int), ("refresh", C.c_int)]
+                ("restarts", C.c_int), ("grid_blocks", C.c_int), ("refresh", C.c_int),
+                ("setup_blocks", C.c_int), ("graphs", C.c_int)]
 
 
 class CSRStruct(C.Structure):
@@ -94,6 +95,8 @@ def _load():
         "rbicg_op_eig_select": (ci, [ci, ci, vp, vp, ci, vp, vp, vp, C.POINTER(ci), vp]),
         "rbicg_op_svd": (ci, [ci, ci, vp, vp, vp, vp, vp]),
         "rbicg_autotune": (ci, [C.POINTER(Params), ci, C.POINTER(CSRStruct), ci, C.POINTER(ci), C.POINTER(cd)]),
+        "rbicg_autotune_params": (ci, [C.POINTER(Params), ci, C.POINTER(CSRStruct), ci, C.POINTER(Params),
+                                       C.POINTER(cd)]),
         "rbicg_engine_create": (ci, [vp, C.POINTER(vp)]),
         "rbicg_engine_submit": (ci, [vp, vp, C.POINTER(CSRStruct), vp, vp, vp, vp, i64]),
         "rbicg_engine_step": (ci, [vp, C.POINTER(ci)]),
@@ -258,6 +261,20 @@ def autotune(op, dtype=None, trial_iters=60, **params):
     us = C.c_double(0.0)
     _check(lib.rbicg_autotune(C.byref(p), dtype, C.byref(op.struct), int(trial_iters), C.byref(g), C.byref(us)))
     return g.value, us.value
+
+
+def autotune_params(op, dtype=None, trial_iters=60, **params):
+    """Launch knobs for operator `op` by timed trials (rbicg_autotune_params): returns a dict with
+    grid_blocks, setup_blocks and graphs (pass them to Solver) and the time per recycled iteration."""
+    p = default_params(**params)
+    if dtype is None:
+        dtype = C128 if op.val.dtype == torch.complex128 else R64
+    out = Params()
+    us = C.c_double(0.0)
+    _check(lib.rbicg_autotune_params(C.byref(p), dtype, C.byref(op.struct), int(trial_iters), C.byref(out),
+                                     C.byref(us)))
+    return {"grid_blocks": out.grid_blocks, "setup_blocks": out.setup_blocks, "graphs": out.graphs,
+            "us_per_iter": us.value}
 
 
 class Engine:

@@ -429,3 +429,21 @@ def test_restart_after_breakdown_matches_oracle(R):
     assert res["status"] in (R.OK, R.BREAKDOWN_RHO, R.BREAKDOWN_PQ)
     rel = np.linalg.norm(b - A.to_scipy() @ x) / np.linalg.norm(b)
     assert np.isfinite(rel) and rel < 1e-1
+
+
+def test_autotune_params_picks_three_knobs(R):
+    # iteration grid, refresh Gram grid and graphs by timed trials; a solve with the picked knobs
+    # gives the result of the defaults (the knobs change launch shapes, not the method)
+    A = I.convdiff(96, [10.0, 10.0])
+    n = A.n
+    op = R.Operator.from_csr(A)
+    t = R.autotune_params(op, trial_iters=40, k=8, s=20, setup_fp32=0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert t["setup_blocks"] in {f * sms for f in (1, 2, 4)} and t["graphs"] in (0, 1)
+    assert t["grid_blocks"] > 0 and t["us_per_iter"] > 0
+    b, bt = I.normal_vector(n, 1), I.normal_vector(n, 2)
+    S = R.Solver(n, k=8, s=20, tol=1e-9, setup_fp32=0, grid_blocks=t["grid_blocks"],
+                 setup_blocks=t["setup_blocks"], graphs=t["graphs"])
+    res, x, xt = _solve_gpu(R, S, A, b, bt)
+    assert res["status"] in (R.OK, R.RECYCLE_EMPTY)
+    assert np.linalg.norm(b - A.to_scipy() @ x) / np.linalg.norm(b) < 2e-9

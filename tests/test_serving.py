@@ -139,3 +139,37 @@ def test_served_results_equal_solo_solves():
                                torch.as_tensor(bt, device="cuda"), x, xt)
             assert res["iters"] == rq.result["iters"], (sp.fid, rq.rid)
             assert torch.equal(x, rq.x), (sp.fid, rq.rid)
+
+
+@pytest.mark.gpu
+def test_served_fp32_refined_requests_overlap_and_equal_solo_solves():
+    # FP32-refined requests step through the engine (their inner FP32 solves are batched with the
+    # other requests' cycles, the FP64 refinement steps run between engine steps): each result
+    # equals a solo solve on a handle of the same precision, bit for bit
+    import torch
+
+    from paper_1010_0762_gb300 import rbicg as R
+
+    torch.cuda.set_device(0)
+    specs = [SV.FamilySpec(0, 20, (10.0, 10.0), 6, 0.01, 21), SV.FamilySpec(1, 24, (3.0, 1.0), 8, 0.01, 22),
+             SV.FamilySpec(2, 16, (5.0, 2.0), 8, 0.01, 23)]
+    be = SV.GpuBackend(s=20, tol=1e-10)
+    srv = SV.Server(specs, be, hbm_budget=8 * 2**30, s=20, max_in_flight=8, keep_x=True)
+    reqs = SV.poisson_arrivals(12, rate=400.0, families=specs, seed=7, p_fp32=0.5)
+    assert {r.precision for r in reqs} == {"fp64", "fp32_refined"}
+    st = srv.run(reqs)
+    assert st["all_converged"], [r.result for r in reqs]
+    assert any(r.result["refine_steps"] >= 1 and r.result["fallback"] == 0 for r in reqs
+               if r.precision == "fp32_refined")
+    for sp in specs:
+        fam = SV.Family(sp)
+        hs = {p: R.Solver(sp.N * sp.N, k=sp.k, s=20, tol=1e-10, precision=p) for p in ("fp64", "fp32_refined")}
+        for rq in [r for r in reqs if r.fid == sp.fid]:
+            A, b, bt = fam.next_problem()
+            x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+            xt = torch.zeros_like(x)
+            res = hs[rq.precision].solve_pair(R.Operator.from_csr(A), torch.as_tensor(b, device="cuda"),
+                                              torch.as_tensor(bt, device="cuda"), x, xt)
+            assert res["iters"] == rq.result["iters"], (sp.fid, rq.rid, rq.precision)
+            assert res["refine_steps"] == rq.result["refine_steps"]
+            assert torch.equal(x, rq.x), (sp.fid, rq.rid, rq.precision)
