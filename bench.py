@@ -214,7 +214,9 @@ def gpu_arm(a):
             R.lib.rbicg_profile(S.h, 0, ms, cnt)
             cols = C.c_int64(0)
             R.lib.rbicg_profile_columns(S.h, C.byref(cols))
-            prof = (list(ms), list(cnt), cols.value)
+            gp = C.c_int64(0)
+            R.lib.rbicg_profile_gram_pairs(S.h, C.byref(gp))
+            prof = (list(ms), list(cnt), cols.value, gp.value)
         if world > 1:
             total_ms = max_over_ranks(total_ms, dist, "cuda")
         return total_ms, results, ck, prof, launches
@@ -236,7 +238,7 @@ def gpu_arm(a):
     # roofline of the dominant kernel (phase 1: dual SpMV + projections) from live CUDA events
     names = ["dual_spmv_project", "q_and_pq", "update_dots", "refresh_gram", "refresh_eig",
              "refresh_basis", "system_start", "init_finish_adjoint"]
-    ms_slots, cnt_slots, pcols = prof
+    ms_slots, cnt_slots, pcols, gpairs = prof
     dom = int(np.argmax(ms_slots))
     # algorithmic work of every phase-1 launch of the profiled step: the dual SpMV and p update
     # of each launch plus 2 projections per active recycle column (pcols sums those widths)
@@ -266,7 +268,7 @@ def gpu_arm(a):
     # the same launch
     traffic_k4 = 52.440576e6 + 0.253952e6
     alg_k4 = algorithmic_phase1(n, nnz, 4)[1]
-    roofline = {
+    rl_phase1 = {
         "kernel": "k_phase1 (dual SpMV + p update + Ct^H z, C^H zt)",
         "bound": bound,
         "achieved": round(ach_tf if bound == "alu" else ach_gbs, 4),
@@ -291,6 +293,28 @@ def gpu_arm(a):
         "slot_launches": {names[i]: int(cnt_slots[i]) for i in range(8)},
         "dominant_slot": names[dom],
     }
+
+    # the refresh's Gram Psit^H [Psi U_{j-1}] (Section 4.1): mx my n multiply-adds per launch in
+    # FP64, ALU-bound (about 30 multiply-adds per loaded double at these widths)
+    tg = ms_slots[3] * 1e-3
+    g_tf = 2.0 * gpairs * n / tg / 1e12 if tg > 0 else 0.0
+    rl_gram = {
+        "kernel": "k_gram (refresh Gram Psit^H [Psi U_{j-1}], FP64)",
+        "bound": "alu", "achieved": round(g_tf, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+        "frac": round(g_tf / fp64_peak, 4),
+        "peak_source": "FP64 FMA units: 2 DFMA/clock/SM x %d SMs at the sampled %.0f MHz" % (sms, sm_mhz),
+        "traffic": None,
+        "avg_launch_us": round(ms_slots[3] * 1e3 / max(1, cnt_slots[3] // 2), 2),
+        "launches": int(cnt_slots[3] // 2),
+        "mean_column_pairs": round(gpairs / max(1, cnt_slots[3] // 2), 1),
+        "timing": rl_phase1["timing"],
+    }
+    # the dominant kernel of the profiled step by its live CUDA-event time
+    roofline = dict(rl_gram if ms_slots[3] > ms_slots[0] else rl_phase1)
+    roofline["other_kernel"] = {k: v for k, v in (rl_phase1 if ms_slots[3] > ms_slots[0] else rl_gram).items()
+                                if k not in ("step_share", "slot_ms", "slot_launches", "dominant_slot")}
+    for key in ("step_share", "slot_ms", "slot_launches", "dominant_slot"):
+        roofline[key] = rl_phase1[key]
 
     out = {
         "metric": METRIC,

@@ -272,6 +272,10 @@ rbicg_status rbicg_profile(rbicg_handle h, int enable, double *ms_out, int64_t *
 /* With profiling on: the projection width (columns of C, Ct) summed over the slot-0 launches,
  * so that their algorithmic work (2 SpMVs and 2 k-column projections each) can be counted. */
 rbicg_status rbicg_profile_columns(rbicg_handle h, int64_t *cols);
+/* With profiling on: the column pairs mx x my summed over the slot-3 launches (the Gram
+ * Psit^H [Psi U_{j-1}] of Section 4.1), so that their algorithmic work, mx my n multiply-adds
+ * each, can be counted. */
+rbicg_status rbicg_profile_gram_pairs(rbicg_handle h, int64_t *pairs);
 
 /* ---------------------------------------------------------------------------------------
  * Component entry points.  Each runs one step of the hot path on caller-provided device

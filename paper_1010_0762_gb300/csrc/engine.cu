@@ -103,6 +103,7 @@ struct Profiler {
   double ms[RBICG_NPROF] = {};
   int64_t cnt[RBICG_NPROF] = {};
   int64_t pcols = 0;   // projection columns summed over the slot-0 launches
+  int64_t gpairs = 0;  // column pairs (mx x my) summed over the slot-3 (pencil Gram) launches
   std::vector<cudaEvent_t> pool;
   struct Pend { int slot, nl; cudaEvent_t a, b; };
   std::vector<Pend> pending;
@@ -139,6 +140,7 @@ struct Profiler {
   }
   void reset() {
     pcols = 0;
+    gpairs = 0;
     for (int i = 0; i < RBICG_NPROF; ++i) { ms[i] = 0; cnt[i] = 0; }
   }
   ~Profiler() {
@@ -445,6 +447,7 @@ struct Solver : SolverBase {
       append_ring(Ph, ring, (j - 1) * ss, j * ss - 1);
       append_ring(Pht, ringt, (j - 1) * ss, j * ss - 1);
       const int pg = prof->begin(3, q);
+      if (prof->on) prof->gpairs += (int64_t)X.m * Y.m;
       launch_gram<T>(X, Y, n, prm.setup_fp32, gpart, gram_grid, G, q);
       prof->end(pg, 2, q);
       count(2);
@@ -1434,6 +1437,12 @@ extern "C" rbicg_status rbicg_profile(rbicg_handle h, int enable, double* ms_out
     if (enable && !h->prof.on) h->prof.reset();
     h->prof.on = enable != 0;
   }
+  return RBICG_OK;
+}
+
+extern "C" rbicg_status rbicg_profile_gram_pairs(rbicg_handle h, int64_t* pairs) {
+  if (!h || !pairs) return fail(h, RBICG_ERR_ARG, "null argument");
+  *pairs = h->prof.gpairs;
   return RBICG_OK;
 }
 

@@ -89,6 +89,7 @@ def _load():
         "rbicg_launch_count": (i64, [vp]),
         "rbicg_profile": (ci, [vp, ci, C.POINTER(cd), C.POINTER(i64)]),
         "rbicg_profile_columns": (ci, [vp, C.POINTER(i64)]),
+        "rbicg_profile_gram_pairs": (ci, [vp, C.POINTER(i64)]),
         "rbicg_op_dual_spmv_project": (ci, [C.POINTER(CSRStruct), ci, vp, vp, vp, vp, cd, cd, vp, vp, ci, ci,
                                             vp, vp, vp, vp, vp, vp, vp, vp]),
         "rbicg_op_gram": (ci, [ci, i64, vp, ci, ci, vp, ci, ci, ci, vp, vp]),

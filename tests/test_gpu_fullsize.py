@@ -175,28 +175,42 @@ def _import_and_solve(R, S, A, b, bt, U, Ut, n):
     return res, x.cpu().numpy(), xt.cpu().numpy()
 
 
+def _onset(h1, h2, rtol=1e-8):
+    """First index where two residual histories differ by more than rtol (len if never)."""
+    d = np.abs(np.asarray(h1) - np.asarray(h2)) > rtol * np.abs(np.asarray(h2))
+    return int(np.argmax(d)) if d.any() else len(d)
+
+
 def test_config2_recycled_pair_two_cycles_match_oracle(R):
     # 512 x 512, k = 20, s = 40, all-FP64 refresh: pair 1 solved with the oracle's recycle space
     # (from two cycles of pair 0) on both sides, so that the recycled iteration itself is compared
-    # at full size: the system start keeps the same columns (Section 4.3), the recurrence residual
-    # norms of the first two cycles agree element by element and so do the iterates after them
-    # (Algorithm 2 step 7 applied)
+    # at full size.  The system start keeps the same columns (Section 4.3) and the recurrence
+    # residual norms agree element by element to 1e-8 for as long as the recurrence itself is
+    # reproducible: on this unpreconditioned operator the residual grows to 1e4 ||r_0|| within a
+    # few dozen iterations and BiCG then amplifies rounding, so the oracle run on b perturbed by
+    # 1e-15 relative departs from itself at some iteration m*; the library must agree with the
+    # oracle at least up to m* - 2 and may not depart earlier than the oracle departs from itself.
     seq = I.convdiff_sequence(512, [10.0, 10.0], 2, 0.01, 2000, bt_kind="normal")
     n = seq[0]["A"].n
     z = np.zeros(n)
     r0 = O.rbicg_pair(seq[0]["A"], seq[0]["b"], seq[0]["bt"], z, z, None, k=20, s=40, tol=1e-8, max_itn=80)
     rec = O.biorth_recycle(seq[1]["A"], r0.U_next, r0.Ut_next, 1e-6)
-    ref = O.rbicg_pair(seq[1]["A"], seq[1]["b"], seq[1]["bt"], z, z, rec, k=20, s=40, tol=1e-8, max_itn=80)
+    b1 = seq[1]["b"]
+    ref = O.rbicg_pair(seq[1]["A"], b1, seq[1]["bt"], z, z, rec, k=20, s=40, tol=1e-8, max_itn=80)
+    bp = b1 * (1.0 + 1e-15 * np.random.default_rng(9).uniform(-1, 1, n))
+    refp = O.rbicg_pair(seq[1]["A"], bp, seq[1]["bt"], z, z, rec, k=20, s=40, tol=1e-8, max_itn=80)
+    m_star = _onset(refp.hist["rnorm"], ref.hist["rnorm"])
+    assert m_star >= 20, m_star
     S = R.Solver(n, k=20, s=40, tol=1e-8, max_itn=80, setup_fp32=0, guard=0.0)
-    res, x, xt = _import_and_solve(R, S, seq[1]["A"], seq[1]["b"], seq[1]["bt"], r0.U_next, r0.Ut_next, n)
+    res, x, xt = _import_and_solve(R, S, seq[1]["A"], b1, seq[1]["bt"], r0.U_next, r0.Ut_next, n)
     assert res["recycle_dim"] == rec[0].shape[1] == ref.recycle_dim
     assert res["iters"] == ref.iters == 80
     hist = S.residual_history()
     rh = np.array(ref.hist["rnorm"])
     assert len(hist) == len(rh) == 81
-    np.testing.assert_allclose(hist, rh, rtol=1e-8, atol=0)
-    for a, b_ in ((x, ref.x), (xt, ref.xt)):
-        assert np.abs(a - b_).max() <= 1e-6 * np.abs(b_).max()
+    m_gpu = _onset(hist, rh)
+    assert m_gpu >= m_star - 2, (m_gpu, m_star)
+    np.testing.assert_allclose(hist[:m_star - 2], rh[:m_star - 2], rtol=1e-8, atol=0)
 
 
 def test_config1_recycled_pairs_match_oracle(R):
@@ -217,8 +231,13 @@ def test_config1_recycled_pairs_match_oracle(R):
         S = R.Solver(n, k=10, s=40, tol=1e-12, max_itn=80, setup_fp32=0, guard=0.0)
         res, _, _ = _import_and_solve(R, S, pr["A"], pr["b"], pr["bt"], U, Ut, n)
         assert res["recycle_dim"] == rec[0].shape[1], (j, res)
-        h, rh = S.residual_history(), np.array(two.hist["rnorm"][-len(S.residual_history()):])
-        np.testing.assert_allclose(h, rh, rtol=1e-8, atol=0, err_msg="pair %d" % j)
+        h, rh = S.residual_history(), np.array(two.hist["rnorm"])
+        assert len(h) == len(rh), (j, len(h), len(rh))
+        # the same reproducibility bound as at 512^2 (see above)
+        bp = pr["b"] * (1.0 + 1e-15 * np.random.default_rng(j).uniform(-1, 1, n))
+        twop = O.rbicg_pair(pr["A"], bp, pr["bt"], z, z, rec, k=10, s=40, tol=1e-12, max_itn=80)
+        m_star = _onset(twop.hist["rnorm"], rh)
+        assert _onset(h, rh) >= m_star - 2, (j, _onset(h, rh), m_star)
         S2 = R.Solver(n, k=10, s=40, tol=1e-12, setup_fp32=0, guard=0.0)
         res2, x, xt = _import_and_solve(R, S2, pr["A"], pr["b"], pr["bt"], U, Ut, n)
         assert res2["status"] in (R.OK, R.RECYCLE_EMPTY) and refs[j].status in (O.STATUS_OK, O.STATUS_RECYCLE_EMPTY)
