@@ -139,11 +139,13 @@ def measure_dgemm_tflops(torch):
     return 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
 
 
-def run_sequence(R, torch, S, ops, bs, bts, xs, xts, results=None):
+def run_sequence(R, torch, S, ops, bs, bts, xs, xts, results=None, refresh_every=1):
     S.reset()
     for j in range(len(ops)):
         xs[j].zero_()
         xts[j].zero_()
+        if refresh_every > 1:   # Section 6.2: a new recycle space only for every refresh_every-th pair
+            S.set_refresh(1 if j % refresh_every == 0 else 0)
         r = S.solve_pair(ops[j], bs[j], bts[j], xs[j], xts[j])
         if results is not None:
             results.append(r)
@@ -179,9 +181,9 @@ def gpu_arm(a):
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
 
-    def timed(S, steps, warmup, profile=False):
+    def timed(S, steps, warmup, profile=False, refresh_every=1):
         for _ in range(warmup):
-            run_sequence(R, torch, S, ops, bs, bts, xs, xts)
+            run_sequence(R, torch, S, ops, bs, bts, xs, xts, refresh_every=refresh_every)
         results = []
         clocks = Clocks()
         if world > 1:
@@ -194,7 +196,7 @@ def gpu_arm(a):
             flush_l2(torch, flush)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            run_sequence(R, torch, S, ops, bs, bts, xs, xts, results)
+            run_sequence(R, torch, S, ops, bs, bts, xs, xts, results, refresh_every=refresh_every)
             e1.record(stream)
             torch.cuda.synchronize()
             total_ms += e0.elapsed_time(e1)
@@ -361,6 +363,16 @@ def gpu_arm(a):
                              "iters_per_pair": [r["iters"] for r in resf[:a.pairs]],
                              "guard_fallback_per_pair": [r["fallback"] for r in resf[:a.pairs]],
                              "all_converged": all(r["status"] in (R.OK, R.RECYCLE_EMPTY) for r in resf)}
+        # --- the same FP64 form with a new recycle space only for every fifth pair (Section 6.2) ---
+        Sr = R.Solver(n, k=a.k, s=a.s, tol=a.tol, grid_blocks=a.grid_blocks, setup_fp32=0)
+        msr, resr, _, _, _ = timed(Sr, x_steps, 1, refresh_every=5)
+        out["refresh_every_5th_pair"] = {
+            "form": "plain FP64 RBiCG (setup_fp32=0), recycle space recomputed for pairs 0, 5, 10, 15 only",
+            "value": round(world * a.pairs * x_steps / (msr * 1e-3), 4), "unit": "solves/s",
+            "ms_per_step": round(msr / x_steps, 3), "steps": x_steps,
+            "iters_per_pair": [r["iters"] for r in resr[:a.pairs]],
+            "guard_fallback_per_pair": [r["fallback"] for r in resr[:a.pairs]],
+            "all_converged": all(r["status"] in (R.OK, R.RECYCLE_EMPTY) for r in resr)}
         out["chosen"] = {"form": "fp32_refined (FP32 inner RBiCG, FP64 residual refinement)",
                          "value": round(world * a.pairs * x_steps / (ms32 * 1e-3), 4), "unit": "solves/s",
                          "ms_per_step": round(ms32 / x_steps, 3), "steps": x_steps,

@@ -579,7 +579,7 @@ def _blockmat(rows, dt):
 # ----------------------------------------------------------------------------------------
 
 def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, seed=0,
-                   x_1=None, xt_1=None, recycle=True, on_pair=None, guard=0.0, restarts=0):
+                   x_1=None, xt_1=None, recycle=True, on_pair=None, guard=0.0, restarts=0, refresh_every=1):
     """Solve a sequence of dual pairs [{A, b, bt}, ...], carrying the recycle space.
 
     recycle=False gives plain BiCG on every pair (RBiCG with an empty recycle space).
@@ -592,6 +592,9 @@ def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, 
     restarts > 0 reproduces the library's restart after a breakdown (also not in the paper): a
     pair that ends in a BiCG breakdown (rho or (pt, q) below the relative threshold) continues
     from its iterate as plain BiCG, at most `restarts` times.
+    refresh_every > 1 (Section 6.2: the recycle space may be recomputed only for some systems of
+    a sequence): pair j computes a new recycle space only when j % refresh_every == 0; the other
+    pairs use the space they were given and hand it on unchanged.
     Returns a list of PairResult (iters counts every leg; hist["fallback"] is True after a
     guard fallback or a restart).
     """
@@ -605,6 +608,7 @@ def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, 
         x0 = np.zeros(n, dtype=b.dtype) if x_1 is None else x_1[j]
         xt0 = np.zeros(n, dtype=bt.dtype) if xt_1 is None else xt_1[j]
         rec = None
+        ref_j = recycle and j % refresh_every == 0
         if recycle and Uc is not None and Uc.shape[1] > 0:
             rec = biorth_recycle(A, Uc, Utc, svd_tol)
         limit = max_itn
@@ -613,14 +617,14 @@ def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, 
             # runs to the first multiple of s at or above guard x last_plain
             limit = min(max_itn, -(-int(guard * last_plain) // s) * s)
         res = rbicg_pair(A, b, bt, x0, xt0, recycle=rec, k=k, s=s, tol=tol, max_itn=limit,
-                         svd_tol=svd_tol, seed=seed + j, refresh=recycle)
+                         svd_tol=svd_tol, seed=seed + j, refresh=ref_j)
         res.hist["fallback"] = False
         res.hist["guard_limit"] = limit if limit < max_itn else None
         if limit < max_itn and res.status != STATUS_OK:
             first = res
             res = rbicg_pair(A, b, bt, first.x, first.xt, recycle=None, k=k, s=s, tol=tol,
                              max_itn=max_itn - first.iters, svd_tol=svd_tol, seed=seed + j,
-                             refresh=recycle)
+                             refresh=ref_j)
             res.iters += first.iters
             res.hist["fallback"] = True
             res.hist["guard_limit"] = limit
@@ -630,7 +634,7 @@ def rbicg_sequence(problems, k=10, s=40, tol=1e-8, max_itn=20000, svd_tol=1e-6, 
             used += 1
             prev = res
             res = rbicg_pair(A, b, bt, prev.x, prev.xt, recycle=None, k=k, s=s, tol=tol,
-                             max_itn=max_itn - prev.iters, svd_tol=svd_tol, seed=seed + j, refresh=recycle)
+                             max_itn=max_itn - prev.iters, svd_tol=svd_tol, seed=seed + j, refresh=ref_j)
             res.iters += prev.iters
             res.hist["fallback"] = True
             res.recycle_dim = 0

@@ -447,3 +447,21 @@ def test_autotune_params_picks_three_knobs(R):
     res, x, xt = _solve_gpu(R, S, A, b, bt)
     assert res["status"] in (R.OK, R.RECYCLE_EMPTY)
     assert np.linalg.norm(b - A.to_scipy() @ x) / np.linalg.norm(b) < 2e-9
+
+
+def test_refresh_every_matches_oracle(R):
+    # Section 6.2 policy through rbicg_set_refresh: a new recycle space only for even pairs, on a
+    # sequence whose harmonic-Ritz pencils are well conditioned (24^2, c = (1, 1), s = 30), so the
+    # per-pair counts and kept columns follow the oracle's refresh_every = 2
+    seq = I.convdiff_sequence(24, [1.0, 1.0], 4, 0.01, 17, bt_kind="normal")
+    n = seq[0]["A"].n
+    ref = O.rbicg_sequence(seq, k=8, s=30, tol=1e-10, refresh_every=2)
+    S = R.Solver(n, k=8, s=30, tol=1e-10, setup_fp32=0)
+    for j, pr in enumerate(seq):
+        S.set_refresh(1 if j % 2 == 0 else 0)
+        res, x, xt = _solve_gpu(R, S, pr["A"], pr["b"], pr["bt"])
+        assert res["status"] in (R.OK, R.RECYCLE_EMPTY)
+        assert res["recycle_dim"] == ref[j].recycle_dim, (j, res, ref[j].recycle_dim)
+        assert abs(res["iters"] - ref[j].iters) <= 2, (j, res["iters"], ref[j].iters)
+        assert (res["cycles"] == 0) == (ref[j].cycles == 0) == (j % 2 == 1)
+        assert _rel(x, ref[j].x) < 1e-8

@@ -513,3 +513,17 @@ def test_guard_baseline_does_not_shrink_after_a_fallback():
         assert r.hist["guard_limit"] == limit
         if r.hist["fallback"]:
             assert r.iters > limit
+
+
+def test_refresh_every_carries_the_space_unchanged():
+    # Section 6.2: a recycle space may be recomputed only for some systems of a sequence.  With
+    # refresh_every = 2 the odd pairs compute no cycle refresh and hand on the space they were
+    # given (the same range after the Section 4.3 rotation of their system start)
+    seq = I.convdiff_sequence(24, [1.0, 1.0], 4, 0.01, 17, bt_kind="normal")
+    rs = O.rbicg_sequence(seq, k=8, s=30, tol=1e-10, refresh_every=2)
+    assert all(r.status == O.STATUS_OK for r in rs)
+    assert rs[0].cycles > 0 and rs[2].cycles > 0 and rs[1].cycles == 0 and rs[3].cycles == 0
+    for j in (1, 3):
+        rec = O.biorth_recycle(seq[j]["A"], rs[j - 1].U_next, rs[j - 1].Ut_next, 1e-6)
+        cos = sla.svdvals(np.linalg.qr(rs[j].U_next)[0].T @ np.linalg.qr(rec[0])[0])
+        assert rs[j].U_next.shape[1] == rec[0].shape[1] and cos.min() > 1 - 1e-12
