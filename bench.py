@@ -458,17 +458,19 @@ def irka_extra(R, torch, a, N=64, nshift=8, steps=10, k=16):
     c = torch.as_tensor(rng.standard_normal(n), device="cuda")
     shifts0 = I.irka_shifts(nshift, 3001)
 
-    def run(strategy, batched):
+    def run(strategy, batched, recycle_count=0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         out = R.irka(op, b, c, shifts0, max_steps=steps, shift_tol=1e-6, strategy=strategy, batched=batched,
-                     solver_k=k, solver_s=a.s, solver_tol=a.tol, solver_setup_fp32=0)
+                     recycle_count=recycle_count, solver_k=k, solver_s=a.s, solver_tol=a.tol,
+                     solver_setup_fp32=0)
         torch.cuda.synchronize()
         return time.perf_counter() - t0, out
 
     run(1, 1)   # warm-up (adjoints, graphs, lazy module loading)
     t1, o1 = run(1, 1)
     t4, o4 = run(4, 1)
+    t2s, o2s = run(1, 1, recycle_count=2)
     t0, o0 = run(0, 1)
     ts, os_ = run(1, 0)
     its = lambda o: [int(v) for v in np.asarray(o["iters"]).sum(axis=1)]
@@ -479,17 +481,20 @@ def irka_extra(R, torch, a, N=64, nshift=8, steps=10, k=16):
             "last_shift_change": o1["last_change"],
             "solves_per_s": rate(t1, o1),
             "solves_per_s_shared_space": rate(t4, o4),
+            "solves_per_s_recycle_two_smallest": rate(t2s, o2s),
             "solves_per_s_bicg": rate(t0, o0),
             "solves_per_s_sequential": rate(ts, os_),
             "batched_over_sequential": round(ts / t1, 3),
             "iters_per_step": its(o1), "iters_per_step_shared_space": its(o4), "iters_per_step_bicg": its(o0),
             "total_iters": o1["total_iters"], "total_iters_shared_space": o4["total_iters"],
+            "total_iters_recycle_two_smallest": o2s["total_iters"],
             "total_iters_bicg": o0["total_iters"],
             "failed_solves": o1["failed_solves"] + o4["failed_solves"] + o0["failed_solves"],
             "final_shifts": [[round(float(z.real), 4), round(float(z.imag), 4)] for z in o1["shifts"]],
             "strategies": "solves_per_s: strategy 1 (per shift index, batched); shared_space: strategy 4 (one space "
-                          "for all shifts, one refresh chain per step); bicg: no recycling; sequential: strategy 1, "
-                          "shifts solved one after another"}
+                          "for all shifts, one refresh chain per step); recycle_two_smallest: strategy 1 for the two "
+                          "shifts of smallest modulus only (Section 6.2 recycles for the small shifts), the others "
+                          "BiCG; bicg: no recycling; sequential: strategy 1, shifts solved one after another"}
 
 
 # ------------------------------------------------------------------ serving
