@@ -216,13 +216,17 @@ def test_config2_recycled_pair_two_cycles_match_oracle(R):
 def test_config1_recycled_pairs_match_oracle(R):
     # 32 x 32, c0 = (10, 10), 1 % drift, bt = ones, k = 10, all-FP64 refresh.  For pairs 1..4
     # the oracle's incoming recycle space is imported, so each recycled pair is compared on its
-    # own (the full sequence is rounding-chaotic, see above): columns kept by the system start,
-    # the first two cycles' residual norms element by element, and at tol 1e-12 the solutions
-    # element by element.
+    # own (the full sequence is rounding-chaotic, see above): columns kept by the system start and
+    # the first two cycles' residual norms element by element up to the oracle's own
+    # reproducibility bound.  The recycled recurrences of this sequence do not reach 1e-12 (the
+    # oracle stalls or breaks down at that tolerance), so the full solves run at the benchmark's
+    # tolerance 1e-8 with the stagnation guard, like the oracle's sequence, and are compared with
+    # the direct solution (kappa(A) is about 440).
+    import scipy.sparse.linalg as spla
     seq = I.convdiff_sequence(32, [10.0, 10.0], 5, 0.01, 1000, bt_kind="ones")
     n = seq[0]["A"].n
     z = np.zeros(n)
-    refs = O.rbicg_sequence(seq, k=10, s=40, tol=1e-12)
+    refs = O.rbicg_sequence(seq, k=10, s=40, tol=1e-8, guard=1.5)
     for j in range(1, 5):
         U, Ut = refs[j - 1].U_next, refs[j - 1].Ut_next
         pr = seq[j]
@@ -237,9 +241,13 @@ def test_config1_recycled_pairs_match_oracle(R):
         bp = pr["b"] * (1.0 + 1e-15 * np.random.default_rng(j).uniform(-1, 1, n))
         twop = O.rbicg_pair(pr["A"], bp, pr["bt"], z, z, rec, k=10, s=40, tol=1e-12, max_itn=80)
         m_star = _onset(twop.hist["rnorm"], rh)
-        assert _onset(h, rh) >= m_star - 2, (j, _onset(h, rh), m_star)
-        S2 = R.Solver(n, k=10, s=40, tol=1e-12, setup_fp32=0, guard=0.0)
+        assert m_star >= 10 and _onset(h, rh) >= m_star - 2, (j, _onset(h, rh), m_star)
+        S2 = R.Solver(n, k=10, s=40, tol=1e-8, setup_fp32=0, guard=1.5)
+        # pair 0 first, so that the guard has the oracle's baseline (pair 0's plain count)
+        _import_and_solve(R, S2, seq[0]["A"], seq[0]["b"], seq[0]["bt"], U[:, :0], Ut[:, :0], n)
         res2, x, xt = _import_and_solve(R, S2, pr["A"], pr["b"], pr["bt"], U, Ut, n)
-        assert res2["status"] in (R.OK, R.RECYCLE_EMPTY) and refs[j].status in (O.STATUS_OK, O.STATUS_RECYCLE_EMPTY)
-        for a, b_ in ((x, refs[j].x), (xt, refs[j].xt)):
-            assert np.abs(a - b_).max() <= 1e-6 * np.abs(b_).max(), j
+        assert refs[j].status == O.STATUS_OK and res2["status"] in (R.OK, R.RECYCLE_EMPTY), (j, res2)
+        Ad = pr["A"].to_scipy().tocsc()
+        for a, b_, M in ((x, pr["b"], Ad), (xt, pr["bt"], Ad.T.tocsc())):
+            xs = spla.spsolve(M, b_)
+            assert np.abs(a - xs).max() <= 1e-5 * np.abs(xs).max(), j

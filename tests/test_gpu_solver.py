@@ -212,21 +212,32 @@ def test_fp32_refined_reaches_fp64_tolerance(R):
         assert np.linalg.norm(pr["bt"] - Ad.T @ xt) / np.linalg.norm(pr["bt"]) <= 1e-10
 
 
-def test_fp32_refined_falls_back_to_fp64_when_fp32_bicg_stalls(R):
-    # On the 128 x 128 convection-diffusion operator plain FP32 BiCG stalls near ||r|| = 4 ||b||
-    # (FP32 rounding destroys the bi-orthogonality the recurrence relies on); the FP32-refined
-    # handle detects the failed inner solves and finishes the pair, and the next one, in FP64.
+def test_fp32_refined_converges_at_128(R):
+    # 128 x 128 convection-diffusion: with compensated FP32 row sums the FP32 inner BiCG reduces
+    # the residual, and FP64 refinement reaches 1e-8 without falling back to FP64 (FP32 row sums
+    # alone stall near ||r|| = 4 ||b|| here)
     seq = I.convdiff_sequence(128, [10.0, 10.0], 2, 0.01, 4100, bt_kind="normal")
     n = seq[0]["A"].n
     S = R.Solver(n, k=10, s=40, tol=1e-8, precision="fp32_refined", inner_tol=1e-5)
     for pr in seq:
         res, x, xt = _solve_gpu(R, S, pr["A"], pr["b"], pr["bt"])
         assert res["status"] in (R.OK, R.RECYCLE_EMPTY), res
-        assert res["fallback"] == 2, res
+        assert res["fallback"] == 0 and res["refine_steps"] >= 1, res
         Ad = pr["A"].to_scipy()
         assert np.linalg.norm(pr["b"] - Ad @ x) / np.linalg.norm(pr["b"]) <= 1e-8
         assert np.linalg.norm(pr["bt"] - Ad.T @ xt) / np.linalg.norm(pr["bt"]) <= 1e-8
         assert _rel(x, sp.linalg.spsolve(Ad.tocsc(), pr["b"])) < 1e-5
+
+
+def test_fp32_refined_falls_back_to_fp64_when_inner_solves_fail(R):
+    # inner solves capped at 5 iterations cannot reduce this residual (BiCG's residual first grows
+    # to about 9.5 ||b|| here), so both the recycled and the plain retry are unusable and the
+    # handle continues in FP64 (fallback = 2), which the same cap stops
+    seq = I.convdiff_sequence(128, [10.0, 10.0], 1, 0.01, 4100, bt_kind="normal")
+    n = seq[0]["A"].n
+    S = R.Solver(n, k=10, s=40, tol=1e-8, max_itn=5, precision="fp32_refined", inner_tol=1e-5)
+    res, x, xt = _solve_gpu(R, S, seq[0]["A"], seq[0]["b"], seq[0]["bt"])
+    assert res["fallback"] == 2 and res["status"] == R.NOT_CONVERGED, res
 
 
 def test_not_converged_status_and_iterate(R):
