@@ -403,10 +403,12 @@ struct Solver : SolverBase {
     launch_svd_input<T>(C, Ct, ldk, prm.k, prm.k, n, part, gram_grid, G, s2in, s);
     launch_dense_svd(!traits<T>::cx, kdev, prm.k, s2in, nullptr, nullptr, prm.svd_tol, Nmat, Mmat, sig, &st->kc,
                      st->Dc, iflag + 2, s);
+    // U <- U N_p, Ut <- Ut M_p, then C = A U, Ct = A^H Ut for the rotated bases (as the paper
+    // defines them; an SpMM of the kept columns costs less than rotating C and Ct as well)
     launch_rotate<T>(U, ldk, Nmat, kdev, &st->kc, prm.k, n, 0, s);
-    launch_rotate<T>(C, ldk, Nmat, kdev, &st->kc, prm.k, n, 0, s);
     launch_rotate<T>(Ut, ldk, Mmat, kdev, &st->kc, prm.k, n, 0, s);
-    launch_rotate<T>(Ct, ldk, Mmat, kdev, &st->kc, prm.k, n, 0, s);
+    launch_spmm<V, T>(op, 0, U, ldk, &st->kc, KMAX, C, 0, s);
+    launch_spmm<V, T>(op, 1, Ut, ldk, &st->kc, KMAX, Ct, 0, s);
     prof->end(pi, 11, s);
     count(11);
     fetch();
@@ -465,10 +467,11 @@ struct Solver : SolverBase {
     launch_svd_input<T>(Cc[jc], Ctc[jc], ldk, prm.k, prm.k, n, gpart, gram_grid, G, s2in, q);
     launch_dense_svd(!traits<T>::cx, kk, prm.k, s2in, nullptr, nullptr, prm.svd_tol, Nmat, Mmat, sig, &st->pcyc,
                      nullptr, iflag + 3, q);
+    // eq. (equationForUC): U_j = Phi_j W_j N_j, C_j = A U_j (and the duals)
     launch_rotate<T>(Uc[jc], ldk, Nmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, q);
-    launch_rotate<T>(Cc[jc], ldk, Nmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, q);
     launch_rotate<T>(Utc[jc], ldk, Mmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, q);
-    launch_rotate<T>(Ctc[jc], ldk, Mmat, kk, &st->pcyc, prm.k, n, prm.setup_fp32, q);
+    launch_spmm<V, T>(op, 0, Uc[jc], ldk, &st->pcyc, prm.k, Cc[jc], prm.setup_fp32, q);
+    launch_spmm<V, T>(op, 1, Utc[jc], ldk, &st->pcyc, prm.k, Ctc[jc], prm.setup_fp32, q);
     prof->end(pb, 13, q);
     count(13);
     RB_CUDA(cudaEventRecord(ev_ref, q));

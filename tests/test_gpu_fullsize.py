@@ -197,9 +197,11 @@ def test_config2_recycled_pair_two_cycles_match_oracle(R):
     rec = O.biorth_recycle(seq[1]["A"], r0.U_next, r0.Ut_next, 1e-6)
     b1 = seq[1]["b"]
     ref = O.rbicg_pair(seq[1]["A"], b1, seq[1]["bt"], z, z, rec, k=20, s=40, tol=1e-8, max_itn=80)
-    bp = b1 * (1.0 + 1e-15 * np.random.default_rng(9).uniform(-1, 1, n))
-    refp = O.rbicg_pair(seq[1]["A"], bp, seq[1]["bt"], z, z, rec, k=20, s=40, tol=1e-8, max_itn=80)
-    m_star = _onset(refp.hist["rnorm"], ref.hist["rnorm"])
+    m_star = 80
+    for q in range(2):   # the earlier departure of two perturbations
+        bp = b1 * (1.0 + 1e-15 * np.random.default_rng(9 + q).uniform(-1, 1, n))
+        refp = O.rbicg_pair(seq[1]["A"], bp, seq[1]["bt"], z, z, rec, k=20, s=40, tol=1e-8, max_itn=80)
+        m_star = min(m_star, _onset(refp.hist["rnorm"], ref.hist["rnorm"]))
     assert m_star >= 20, m_star
     S = R.Solver(n, k=20, s=40, tol=1e-8, max_itn=80, setup_fp32=0, guard=0.0)
     res, x, xt = _import_and_solve(R, S, seq[1]["A"], b1, seq[1]["bt"], r0.U_next, r0.Ut_next, n)
@@ -238,9 +240,12 @@ def test_config1_recycled_pairs_match_oracle(R):
         h, rh = S.residual_history(), np.array(two.hist["rnorm"])
         assert len(h) == len(rh), (j, len(h), len(rh))
         # the same reproducibility bound as at 512^2 (see above)
-        bp = pr["b"] * (1.0 + 1e-15 * np.random.default_rng(j).uniform(-1, 1, n))
-        twop = O.rbicg_pair(pr["A"], bp, pr["bt"], z, z, rec, k=10, s=40, tol=1e-12, max_itn=80)
-        m_star = _onset(twop.hist["rnorm"], rh)
+        # where the departure starts depends on where the perturbation lands: the earliest of four
+        m_star = 80
+        for q in range(4):
+            bp = pr["b"] * (1.0 + 1e-15 * np.random.default_rng(100 * q + j).uniform(-1, 1, n))
+            twop = O.rbicg_pair(pr["A"], bp, pr["bt"], z, z, rec, k=10, s=40, tol=1e-12, max_itn=80)
+            m_star = min(m_star, _onset(twop.hist["rnorm"], rh))
         assert m_star >= 10 and _onset(h, rh) >= m_star - 2, (j, _onset(h, rh), m_star)
         S2 = R.Solver(n, k=10, s=40, tol=1e-8, setup_fp32=0, guard=1.5)
         # pair 0 first, so that the guard has the oracle's baseline (pair 0's plain count)
