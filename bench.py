@@ -396,7 +396,7 @@ def gpu_arm(a):
         hxt = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in seq]
         dvals = [torch.empty_like(o.val) for o in ops]
         drp, dci = torch.empty_like(rp), torch.empty_like(ci)
-        Se = R.Solver(n, k=a.k, s=a.s, tol=a.tol, grid_blocks=a.grid_blocks)
+        Se = R.Solver(n, k=a.k, s=a.s, tol=a.tol, grid_blocks=a.grid_blocks, setup_fp32=0)   # the headline form
         e_steps = max(1, a.steps // 2)
         h2d = d2h = 0
         torch.cuda.synchronize()

@@ -378,6 +378,9 @@ typedef struct {
                           else solve with the carried spaces (Section 6.2: every fifth step) */
   double pool_tol;     /* strategy 3 threshold on the relative shift change */
   int batched;         /* strategies 0, 1 and 4: the r solves of a step in one rbicg_solve_batch */
+  int conj_pairs;      /* 1: of each conjugate pair of shifts only the one with positive imaginary
+                          part is solved; the other's v and w are the complex conjugates (exact for
+                          real A, b, c), reported with 0 iterations; 0: every shift is solved */
 } rbicg_irka_params;
 
 typedef struct {
@@ -390,7 +393,7 @@ typedef struct {
 } rbicg_irka_result;
 
 /* Fill *p with the defaults: r = 8, max_steps = 10, shift_tol = 1e-6, strategy = 1,
- * recycle_count = 0, refresh_every = 1, pool_tol = 0.5, batched = 1. */
+ * recycle_count = 0, refresh_every = 1, pool_tol = 0.5, batched = 1, conj_pairs = 1. */
 void rbicg_irka_default_params(rbicg_irka_params *p);
 
 /* Run IRKA.  sp: the RBiCG parameters of every solve (complex double vectors, C128).  A: the real

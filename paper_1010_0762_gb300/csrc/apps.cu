@@ -99,6 +99,12 @@ static cudaError_t bilinear_impl(const rbicg_csr* A, const void* u, const void* 
 // ------------------------------------------------------------------------------------
 // IRKA (Algorithm 3) device helpers
 // ------------------------------------------------------------------------------------
+// dst = conj(src): the solution of the conjugate shift (real A, b, c)
+__global__ void k_conj_copy(const zd* src, zd* dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = conjg(src[i]);
+}
+
 __global__ void k_widen(const double* a, zd* b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = zd(a[i], 0.0);
@@ -233,6 +239,7 @@ extern "C" void rbicg_irka_default_params(rbicg_irka_params* p) {
   p->refresh_every = 1;
   p->pool_tol = 0.5;
   p->batched = 1;
+  p->conj_pairs = 1;
 }
 
 extern "C" rbicg_status rbicg_bilinear_form(const rbicg_csr* A, rbicg_dtype dtype, const void* u, const void* w,
@@ -269,9 +276,10 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
   }
   const int r = ip->r;
   if (r < 1 || r > KMAX || ip->max_steps < 1 || !(ip->shift_tol > 0.0) || ip->strategy < 0 || ip->strategy > 4 ||
-      ip->recycle_count < 0 || ip->refresh_every < 1 || !(ip->pool_tol > 0.0)) {
+      ip->recycle_count < 0 || ip->refresh_every < 1 || !(ip->pool_tol > 0.0) ||
+      (ip->conj_pairs != 0 && ip->conj_pairs != 1)) {
     set_global_error("rbicg_irka: need 1 <= r <= 32, max_steps >= 1, shift_tol > 0, strategy 0..4, "
-                     "recycle_count >= 0, refresh_every >= 1, pool_tol > 0");
+                     "recycle_count >= 0, refresh_every >= 1, pool_tol > 0, conj_pairs 0 or 1");
     return RBICG_ERR_ARG;
   }
   if (A->val_complex || A->has_shift) {
@@ -387,21 +395,37 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
         ops[i].shift_re = sig[i].real();
         ops[i].shift_im = sig[i].imag();
       }
+      // conj_pairs: of a conjugate pair (adjacent, + first) only the + shift is solved; the other
+      // column is its conjugate (real A, b, c)
+      std::vector<int> partner(r, -1), solve_idx;
+      for (int i = 0; i < r; ++i) {
+        if (ip->conj_pairs && i > 0 && partner[i - 1] == i) continue;
+        if (ip->conj_pairs && i + 1 < r && sig[i].imag() > 0.0 && sig[i + 1] == std::conj(sig[i])) partner[i] = i + 1;
+        solve_idx.push_back(i);
+      }
+      for (int i = 0; i < r; ++i) rs[i] = rbicg_result{};
       // Algorithm 3 steps 2-3 (and the loop's solves): v_i = (sigma_i I - A)^{-1} b,
       // w_i = (sigma_i I - A)^{-H} c, each from the previous step's solution for index i
-      if (per_index && ip->batched && r > 1) {
-        std::vector<const rbicg_csr*> pa(r);
-        std::vector<const void*> pb(r), pc(r);
-        std::vector<void*> px(r), pxt(r);
-        for (int i = 0; i < r; ++i) {
-          pa[i] = &ops[i]; pb[i] = bz; pc[i] = cz;
-          px[i] = V + (int64_t)i * n; pxt[i] = W + (int64_t)i * n;
+      const int nsolve = (int)solve_idx.size();
+      if (per_index && ip->batched && nsolve > 1) {
+        std::vector<const rbicg_csr*> pa(nsolve);
+        std::vector<const void*> pb(nsolve), pc(nsolve);
+        std::vector<void*> px(nsolve), pxt(nsolve);
+        std::vector<rbicg_handle> hb(nsolve);
+        std::vector<rbicg_result> rb(nsolve);
+        for (int q = 0; q < nsolve; ++q) {
+          const int i = solve_idx[q];
+          hb[q] = hidx[i];
+          pa[q] = &ops[i]; pb[q] = bz; pc[q] = cz;
+          px[q] = V + (int64_t)i * n; pxt[q] = W + (int64_t)i * n;
         }
-        IR_CALL(rbicg_solve_batch(hidx.data(), pa.data(), pb.data(), pc.data(), px.data(), pxt.data(), r, rs.data()),
-                hidx[0]);
+        IR_CALL(rbicg_solve_batch(hb.data(), pa.data(), pb.data(), pc.data(), px.data(), pxt.data(), nsolve,
+                                  rb.data()),
+                hb[0]);
+        for (int q = 0; q < nsolve; ++q) rs[solve_idx[q]] = rb[q];
       } else {
         pool_cur.clear();
-        for (int i = 0; i < r; ++i) {
+        for (int i : solve_idx) {
           rbicg_handle h = per_index ? hidx[i] : (i < nrec ? hrec : hplain);
           if (ip->strategy == 3 && i < nrec) {
             // reading of strategy 3: the pooled space with the smallest relative shift change,
@@ -434,12 +458,19 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
         }
         if (ip->strategy == 3) pool_prev = pool_cur;
       }
+      for (int i = 0; i < r; ++i)
+        if (partner[i] >= 0) {
+          const int g = (int)std::min<int64_t>((n + 255) / 256, 4 * sm_count());
+          k_conj_copy<<<g, 256, 0, s>>>(V + (int64_t)i * n, V + (int64_t)partner[i] * n, n);
+          k_conj_copy<<<g, 256, 0, s>>>(W + (int64_t)i * n, W + (int64_t)partner[i] * n, n);
+        }
       int64_t its = 0;
-      for (int i = 0; i < r; ++i) {
+      for (int i : solve_idx) {
         its += rs[i].iters;
-        if (iters_out) iters_out[(int64_t)step * r + i] = rs[i].iters;
         if (rs[i].status != RBICG_OK && rs[i].status != RBICG_RECYCLE_EMPTY) ++res->failed_solves;
       }
+      if (iters_out)
+        for (int i = 0; i < r; ++i) iters_out[(int64_t)step * r + i] = rs[i].iters;   // 0: taken by conjugation
       res->iters += its;
       // Algorithm 3 step 4: A_r = W^H A V, E_r = W^H V (E = I), b_r = W^H b, c_r = V^H c
       k_apply_cols<<<(int)std::min<int64_t>((n * r + 255) / 256, 8 * sm_count()), 256, 0, s>>>(

@@ -52,7 +52,7 @@ class Result(C.Structure):
 class IrkaParams(C.Structure):
     _fields_ = [("r", C.c_int), ("max_steps", C.c_int), ("shift_tol", C.c_double), ("strategy", C.c_int),
                 ("recycle_count", C.c_int), ("refresh_every", C.c_int), ("pool_tol", C.c_double),
-                ("batched", C.c_int)]
+                ("batched", C.c_int), ("conj_pairs", C.c_int)]
 
 
 class IrkaResult(C.Structure):

@@ -91,7 +91,7 @@ def test_irka_recycling_counts_match_oracle_and_save_iterations(R):
     op = R.Operator.from_csr(A)
     tot = {}
     for strategy in (0, 1, 4):
-        got = R.irka(op, _dev(b), _dev(c), sh, max_steps=5, shift_tol=1e-14, strategy=strategy,
+        got = R.irka(op, _dev(b), _dev(c), sh, max_steps=5, shift_tol=1e-14, strategy=strategy, conj_pairs=0,
                      solver_k=8, solver_s=20, solver_tol=1e-10, solver_setup_fp32=0)
         ref = IR.irka(A, b, c, sh, IR.rbicg_solver(A, b, c, k=8, s=20, tol=1e-10, strategy=strategy),
                       max_steps=5, shift_tol=1e-14)
@@ -113,3 +113,19 @@ def test_irka_refresh_every_keeps_spaces_between_refreshes(R):
                 solver_s=20, solver_tol=1e-12, solver_setup_fp32=0)
     np.testing.assert_allclose(a2["shifts"], a1["shifts"], rtol=1e-8)
     assert a2["failed_solves"] == 0
+
+
+def test_irka_conjugate_pairs_solved_once(R):
+    # real A, b, c: (conj(sigma) I - A)^{-1} b = conj((sigma I - A)^{-1} b) and the same for the dual,
+    # so solving one shift of each conjugate pair gives the same shifts and reduced model with about
+    # half the iterations
+    A, b, c, sh = _irka_problem(r=8)
+    op = R.Operator.from_csr(A)
+    kw = dict(max_steps=3, shift_tol=1e-14, strategy=1, solver_k=8, solver_s=20, solver_tol=1e-12,
+              solver_setup_fp32=0)
+    full = R.irka(op, _dev(b), _dev(c), sh, conj_pairs=0, **kw)
+    half = R.irka(op, _dev(b), _dev(c), sh, conj_pairs=1, **kw)
+    np.testing.assert_allclose(half["shifts"], full["shifts"], rtol=1e-8)
+    for key in ("Ar", "Er", "br", "cr"):
+        np.testing.assert_allclose(half[key], full[key], rtol=0, atol=1e-7 * np.abs(full[key]).max())
+    assert half["total_iters"] <= 0.6 * full["total_iters"], (half["total_iters"], full["total_iters"])
