@@ -47,6 +47,10 @@ def parse():
                     help="blocks per iteration-phase launch (0: the library default)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32-refined, BiCG and e2e passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config4", action="store_true",
+                    help="also run the 1024^2 mixed-precision sequence (10 pairs, 0.5 %% drift, tol 1e-10)")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="serve 256 requests from families of grid sides 64..1024 instead of 64 from 64..256")
     return ap.parse_args()
 
 
@@ -426,7 +430,10 @@ def gpu_arm(a):
                       "h2d_bytes_per_step": int(h2d // e_steps), "d2h_bytes_per_step": int(d2h // e_steps),
                       "steps": e_steps}
 
-        for key, fn in (("irka", irka_extra), ("serving", serving_extra)):
+        extras = [("irka", irka_extra), ("serving", serving_extra)]
+        if a.config4:
+            extras.append(("config4", config4_extra))
+        for key, fn in extras:
             try:
                 out[key] = fn(R, torch, a)
             except Exception as exc:   # an extra must not take the headline line down
@@ -498,20 +505,66 @@ def irka_extra(R, torch, a, N=64, nshift=8, steps=10, k=16):
 
 
 # ------------------------------------------------------------------ serving
-def serving_extra(R, torch, a, families=16, requests=64, seed=5000):
+def config4_extra(R, torch, a, N=1024, pairs=10, tol=1e-10):
+    """Mixed precision at 1024^2 (n = 1048576, nnz = 5238784): 10 pairs with 0.5 % drift, relative
+    tolerance 1e-10, the FP32-refined form against all-FP64 RBiCG on the same sequence (one timed
+    pass each, after a warm-up pass); the refined solutions are compared with the FP64 ones."""
+    from paper_1010_0762_gb300 import inputs as I
+    seq = I.convdiff_sequence(N, [10.0, 10.0], pairs, 0.005, 4000, bt_kind="normal")
+    n = seq[0]["A"].n
+    rp = torch.as_tensor(seq[0]["A"].row_ptr, device="cuda")
+    ci = torch.as_tensor(seq[0]["A"].col_idx, device="cuda")
+    ops = [R.Operator(rp, ci, torch.as_tensor(p["A"].val, device="cuda")) for p in seq]
+    bs = [torch.as_tensor(p["b"], device="cuda") for p in seq]
+    bts = [torch.as_tensor(p["bt"], device="cuda") for p in seq]
+    out = {"workload": "convdiff2d-%dx%d-seq%d-k%d, drift 0.5 %%, tol %g" % (N, N, pairs, a.k, tol), "n": n,
+           "nnz": seq[0]["A"].nnz}
+    sols = {}
+    for form, kw in (("fp64", dict(setup_fp32=0)), ("fp32_refined", dict(precision="fp32_refined"))):
+        S = R.Solver(n, k=a.k, s=a.s, tol=tol, **kw)
+        xs = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in seq]
+        xts = [torch.zeros_like(xs[0]) for _ in seq]
+        res = []
+        for rep in range(2):
+            res = []
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            run_sequence(R, torch, S, ops, bs, bts, xs, xts, res)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        sols[form] = xs
+        out[form] = {"solves_per_s": round(pairs / dt, 4), "s_per_sequence": round(dt, 3),
+                     "iters_per_pair": [r["iters"] for r in res], "refine_steps": [r["refine_steps"] for r in res],
+                     "fp64_fallback_pairs": sum(1 for r in res if r["fallback"] == 2),
+                     "worst_true_relres": max(max(r["true_relres"], r["true_relres_dual"]) for r in res),
+                     "all_converged": all(r["status"] in (R.OK, R.RECYCLE_EMPTY) for r in res)}
+        S.destroy()
+    out["max_rel_diff_fp32_refined_vs_fp64"] = max(
+        float(torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0)) for x0, x1 in zip(sols["fp64"], sols["fp32_refined"]))
+    return out
+
+
+def serving_extra(R, torch, a, families=16, requests=64, seed=5000, restarts=8):
     """Continuous batching over the engine: Poisson arrivals of dual-pair requests from
     `families` convection-diffusion families (grid sides log-uniform in [64, 256] here, so the
     run stays within a minute; (c1, c2) ~ U[1, 50]^2, 1 % drift per request, k ~ U{10..20},
     precision fp32_refined with probability 0.5), recycle spaces resident per family, HBM
     budget 80 % of free memory.  A closed-loop run (all requests at t = 0) measures capacity;
-    the open-loop run offers 0.8 x that rate."""
+    the open-loop runs offer 0.8 x and 1.2 x that rate.  With (c1 + c2) / 2 up to 50 the
+    operators are far from normal (the diagonal that symmetrises them spans about
+    e^((c1 + c2) / 2)), so BiCG's shadow and primary residuals lose their correlation and many
+    requests break down after ~130 iterations; the requests are served with `restarts`
+    restarts after a breakdown (plain BiCG from the iterate; not in the paper)."""
     from paper_1010_0762_gb300 import serving as SV
-    specs = SV.random_families(families, seed, side_lo=64, side_hi=256)
+    side_hi = 1024 if a.serving_full else 256
+    if a.serving_full:
+        requests = 256
+    specs = SV.random_families(families, seed, side_lo=64, side_hi=side_hi)
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
 
     def serve(rate):
-        be = SV.GpuBackend(s=a.s, tol=a.tol)
+        be = SV.GpuBackend(s=a.s, tol=a.tol, restarts=restarts)
         srv = SV.Server(specs, be, budget, s=a.s, max_in_flight=32)
         reqs = SV.poisson_arrivals(requests, rate if rate > 0 else 1.0, specs, seed + 1, p_fp32=0.5)
         if rate <= 0:
@@ -526,7 +579,8 @@ def serving_extra(R, torch, a, families=16, requests=64, seed=5000):
     serve(1e9)   # warm-up
     closed = serve(0)
     cap = closed["requests_per_s"]
-    out = {"workload": "%d families, grid sides 64..256, %d requests, fp32_refined p=0.5" % (families, requests),
+    out = {"workload": "%d families, grid sides 64..%d, %d requests, fp32_refined p=0.5, %d restarts after a "
+                       "breakdown" % (families, side_hi, requests, restarts),
            "closed_loop": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in closed.items()}}
     for f in (0.8, 1.2):
         st = serve(f * cap)

@@ -353,6 +353,7 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
     zd* shU = ip->strategy == 4 ? run.alloc<zd>((size_t)n * kk) : nullptr;
     zd* shUt = ip->strategy == 4 ? run.alloc<zd>((size_t)n * kk) : nullptr;
 
+    std::vector<char> has_op(r, 0);   // handle hidx[i] has been given an operator
     std::vector<cd> sig(r);
     for (int i = 0; i < r; ++i) sig[i] = cd(shifts_in[2 * i], shifts_in[2 * i + 1]);
     {
@@ -370,25 +371,6 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
     for (int step = 0; step < ip->max_steps; ++step) {
       const int refresh = step % ip->refresh_every == 0 ? 1 : 0;
       for (rbicg_handle h : run.handles) IR_CALL(rbicg_set_refresh(h, refresh), h);
-      if (ip->strategy == 4) {
-        // one recycle space shared by all shifts (E = I: sigma I - A has A's eigenvectors): the
-        // solve of shift index 0 computes it, the other shifts use the one it computed last step
-        for (int i = 1; i < nrec; ++i) IR_CALL(rbicg_set_refresh(hidx[i], 0), hidx[i]);
-        if (step > 0 && nrec > 1) {
-          int p = 0;
-          IR_CALL(rbicg_export_recycle(hidx[0], shU, shUt, &p), hidx[0]);
-          if (p > 0) {
-            IR_CUDA(cudaMemcpy2DAsync(tmpU, sizeof(zd) * p, shU, sizeof(zd) * kk, sizeof(zd) * p, n,
-                                      cudaMemcpyDeviceToDevice, s));
-            IR_CUDA(cudaMemcpy2DAsync(tmpUt, sizeof(zd) * p, shUt, sizeof(zd) * kk, sizeof(zd) * p, n,
-                                      cudaMemcpyDeviceToDevice, s));
-          }
-          for (int i = 1; i < nrec; ++i) {
-            if (p > 0) IR_CALL(rbicg_import_recycle(hidx[i], tmpU, tmpUt, p), hidx[i]);
-            else IR_CALL(rbicg_reset(hidx[i]), hidx[i]);
-          }
-        }
-      }
       for (int i = 0; i < r; ++i) {
         ops[i] = *A;
         ops[i].has_shift = 1;
@@ -402,6 +384,31 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
         if (ip->conj_pairs && i > 0 && partner[i - 1] == i) continue;
         if (ip->conj_pairs && i + 1 < r && sig[i].imag() > 0.0 && sig[i + 1] == std::conj(sig[i])) partner[i] = i + 1;
         solve_idx.push_back(i);
+      }
+      if (ip->strategy == 4) {
+        // one recycle space shared by all shifts (E = I: sigma I - A has A's eigenvectors): the
+        // solve of shift index 0 computes it, the other shifts use the one it computed last step
+        for (int i = 1; i < nrec; ++i) IR_CALL(rbicg_set_refresh(hidx[i], 0), hidx[i]);
+        if (step > 0 && nrec > 1) {
+          int p = 0;
+          IR_CALL(rbicg_export_recycle(hidx[0], shU, shUt, &p), hidx[0]);
+          if (p > 0) {
+            IR_CUDA(cudaMemcpy2DAsync(tmpU, sizeof(zd) * p, shU, sizeof(zd) * kk, sizeof(zd) * p, n,
+                                      cudaMemcpyDeviceToDevice, s));
+            IR_CUDA(cudaMemcpy2DAsync(tmpUt, sizeof(zd) * p, shUt, sizeof(zd) * kk, sizeof(zd) * p, n,
+                                      cudaMemcpyDeviceToDevice, s));
+          }
+          for (int i : solve_idx) {
+            if (i == 0 || i >= nrec) continue;
+            if (p > 0) {
+              // a handle whose index was a conjugate partner so far has no operator yet
+              if (!has_op[i]) IR_CALL(rbicg_update_recycle(hidx[i], &ops[i]), hidx[i]);
+              IR_CALL(rbicg_import_recycle(hidx[i], tmpU, tmpUt, p), hidx[i]);
+            } else {
+              IR_CALL(rbicg_reset(hidx[i]), hidx[i]);
+            }
+          }
+        }
       }
       for (int i = 0; i < r; ++i) rs[i] = rbicg_result{};
       // Algorithm 3 steps 2-3 (and the loop's solves): v_i = (sigma_i I - A)^{-1} b,
@@ -423,6 +430,7 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
                                   rb.data()),
                 hb[0]);
         for (int q = 0; q < nsolve; ++q) rs[solve_idx[q]] = rb[q];
+        for (int i : solve_idx) has_op[i] = 1;
       } else {
         pool_cur.clear();
         for (int i : solve_idx) {
@@ -449,6 +457,7 @@ extern "C" rbicg_status rbicg_irka(const rbicg_params* sp, const rbicg_irka_para
             }
           }
           IR_CALL(rbicg_solve_pair(h, &ops[i], bz, cz, V + (int64_t)i * n, W + (int64_t)i * n, &rs[i]), h);
+          has_op[i] = 1;
           if (ip->strategy == 3 && i < nrec) {
             zd* buf = slot_bufs[(step & 1) * r + i];
             Slot sl{sig[i], 0, buf, buf + (size_t)n * kk};

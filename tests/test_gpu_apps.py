@@ -117,15 +117,20 @@ def test_irka_refresh_every_keeps_spaces_between_refreshes(R):
 
 def test_irka_conjugate_pairs_solved_once(R):
     # real A, b, c: (conj(sigma) I - A)^{-1} b = conj((sigma I - A)^{-1} b) and the same for the dual,
-    # so solving one shift of each conjugate pair gives the same shifts and reduced model with about
-    # half the iterations
-    A, b, c, sh = _irka_problem(r=8)
+    # so solving one shift of each conjugate pair gives the shifts and reduced model of the oracle's
+    # direct solves with fewer iterations (r = 4: two pairs at the start, one pair and two real shifts
+    # after the first step, so 2 + 3 + 3 of 12 solves).  A larger r on this n = 144 problem leaves
+    # E_r near singular (cond ~ 3e10 at r = 8), where solves at 1e-12 already move the shifts.
+    A, b, c, sh = _irka_problem(r=4)
     op = R.Operator.from_csr(A)
+    ref = IR.irka(A, b, c, sh, IR.direct_solver(A, b, c), max_steps=3, shift_tol=1e-14)
     kw = dict(max_steps=3, shift_tol=1e-14, strategy=1, solver_k=8, solver_s=20, solver_tol=1e-12,
               solver_setup_fp32=0)
     full = R.irka(op, _dev(b), _dev(c), sh, conj_pairs=0, **kw)
     half = R.irka(op, _dev(b), _dev(c), sh, conj_pairs=1, **kw)
-    np.testing.assert_allclose(half["shifts"], full["shifts"], rtol=1e-8)
-    for key in ("Ar", "Er", "br", "cr"):
-        np.testing.assert_allclose(half[key], full[key], rtol=0, atol=1e-7 * np.abs(full[key]).max())
-    assert half["total_iters"] <= 0.6 * full["total_iters"], (half["total_iters"], full["total_iters"])
+    m = ref["model"]
+    for got in (full, half):
+        assert np.max(np.abs(got["shifts"] - ref["shifts"]) / np.abs(ref["shifts"])) < 1e-8
+        for key in ("Ar", "Er", "br", "cr"):
+            np.testing.assert_allclose(got[key], m[key], rtol=0, atol=1e-7 * np.abs(m[key]).max())
+    assert half["total_iters"] <= 0.75 * full["total_iters"], (half["total_iters"], full["total_iters"])
