@@ -260,7 +260,9 @@ int64_t rbicg_launch_count(rbicg_handle h);
 
 /* Measurement hooks (no counterpart in the paper): device time of each step of the solve,
  * taken with CUDA events on the handle's stream.  enable = 1 starts collection (clearing the
- * accumulators), 0 stops it, -1 only reads.  ms_out / launches_out (host arrays of
+ * accumulators), 2 starts it with every cycle refresh run alone (the refresh waits for the
+ * iteration stream and the iteration stream for the refresh, so each step's time is its own,
+ * not shared with the concurrent next cycle), 0 stops it, -1 only reads.  ms_out / launches_out (host arrays of
  * RBICG_NPROF, may be NULL) receive the accumulated milliseconds and kernel launches per
  * slot: 0 dual SpMV + projections (Algorithm 2 step 5, lines 1-3; without a recycle space
  * also (pt, q) and alpha), 1 q and (pt, q) (iterations with a recycle space only),

@@ -100,6 +100,7 @@ struct OpKey {
 // ------------------------------------------------------------------------------------
 struct Profiler {
   bool on = false;
+  bool serial = false;   // refreshes run alone: no overlap with the iteration stream
   double ms[RBICG_NPROF] = {};
   int64_t cnt[RBICG_NPROF] = {};
   int64_t pcols = 0;   // projection columns summed over the slot-0 launches
@@ -420,6 +421,9 @@ struct Solver : SolverBase {
   // at the next sync (st->pcyc, st->eig_status).
   void refresh(int j, int kp, bool cycle_end_recorded = false) {
     if (!cycle_end_recorded) RB_CUDA(cudaEventRecord(ev_cycle, s));
+    // serialised profiling: the refresh also waits for everything queued on the iteration
+    // stream so far (a next cycle launched before it), and that stream waits for the refresh
+    if (prof->on && prof->serial) RB_CUDA(cudaEventRecord(ev_cycle, s));
     RB_CUDA(cudaStreamWaitEvent(s2, ev_cycle, 0));
     cudaStream_t q = s2;
     const bool first = kc == 0;
@@ -476,6 +480,7 @@ struct Solver : SolverBase {
     count(13);
     RB_CUDA(cudaEventRecord(ev_ref, q));
     ref_pending = true;
+    if (prof->on && prof->serial) join_refresh();
   }
 
   // ------------------------------------------------------------------ Algorithm 2
@@ -1439,6 +1444,7 @@ extern "C" rbicg_status rbicg_profile(rbicg_handle h, int enable, double* ms_out
   if (enable >= 0) {
     if (enable && !h->prof.on) h->prof.reset();
     h->prof.on = enable != 0;
+    h->prof.serial = enable == 2;
   }
   return RBICG_OK;
 }

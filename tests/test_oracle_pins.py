@@ -527,3 +527,26 @@ def test_refresh_every_carries_the_space_unchanged():
         rec = O.biorth_recycle(seq[j]["A"], rs[j - 1].U_next, rs[j - 1].Ut_next, 1e-6)
         cos = sla.svdvals(np.linalg.qr(rs[j].U_next)[0].T @ np.linalg.qr(rec[0])[0])
         assert rs[j].U_next.shape[1] == rec[0].shape[1] and cos.min() > 1 - 1e-12
+
+
+def test_breakdown_restart_continues_as_bicg_from_the_iterate():
+    # The restart after a breakdown (rbicg_sequence restarts > 0; a library policy, not in the
+    # paper) must be plain BiCG (Algorithm 1, the oracle's separate bicg routine) started from the
+    # iterate at which the first leg broke down.  On this strongly convective operator BiCG's
+    # (pt, q) falls below 1e-14 of the norms after 69 iterations; the restarted leg converges.
+    A = I.convdiff(32, [30.0, 30.0])
+    rng = np.random.default_rng(7)
+    b, bt = rng.standard_normal(A.n), rng.standard_normal(A.n)
+    z = np.zeros(A.n)
+    first = O.bicg(A, b, bt, z, z, 1e-8, 5000)
+    assert first.status in (O.STATUS_BREAKDOWN_RHO, O.STATUS_BREAKDOWN_PQ)
+    second = O.bicg(A, b, bt, first.x, first.xt, 1e-8, 5000)
+    assert second.status == O.STATUS_OK
+    pr = [{"A": A, "b": b, "bt": bt}]
+    no = O.rbicg_sequence(pr, k=6, s=20, tol=1e-8, max_itn=5000, restarts=0)[0]
+    assert no.status == first.status and abs(no.iters - first.iters) <= 2
+    got = O.rbicg_sequence(pr, k=6, s=20, tol=1e-8, max_itn=5000, restarts=1)[0]
+    assert got.status == O.STATUS_OK and got.hist["fallback"]
+    assert abs(got.iters - (first.iters + second.iters)) <= 3, (got.iters, first.iters, second.iters)
+    assert np.linalg.norm(got.x - second.x) <= 1e-6 * np.linalg.norm(second.x)
+    assert got.true_relres <= 1e-8 and got.true_relres_dual <= 1e-8
