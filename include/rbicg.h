@@ -106,7 +106,9 @@ typedef struct {
                               (pt, q) below 1e-14 of the norms) applies step 7 and continues from
                               its iterate as plain BiCG, at most this many times */
   int grid_blocks;         /* blocks of 256 threads per iteration-phase launch (0: the default,
-                              min(ceil(n / 256), 3 x SMs)); rbicg_autotune picks one by timed
+                              min(ceil(n / 256), 2 x SMs) with recycling, whose cycle refresh runs
+                              concurrently and needs room on the SMs, 3 x SMs without);
+                              rbicg_autotune picks one by timed
                               trials.  Reductions follow the block partition, so results are
                               reproducible for a given value. */
   int refresh;             /* 1 (default): refresh the recycle space every s iterations and hand the

@@ -236,11 +236,15 @@ struct Solver : SolverBase {
     RB_CUDA(cudaEventCreateWithFlags(&ev_g0, cudaEventDisableTiming));
     RB_CUDA(cudaEventCreateWithFlags(&ev_g1, cudaEventDisableTiming));
     const int sms = num_sms();
-    // default: one wave of the recycling phase-1 kernel (3 resident blocks per SM); every block
-    // walks an equal share of whole 32-row chunks, so each SM gets the same rows
+    // default: 3 blocks per SM (one wave of the phase-1 kernel, which then fills the register
+    // file) without recycling; 2 per SM with it, so that the cycle refresh, which runs concurrently
+    // on its own stream and is bound by the same FP64 units, finds room on every SM (512^2
+    // benchmark sequence: 189 us per iteration in all against 228 us with 3 per SM and 202 us with
+    // 1).  Every block walks an equal share of whole 32-row chunks, so each SM gets the same rows.
+    const int per_sm = prm.recycle ? 2 : 3;
     grid = prm.grid_blocks > 0
                ? (int)std::min<int64_t>(prm.grid_blocks, std::max<int64_t>(1, (n + NTHREADS - 1) / NTHREADS))
-               : (int)std::max<int64_t>(1, std::min<int64_t>((n + NTHREADS - 1) / NTHREADS, (int64_t)sms * 3));
+               : (int)std::max<int64_t>(1, std::min<int64_t>((n + NTHREADS - 1) / NTHREADS, (int64_t)sms * per_sm));
     // blocks of the refresh's Gram products (rbicg_params.setup_blocks; default 2 x SMs)
     gram_grid = prm.setup_blocks > 0 ? prm.setup_blocks : 2 * sms;
     const int64_t ldv = ((n + 31) / 32) * 32;   // padded vector stride (256-byte aligned slots)

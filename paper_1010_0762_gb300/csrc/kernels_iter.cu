@@ -559,7 +559,8 @@ __device__ __forceinline__ int batch_slot(const BatchArgs<V, T>* ba) {
 }
 // MINB resident blocks per SM: the unrolled slab projection of phase 1 otherwise takes 128
 // registers a thread and halves the warps that hide the gather latency.  Three blocks per SM is
-// the default grid's one wave (3 x SMs blocks); phase 2's staged slices need that many
+// the default grid's one wave without recycling (3 x SMs blocks; with recycling the default is
+// 2 x SMs, leaving room for the concurrent refresh); phase 2's staged slices need that many
 // registers to stay out of local memory.
 #define RB_PHASE_KERNELS(NAME, BODY, MINB, TPARAMS, TARGS)                                               \
   template <TPARAMS>                                                                                    \

@@ -372,17 +372,19 @@ def test_second_system_recycle_space_matches_oracle(R, setup_fp32):
 @pytest.mark.parametrize("setup_fp32", [0, 1])
 def test_well_conditioned_sequence_recycle_spaces_match_oracle(R, setup_fp32):
     # A sequence whose harmonic-Ritz pencils are well conditioned (24^2, c = (1, 1), s = 30: a
-    # relative perturbation of 1e-14 of (L, R) moves its selected eigenvalues by about 2e-7): every
-    # pair's iteration count within 2 of the oracle's, and after every pair every principal angle
-    # between the library's recycle spaces and the oracle's, primal and dual (FP64 refresh: cosines
-    # above 1 - 1e-6; FP32-multiplied refresh products perturb the pencil at the 1e-7 level, which
-    # this conditioning turns into about 1e-3 in the selected directions)
+    # relative perturbation of 1e-14 of (L, R) moves the first system's selected eigenvalues by
+    # about 2e-7): every pair's iteration count within 2 of the oracle's, and after every pair every
+    # principal angle between the library's recycle spaces and the oracle's, primal and dual.
+    # FP64 refresh: the first system's spaces to 1 - cos < 1e-8; the recycled pair's to 1e-4, the
+    # oracle's own reproducibility there (perturbing b of pair 0 by 1e-15 or 1e-13 relative moves
+    # the oracle's pair-1 spaces by 1.5e-5 primal and 3e-5 dual).  FP32-multiplied refresh products
+    # perturb the pencil at the 1e-7 level: 1e-2 for both pairs.
     # (two pairs: on the third the recycled recurrence of this sequence stalls, oracle included)
     seq = I.convdiff_sequence(24, [1.0, 1.0], 2, 0.01, 17, bt_kind="normal")
     n = seq[0]["A"].n
     ref = O.rbicg_sequence(seq, k=8, s=30, tol=1e-10)
     S = R.Solver(n, k=8, s=30, tol=1e-10, setup_fp32=setup_fp32)
-    tol = 1e-6 if setup_fp32 == 0 else 1e-2
+    tols = (1e-8, 1e-4) if setup_fp32 == 0 else (1e-2, 1e-2)
     worst = []
     for j, pr in enumerate(seq):
         res, x, xt = _solve_gpu(R, S, pr["A"], pr["b"], pr["bt"])
@@ -393,7 +395,7 @@ def test_well_conditioned_sequence_recycle_spaces_match_oracle(R, setup_fp32):
         assert U.shape[1] == ref[j].U_next.shape[1] == Ut.shape[1]
         cos, cost = _angles(U, ref[j].U_next), _angles(Ut, ref[j].Ut_next)
         worst.append((j, 1 - cos.min(), 1 - cost.min()))
-    assert all(w[1] < tol and w[2] < tol for w in worst), worst
+    assert all(w[1] < tols[w[0]] and w[2] < tols[w[0]] for w in worst), worst
 
 
 def test_stagnation_guard_matches_oracle_and_converges(R):
