@@ -550,12 +550,13 @@ def irka_extra(R, torch, a, N=64, nshift=8, steps=10, k=16):
 
 
 # ------------------------------------------------------------------ serving
-def config4_extra(R, torch, a, N=1024, pairs=10, tol=1e-10):
+def config4_extra(R, torch, a, N=1024, pairs=10, tol=1e-10, restarts=8):
     """Mixed precision at 1024^2 (n = 1048576, nnz = 5238784): 10 pairs with 0.5 % drift, relative
     tolerance 1e-10, the FP32-refined form against all-FP64 RBiCG on the same sequence (one timed
     pass each, after an untimed solve of pair 0); both forms run their refresh products in FP64
-    (setup_fp32 = 0), so the refined form's FP64 fallback is the FP64 form itself.  The refined
-    solutions are compared with the FP64 ones."""
+    (setup_fp32 = 0), so the refined form's FP64 fallback is the FP64 form itself.  Both restart
+    as plain BiCG after a breakdown (`restarts`, as the serving run: at this tolerance a pair can
+    end in a BiCG breakdown).  The refined solutions are compared with the FP64 ones."""
     from paper_1010_0762_gb300 import inputs as I
     seq = I.convdiff_sequence(N, [10.0, 10.0], pairs, 0.005, 4000, bt_kind="normal")
     n = seq[0]["A"].n
@@ -568,7 +569,7 @@ def config4_extra(R, torch, a, N=1024, pairs=10, tol=1e-10):
            "nnz": seq[0]["A"].nnz}
     sols = {}
     for form, kw in (("fp64", dict(setup_fp32=0)), ("fp32_refined", dict(precision="fp32_refined", setup_fp32=0))):
-        S = R.Solver(n, k=a.k, s=a.s, tol=tol, **kw)
+        S = R.Solver(n, k=a.k, s=a.s, tol=tol, restarts=restarts, **kw)
         xs = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in seq]
         xts = [torch.zeros_like(xs[0]) for _ in seq]
         run_sequence(R, torch, S, ops[:1], bs[:1], bts[:1], xs[:1], xts[:1])   # warm-up (untimed)
@@ -582,11 +583,15 @@ def config4_extra(R, torch, a, N=1024, pairs=10, tol=1e-10):
         out[form] = {"solves_per_s": round(pairs / dt, 4), "s_per_sequence": round(dt, 3),
                      "iters_per_pair": [r["iters"] for r in res], "refine_steps": [r["refine_steps"] for r in res],
                      "fp64_fallback_pairs": sum(1 for r in res if r["fallback"] == 2),
+                     "status_per_pair": [int(r["status"]) for r in res],
+                     "fallback_per_pair": [int(r["fallback"]) for r in res],
                      "worst_true_relres": max(max(r["true_relres"], r["true_relres_dual"]) for r in res),
                      "all_converged": all(r["status"] in (R.OK, R.RECYCLE_EMPTY) for r in res)}
         S.destroy()
-    out["max_rel_diff_fp32_refined_vs_fp64"] = max(
-        float(torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0)) for x0, x1 in zip(sols["fp64"], sols["fp32_refined"]))
+    out["rel_diff_fp32_refined_vs_fp64_per_pair"] = [
+        float("%.3g" % float(torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0)))
+        for x0, x1 in zip(sols["fp64"], sols["fp32_refined"])]
+    out["max_rel_diff_fp32_refined_vs_fp64"] = max(out["rel_diff_fp32_refined_vs_fp64_per_pair"])
     return out
 
 

@@ -69,8 +69,12 @@ typedef enum {
                               inner solve fails twice in a row (no residual reduction, even
                               without a recycle space; an inner residual above 1e6 ||b||; or
                               no new residual minimum for max(1000, 25 s) iterations),
-                              the handle solves this and later pairs with FP64 RBiCG from the
-                              refined iterate (rbicg_result.fallback = 2) until rbicg_reset */
+                              the handle continues the refinement of this and later pairs with
+                              FP64 RBiCG correction solves (A d = r from d = 0, to the relative
+                              tolerance that brings r to tol, at least 1e-13), which reach tol
+                              in the FP64 true residual where one FP64 solve of the whole system
+                              can stop short of it (rbicg_result.fallback = 2), until
+                              rbicg_reset */
 } rbicg_precision;
 
 /* Solver parameters.  Defaults (rbicg_default_params): k = 10, s = 40, max_itn = 20000,
@@ -117,7 +121,7 @@ typedef struct {
                               the recycle space may be recomputed only for some systems of a
                               sequence, e.g. every fifth IRKA step).  Changeable between pairs
                               with rbicg_set_refresh. */
-  int setup_blocks;        /* blocks of the refresh's Gram products (0: the default, 2 x SMs);
+  int setup_blocks;        /* blocks of the refresh's Gram products (0: the default, 8 x SMs);
                               rbicg_autotune_params picks one by timed trials */
   int graphs;              /* 1 (default): each cycle's iteration launches run as one CUDA graph;
                               0: launched one by one */
@@ -192,8 +196,10 @@ rbicg_status rbicg_solve_batch(rbicg_handle *hs, const rbicg_csr *const *As, con
  * submit time and leave when they finish, between steps.  Each request is one dual pair on its
  * own handle (at most one in flight per handle; at most 32 in flight), and its results are
  * bit-identical to rbicg_solve_pair on that handle: the batched launch gives every request its
- * own blocks, partial sums and reduction order.  FP32_REFINED requests are solved whole inside
- * submit.  The paper has no counterpart (serving layer).  Buffers must stay valid until the
+ * own blocks, partial sums and reduction order.  FP32_REFINED requests step through the same
+ * engine: their FP64 residual and correction steps run between engine steps and their inner
+ * solves advance one cycle per step with the other requests.  The paper has no counterpart
+ * (serving layer).  Buffers must stay valid until the
  * request is polled.  stream: the engine's cudaStream_t (NULL = legacy default stream); the
  * handles' own streams are used again once their requests finish. */
 typedef struct rbicg_engine_s *rbicg_engine;
@@ -219,7 +225,7 @@ rbicg_status rbicg_autotune(const rbicg_params *params, rbicg_dtype dtype, const
                             int *grid_blocks, double *us_per_iter);
 
 /* Autotuner over three launch knobs (no counterpart in the paper): grid_blocks as rbicg_autotune
- * does; then, with that grid, setup_blocks in {1, 2, 4} x SMs and graphs in {1, 0}, each by timing
+ * does; then, with that grid, setup_blocks in {4, 8, 12} x SMs and graphs in {1, 0}, each by timing
  * three cycles of recycled iterations with their refreshes (k, s from params, tolerance 0, on a
  * private stream, from a random start).  *out = *params with the three fields set to the fastest
  * (the grid from the cache when rbicg_autotune already tuned this shape); *us_per_iter (may be

@@ -245,8 +245,11 @@ struct Solver : SolverBase {
     grid = prm.grid_blocks > 0
                ? (int)std::min<int64_t>(prm.grid_blocks, std::max<int64_t>(1, (n + NTHREADS - 1) / NTHREADS))
                : (int)std::max<int64_t>(1, std::min<int64_t>((n + NTHREADS - 1) / NTHREADS, (int64_t)sms * per_sm));
-    // blocks of the refresh's Gram products (rbicg_params.setup_blocks; default 2 x SMs)
-    gram_grid = prm.setup_blocks > 0 ? prm.setup_blocks : 2 * sms;
+    // blocks of the refresh's Gram products (rbicg_params.setup_blocks; default 8 x SMs: a Gram
+    // block's work depends on how many of its column tiles' warps are active, and several waves
+    // of short blocks let the scheduler even that out across the SMs -- 512^2 benchmark sequence,
+    // the Gram run alone: 0.73 TFLOP/s at 2 x SMs, 0.82 at 4 x, 0.92 at 8 x, 0.93 at 12 x)
+    gram_grid = prm.setup_blocks > 0 ? prm.setup_blocks : 8 * sms;
     const int64_t ldv = ((n + 31) / 32) * 32;   // padded vector stride (256-byte aligned slots)
     ring = dmalloc<T>(ldv * R);
     ringt = dmalloc<T>(ldv * R);
@@ -264,8 +267,8 @@ struct Solver : SolverBase {
     st = dmalloc<DevState>(1);
     RB_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
     // Gram partials: one 32 x 32 tile per (row chunk, tile) with at most max(grid, tiles) of them
-    // (36 tiles at 176 x 176 columns), then the SVD input's column-norm partials
-    const size_t gelems = (size_t)std::max(gram_grid, 64) * 64 * 64;
+    // (36 tiles at 176 x 176 columns), then the SVD input's 64 column-norm partials per block
+    const size_t gelems = (size_t)std::max(gram_grid, 64) * (32 * 32 + 64);
     const size_t part_elems = std::max<size_t>(part_elems_for(grid), gelems);
     part = dmalloc<A>(part_elems);
     gpart = dmalloc<A>(gelems);
@@ -893,7 +896,7 @@ struct ImplT : Impl {
   V32* va32 = nullptr;
   T *r64 = nullptr, *rt64 = nullptr;
   T32 *r32 = nullptr, *rt32 = nullptr, *d32 = nullptr, *dt32 = nullptr;
-  T *d64 = nullptr;
+  T *d64 = nullptr, *dt64 = nullptr;
   double* nrm = nullptr;
   double* hnrm = nullptr;
 
@@ -915,7 +918,7 @@ struct ImplT : Impl {
       // recurrence has lost its way (FP64 BiCG residuals of these problems peak near 1e3 ||b||)
       lo->diverge = 1e6;
       lo->stall_window = std::max(1000, 25 * prm.s);
-      r64 = dmalloc<T>(n); rt64 = dmalloc<T>(n); d64 = dmalloc<T>(n);
+      r64 = dmalloc<T>(n); rt64 = dmalloc<T>(n); d64 = dmalloc<T>(n); dt64 = dmalloc<T>(n);
       r32 = dmalloc<T32>(n); rt32 = dmalloc<T32>(n); d32 = dmalloc<T32>(n); dt32 = dmalloc<T32>(n);
       nrm = dmalloc<double>(1024);
       RB_CUDA(cudaMallocHost(&hnrm, sizeof(double) * 1024));
@@ -924,7 +927,7 @@ struct ImplT : Impl {
   ~ImplT() override {
     cudaStreamSynchronize(s);
     if (va32) cudaFree(va32);
-    void* bufs[] = {r64, rt64, d64, r32, rt32, d32, dt32, nrm};
+    void* bufs[] = {r64, rt64, d64, dt64, r32, rt32, d32, dt32, nrm};
     for (void* b : bufs) if (b) cudaFree(b);
     if (hnrm) cudaFreeHost(hnrm);
   }
@@ -961,12 +964,13 @@ struct ImplT : Impl {
     const T* b = nullptr; const T* bt = nullptr; T* x = nullptr; T* xt = nullptr;
     double nb = 0, nbt = 0, rr = 0, rtr = 0;
     int step = 0, total_iters = 0, cycles = 0, rdim = 0, first_inner = -1, inner_cap = 0, status = 0;
+    double prev_rr = -1.0, prev_rtr = -1.0;   // residual norms before the last FP64 correction
     bool retried_plain = false, pc = false, dc = false;
     rbicg_result res{};
   } rs;
 
   rbicg_result solve(const void* bv, const void* btv, void* xv, void* xtv) override {
-    if (!lo || fp64_only) {
+    if (!lo) {
       return solve_fp64(reinterpret_cast<const T*>(bv), reinterpret_cast<const T*>(btv), reinterpret_cast<T*>(xv),
                         reinterpret_cast<T*>(xtv), 0, 0);
     }
@@ -1004,6 +1008,11 @@ struct ImplT : Impl {
     rs.dc = rs.nbt == 0.0 || rs.rtr <= prm.tol * rs.nbt;
     if (rs.pc && rs.dc) { rs.status = RBICG_OK; return finish_refined(); }
     if (rs.step >= prm.refine_max) return finish_refined();
+    if (fp64_only) {
+      // an FP64 correction made no progress on either side: stop (status NOT_CONVERGED)
+      if (rs.prev_rr >= 0.0 && !(rs.rr < 0.9 * rs.prev_rr) && !(rs.rtr < 0.9 * rs.prev_rtr)) return finish_refined();
+      return begin_fp64_correction();
+    }
     launch_convert<T, T32>(r64, r32, n, s);
     launch_convert<T, T32>(rt64, rt32, n, s);
     RB_CUDA(cudaMemsetAsync(d32, 0, sizeof(T32) * n, s));
@@ -1036,11 +1045,9 @@ struct ImplT : Impl {
     if (!usable) {
       if (rs.retried_plain) {
         // the FP32 recurrence does not converge on this problem even without a recycle space:
-        // this handle continues in FP64 RBiCG from the refined iterate
+        // this handle continues the refinement with FP64 RBiCG correction solves
         fp64_only = true;
-        hi->begin(rs.b, rs.bt, rs.x, rs.xt, prm.tol, prm.max_itn, prm.seed);
-        if (!hi->run.done) return REF_FP64;
-        return after_fp64(hi->run_to_end());
+        return begin_fp64_correction();   // the residual of this step is unchanged
       }
       rs.retried_plain = true;
       lo->kU = 0;
@@ -1062,15 +1069,55 @@ struct ImplT : Impl {
     return advance();
   }
 
+  // FP64 correction solve of a handle that fell back: A d = r, A^H dt = rt (r, rt: the FP64
+  // residuals of the refined iterate, left in r64, rt64 by advance()) with FP64 RBiCG from d = 0,
+  // to the relative tolerance that brings the unconverged side(s) to tol (half of it, for margin;
+  // at least 1e-13, at most 0.5).  A correction solve's attainable accuracy is relative to ||r||,
+  // so repeated steps reach tol in the true residual where one FP64 solve of the whole system
+  // stalls at the gap between its recurrence and its true residual.
+  int begin_fp64_correction() {
+    double need = 0.5;
+    if (!rs.pc && rs.rr > 0) need = std::min(need, 0.5 * prm.tol * (rs.nb > 0 ? rs.nb : 1.0) / rs.rr);
+    if (!rs.dc && rs.rtr > 0) need = std::min(need, 0.5 * prm.tol * rs.nbt / rs.rtr);
+    const double tc = std::max(1e-13, need);
+    RB_CUDA(cudaMemsetAsync(d64, 0, sizeof(T) * n, s));
+    RB_CUDA(cudaMemsetAsync(dt64, 0, sizeof(T) * n, s));
+    rs.prev_rr = rs.rr;
+    rs.prev_rtr = rs.rtr;
+    hi->begin(r64, rt64, d64, dt64, tc, prm.max_itn, prm.seed + rs.step);
+    if (!hi->run.done) return REF_FP64;
+    return after_fp64(hi->run_to_end());
+  }
+
+  // an FP64 correction solve ended: apply its correction (if it reduced its own residual) and
+  // go on with the next refinement step
   int after_fp64(const typename Solver<V, T>::PairOut& o) {
+    rs.total_iters += o.iters;
+    rs.cycles += o.cycles;
+    rs.rdim = o.recycle_dim;
+    if (o.status < 0 && o.status != RBICG_ERR_NONFINITE) { rs.status = o.status; return finish_refined(); }
+    const bool usable = o.status != RBICG_ERR_NONFINITE &&
+                        (o.status == RBICG_OK || o.status == RBICG_RECYCLE_EMPTY ||
+                         (o.true_relres < 0.5 && (rs.dc || o.true_relres_dual < 0.5)));
+    if (debug_on())
+      fprintf(stderr, "[rbicg] fp64 correction %d status %d iters %d relres %.3e/%.3e usable %d\n", rs.step,
+              o.status, o.iters, o.true_relres, o.true_relres_dual, (int)usable);
+    if (!usable) return finish_refined();
+    if (!rs.pc) { launch_axpy_inplace<T>(rs.x, d64, n, s); *launches += 1; }
+    if (!rs.dc) { launch_axpy_inplace<T>(rs.xt, dt64, n, s); *launches += 1; }
+    ++rs.step;
+    return advance();
+  }
+
+  // an FP64 handle's solve ended (no refinement): its result as it stands
+  int after_plain(const typename Solver<V, T>::PairOut& o) {
     rbicg_result& res = rs.res;
     res = rbicg_result{};
-    res.iters = rs.total_iters + o.iters; res.cycles = o.cycles; res.recycle_dim = o.recycle_dim;
-    res.refine_steps = rs.step;
+    res.iters = o.iters; res.cycles = o.cycles; res.recycle_dim = o.recycle_dim;
     res.relres = o.relres; res.relres_dual = o.relres_dual;
     res.true_relres = o.true_relres; res.true_relres_dual = o.true_relres_dual;
     res.status = o.status;
-    res.fallback = 2;
+    res.fallback = o.fallback;
     return REF_DONE;
   }
 
@@ -1086,6 +1133,7 @@ struct ImplT : Impl {
     res.true_relres = res.relres;
     res.true_relres_dual = res.relres_dual;
     res.status = rs.status;
+    res.fallback = fp64_only ? 2 : 0;
     return REF_DONE;
   }
 
@@ -1094,11 +1142,11 @@ struct ImplT : Impl {
   static int kind_of_lo() { return traits<T>::cx ? (traits<V>::cx ? 5 : 4) : 3; }
   int refine_begin(const void* b, const void* bt, void* x, void* xt, void** solver, int* kind) override {
     int w;
-    if (!lo || fp64_only) {
+    if (!lo) {
       rs = RefState{};
       hi->begin(reinterpret_cast<const T*>(b), reinterpret_cast<const T*>(bt), reinterpret_cast<T*>(x),
                 reinterpret_cast<T*>(xt), prm.tol, prm.max_itn, prm.seed);
-      w = hi->run.done ? after_fp64(hi->run_to_end()) : REF_FP64;
+      w = hi->run.done ? after_plain(hi->run_to_end()) : REF_FP64;
     } else {
       w = refine_begin_t(reinterpret_cast<const T*>(b), reinterpret_cast<const T*>(bt), reinterpret_cast<T*>(x),
                          reinterpret_cast<T*>(xt));
@@ -1106,7 +1154,7 @@ struct ImplT : Impl {
     return route(w, solver, kind);
   }
   int refine_after(int kind, void** solver, int* kindout) override {
-    const int w = kind >= 3 ? after_inner(lo->end()) : after_fp64(hi->end());
+    const int w = kind >= 3 ? after_inner(lo->end()) : (lo ? after_fp64(hi->end()) : after_plain(hi->end()));
     return route(w, solver, kindout);
   }
   int route(int w, void** solver, int* kind) {
@@ -2217,7 +2265,7 @@ extern "C" rbicg_status rbicg_autotune_params(const rbicg_params* params, rbicg_
   const int sms = num_sms();
   double best_us = 1e300;
   rbicg_status err = RBICG_OK;
-  for (int f : {2, 1, 4}) {
+  for (int f : {8, 4, 12}) {
     for (int gr : {1, 0}) {
       rbicg_params q = best;
       q.setup_blocks = f * sms;

@@ -267,3 +267,22 @@ def test_config1_recycled_pairs_match_oracle(R):
             xs = spla.spsolve(M, b_)
             assert np.abs(a - xs).max() <= 1e-5 * np.abs(xs).max(), j
     assert compared >= 2
+
+
+def test_fp32_refined_fallback_reaches_tol_in_the_true_residual(R):
+    # 512 x 512 at tol 1e-10: the FP32 inner recurrence cannot reduce this residual (BiCG's
+    # residual peaks), so the handle falls back to FP64 correction solves inside the refinement
+    # loop.  The refined iterate must meet tol in the true residual, primal and dual, checked here
+    # with SciPy's own products, whatever the FP64 form's recurrence-stopped solve reaches.
+    seq = I.convdiff_sequence(512, [10.0, 10.0], 1, 0.01, 2000, bt_kind="normal")
+    A, b, bt = seq[0]["A"], seq[0]["b"], seq[0]["bt"]
+    n = A.n
+    As = A.to_scipy()
+    S = R.Solver(n, k=20, s=40, tol=1e-10, precision="fp32_refined", setup_fp32=0)
+    x, xt = _dev(np.zeros(n)), _dev(np.zeros(n))
+    res = S.solve_pair(R.Operator.from_csr(A), _dev(b), _dev(bt), x, xt)
+    assert res["fallback"] == 2 and res["status"] == R.OK, res
+    xr, xtr = x.cpu().numpy(), xt.cpu().numpy()
+    assert _relres(As, xr, b) <= 1.01e-10
+    assert _relres(As.T.tocsr(), xtr, bt) <= 1.01e-10
+    assert abs(res["true_relres"] - _relres(As, xr, b)) <= 1e-12
