@@ -89,16 +89,32 @@ __global__ void __launch_bounds__(256) k_gram(ColList<T> X, ColList<T> Y, int64_
     for (int j = 0; j < 2; ++j) out[(ra + i) * GT + (cb + j)] = acc[i][j] + cvt<A>(loc[i][j]);
 }
 
+// Warp-shuffle sum in a fixed order (xor 16, 8, 4, 2, 1): the same bits whatever the timing.
+__device__ __forceinline__ double warp_sum_fixed(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ cplx<double> warp_sum_fixed(cplx<double> v) {
+  return cplx<double>(warp_sum_fixed(v.re), warp_sum_fixed(v.im));
+}
+
+// G[e] = sum over the row chunks of the partial tiles: one warp per entry, lane l summing chunks
+// l, l + 32, ... in order, then the fixed shuffle tree (the chain is nchunk / 32 long instead of
+// nchunk: with several waves of Gram blocks there are hundreds of chunks)
 template <class A>
 __global__ void k_gram_reduce(const A* part, int nchunk, int ty, int tz, int mx, int my, A* G) {
   const int ntile = ty * tz;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < mx * my; e += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < mx * my; e += gridDim.x * wpb) {
     const int a = e / my, b = e % my;
     const int tile = (a / GT) * tz + (b / GT);
     const int64_t off = (int64_t)tile * GT * GT + (a % GT) * GT + (b % GT);
     A s = A(0.0);
-    for (int c = 0; c < nchunk; ++c) s += part[(int64_t)c * ntile * GT * GT + off];
-    G[e] = s;
+    for (int c = lane; c < nchunk; c += 32) s += part[(int64_t)c * ntile * GT * GT + off];
+    s = warp_sum_fixed(s);
+    if (lane == 0) G[e] = s;
   }
 }
 
@@ -116,8 +132,8 @@ void launch_gram(const ColList<T>& X, const ColList<T>& Y, int64_t n, int fp32, 
     k_gram<T, typename comp_of<T, true>::type><<<g, 256, 0, s>>>(X, Y, n, rpb, (A*)part);
   else
     k_gram<T, T><<<g, 256, 0, s>>>(X, Y, n, rpb, (A*)part);
-  k_gram_reduce<A><<<std::max(1, std::min(64, (X.m * Y.m + 255) / 256)), 256, 0, s>>>((const A*)part, nchunk, ty,
-                                                                                     tz, X.m, Y.m, G);
+  k_gram_reduce<A><<<std::max(1, std::min(1024, (X.m * Y.m + 7) / 8)), 256, 0, s>>>((const A*)part, nchunk, ty, tz,
+                                                                                   X.m, Y.m, G);
 }
 
 // ------------------------------------------------------------------------------------
@@ -152,11 +168,16 @@ __global__ void k_svd_pack(const double* part, int nblk, const A* G, int k, int 
   for (int e = threadIdx.x; e < ld2 * ld2; e += blockDim.x) S2[e] = zd(0.0);
   __syncthreads();
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) S2[(e / k) * ld2 + e % k] = to_zd(G[e]);
-  for (int c = threadIdx.x; c < 2 * k; c += blockDim.x) {
+  // column sums of the blocks' partials: one warp per column, fixed order (see k_gram_reduce)
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int c = threadIdx.x >> 5; c < 2 * k; c += wpb) {
     double sacc = 0.0;
-    for (int b = 0; b < nblk; ++b) sacc += part[(int64_t)b * 64 + c];
-    if (c < k) S2[(kmax + c) * ld2 + c] = zd(sacc);              // ||C e_c||^2
-    else S2[(c - k) * ld2 + kmax + (c - k)] = zd(sacc);            // ||Ct e_c||^2
+    for (int b = lane; b < nblk; b += 32) sacc += part[(int64_t)b * 64 + c];
+    sacc = warp_sum_fixed(sacc);
+    if (lane == 0) {
+      if (c < k) S2[(kmax + c) * ld2 + c] = zd(sacc);              // ||C e_c||^2
+      else S2[(c - k) * ld2 + kmax + (c - k)] = zd(sacc);            // ||Ct e_c||^2
+    }
   }
 }
 
