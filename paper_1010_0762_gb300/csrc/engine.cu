@@ -370,6 +370,12 @@ struct Solver : SolverBase {
     op.tva = tva;
     op.shared = shared;
     if (!shared) { trp_own = trp; tci_own = tci; }
+    // bandwidth for phase 1's staging of p (-1 when it cannot be read: no staging)
+    int bw = -1;
+    if (csr_bandwidth(op.n, op.rp, op.ci, iflag, s, &bw) != 0) bw = -1;
+    op.bw = bw;
+    op.stage_rows = 0;
+    prepare_phase1<V, T>();
     op_ready = 1;
     pending_start = 1;
   }

@@ -79,6 +79,9 @@ struct OpArgs {
   const int* trp; const int* tci; const V* tva;  // A^H, CSR (conjugated transposed values)
   int shared;                                    // trp == rp and tci == ci
   int has_shift; double sh_re, sh_im;
+  int bw = -1;          // bandwidth max |j - i| over the nonzeros (the same for A^H); <= 0: unknown
+  int stage_rows = 0;   // phase 1 (one solve's launch, real types): rows of p and pt its dynamic
+                        // shared memory holds per side; 0: no staging
 };
 
 // Vectors of one solve.
@@ -149,6 +152,11 @@ template <class V>
 int build_adjoint(int n, const int* rp, const int* ci, const V* va, int** trp, int** tci, V** tva,
                   int* shared, int* flag_dev, cudaStream_t s);   // returns 0 or a cuda error
 int validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* flag_dev, cudaStream_t s);
+// bandwidth of a CSR pattern (max |col - row| over its nonzeros) into *bw; returns 0 or a cuda error
+int csr_bandwidth(int n, const int* rp, const int* ci, int* flag_dev, cudaStream_t s, int* bw);
+// sets the phase-1 kernels' dynamic shared memory limit (call outside stream capture)
+template <class V, class T>
+void prepare_phase1();
 
 // ---- launchers (kernels_basis.cu) ----
 template <class T>

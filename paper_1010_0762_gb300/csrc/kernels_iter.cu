@@ -336,56 +336,138 @@ __device__ __forceinline__ void phase1_body(const OpArgs<V> op, const VecArgs<T>
   A pq = A(0.0), nq = A(0.0), npt = A(0.0);
   int r0, r1;
   block_rows(op.n, g, r0, r1);
-  for (int base = r0 + warp * 32; base < r1; base += NTHREADS) {
-    const int row = base + lane;
-    T z = T(0), zt = T(0);
-    if (row < r1) {
-      SpAcc<T> za, zta;
-      const int e0 = op.rp[row], e1 = op.rp[row + 1];
-      if (op.shared) {
-        for (int e = e0; e < e1; ++e) {
-          const int j = op.ci[e];
-          za.add(op.va[e], r[j] + beta * po[j]);
-          zta.add(op.tva[e], rt[j] + cbeta * pto[j]);
+  // Staged (one solve's launch, real types, when the launch gives the dynamic shared memory):
+  // the block first forms p_i = r_{i-1} + beta p_{i-1} and pt_i for its rows and the op.bw rows
+  // on either side -- every column its rows' nonzeros can reach -- in shared memory, and stores
+  // its own rows once; the SpMV then gathers p from there instead of forming r_j + beta p_j again
+  // for every nonzero.  The same expressions give the same values, so the results are unchanged.
+  bool staged = false;
+  int slo = 0;
+  if constexpr (!traits<T>::cx) {
+    if (op.stage_rows > 0 && op.bw > 0 && r1 > r0) {
+      slo = r0 - op.bw > 0 ? r0 - op.bw : 0;
+      const int shi = r1 + op.bw < op.n ? r1 + op.bw : op.n;
+      staged = shi - slo <= op.stage_rows;   // block-uniform
+      if (staged) {
+        extern __shared__ __align__(16) unsigned char rb_phase1_dyn[];
+        T* __restrict__ ps = reinterpret_cast<T*>(rb_phase1_dyn);
+        T* __restrict__ pts = ps + op.stage_rows;
+        for (int row = slo + (int)threadIdx.x; row < shi; row += NTHREADS) {
+          const T prow = r[row] + beta * po[row];
+          const T ptrow = rt[row] + cbeta * pto[row];
+          ps[row - slo] = prow;
+          pts[row - slo] = ptrow;
+          if (row >= r0 && row < r1) {
+            pn[row] = prow;
+            ptn[row] = ptrow;
+          }
         }
-      } else {
-        for (int e = e0; e < e1; ++e) {
-          const int j = op.ci[e];
-          za.add(op.va[e], r[j] + beta * po[j]);
-        }
-        const int f0 = op.trp[row], f1 = op.trp[row + 1];
-        for (int e = f0; e < f1; ++e) {
-          const int j = op.tci[e];
-          zta.add(op.tva[e], rt[j] + cbeta * pto[j]);
-        }
-      }
-      const T prow = r[row] + beta * po[row];
-      const T ptrow = rt[row] + cbeta * pto[row];
-      pn[row] = prow;
-      ptn[row] = ptrow;
-      if (op.has_shift) { z = za.shifted(sh, prow); zt = zta.shifted(shc, ptrow); }
-      else { z = za.value(); zt = zta.value(); }
-      v.z[row] = z;
-      v.zt[row] = zt;
-      if (LD == 0) alpha_terms(pq, nq, npt, ptrow, z);
-    }
-    if (LD > 0) {
-      zs[warp][lane] = z;
-      zts[warp][lane] = zt;
-      __syncwarp();
-      const int nvalid = r1 - base < 32 ? r1 - base : 32;
-      const T* __restrict__ ctb = v.Ct + (int64_t)base * LDA;
-      const T* __restrict__ cb = v.C + (int64_t)base * LDA;
+        __syncthreads();
+        for (int base = r0 + warp * 32; base < r1; base += NTHREADS) {
+          const int row = base + lane;
+          T z = T(0), zt = T(0);
+          if (row < r1) {
+            SpAcc<T> za, zta;
+            const int e0 = op.rp[row], e1 = op.rp[row + 1];
+            if (op.shared) {
+              for (int e = e0; e < e1; ++e) {
+                const int j = op.ci[e];
+                za.add(op.va[e], ps[j - slo]);
+                zta.add(op.tva[e], pts[j - slo]);
+              }
+            } else {
+              for (int e = e0; e < e1; ++e) {
+                const int j = op.ci[e];
+                za.add(op.va[e], ps[j - slo]);
+              }
+              const int f0 = op.trp[row], f1 = op.trp[row + 1];
+              for (int e = f0; e < f1; ++e) {
+                const int j = op.tci[e];
+                zta.add(op.tva[e], pts[j - slo]);
+              }
+            }
+            const T prow = ps[row - slo];
+            const T ptrow = pts[row - slo];
+            if (op.has_shift) { z = za.shifted(sh, prow); zt = zta.shifted(shc, ptrow); }
+            else { z = za.value(); zt = zta.value(); }
+            v.z[row] = z;
+            v.zt[row] = zt;
+            if (LD == 0) alpha_terms(pq, nq, npt, ptrow, z);
+          }
+          if (LD > 0) {
+            zs[warp][lane] = z;
+            zts[warp][lane] = zt;
+            __syncwarp();
+            const int nvalid = r1 - base < 32 ? r1 - base : 32;
+            const T* __restrict__ ctb = v.Ct + (int64_t)base * LDA;
+            const T* __restrict__ cb = v.C + (int64_t)base * LDA;
 #pragma unroll
-      for (int t = 0; t < LDA; ++t) {
-        const int e = lane + 32 * t;
-        const int rr = e / LDA;
-        if (rr < nvalid) {
-          a1[t % P] += cmul(ctb[e], zs[warp][rr]);
-          a2[t % P] += cmul(cb[e], zts[warp][rr]);
+            for (int t = 0; t < LDA; ++t) {
+              const int e = lane + 32 * t;
+              const int rr = e / LDA;
+              if (rr < nvalid) {
+                a1[t % P] += cmul(ctb[e], zs[warp][rr]);
+                a2[t % P] += cmul(cb[e], zts[warp][rr]);
+              }
+            }
+            __syncwarp();
+          }
         }
       }
-      __syncwarp();
+    }
+  }
+  if (!staged) {
+    for (int base = r0 + warp * 32; base < r1; base += NTHREADS) {
+      const int row = base + lane;
+      T z = T(0), zt = T(0);
+      if (row < r1) {
+        SpAcc<T> za, zta;
+        const int e0 = op.rp[row], e1 = op.rp[row + 1];
+        if (op.shared) {
+          for (int e = e0; e < e1; ++e) {
+            const int j = op.ci[e];
+            za.add(op.va[e], r[j] + beta * po[j]);
+            zta.add(op.tva[e], rt[j] + cbeta * pto[j]);
+          }
+        } else {
+          for (int e = e0; e < e1; ++e) {
+            const int j = op.ci[e];
+            za.add(op.va[e], r[j] + beta * po[j]);
+          }
+          const int f0 = op.trp[row], f1 = op.trp[row + 1];
+          for (int e = f0; e < f1; ++e) {
+            const int j = op.tci[e];
+            zta.add(op.tva[e], rt[j] + cbeta * pto[j]);
+          }
+        }
+        const T prow = r[row] + beta * po[row];
+        const T ptrow = rt[row] + cbeta * pto[row];
+        pn[row] = prow;
+        ptn[row] = ptrow;
+        if (op.has_shift) { z = za.shifted(sh, prow); zt = zta.shifted(shc, ptrow); }
+        else { z = za.value(); zt = zta.value(); }
+        v.z[row] = z;
+        v.zt[row] = zt;
+        if (LD == 0) alpha_terms(pq, nq, npt, ptrow, z);
+      }
+      if (LD > 0) {
+        zs[warp][lane] = z;
+        zts[warp][lane] = zt;
+        __syncwarp();
+        const int nvalid = r1 - base < 32 ? r1 - base : 32;
+        const T* __restrict__ ctb = v.Ct + (int64_t)base * LDA;
+        const T* __restrict__ cb = v.C + (int64_t)base * LDA;
+#pragma unroll
+        for (int t = 0; t < LDA; ++t) {
+          const int e = lane + 32 * t;
+          const int rr = e / LDA;
+          if (rr < nvalid) {
+            a1[t % P] += cmul(ctb[e], zs[warp][rr]);
+            a2[t % P] += cmul(cb[e], zts[warp][rr]);
+          }
+        }
+        __syncwarp();
+      }
     }
   }
   pdl_release();
@@ -571,7 +653,8 @@ __device__ __forceinline__ int batch_slot(const BatchArgs<V, T>* ba) {
   template <TPARAMS>                                                                                    \
   __global__ void __launch_bounds__(NTHREADS, MINB) NAME##_b(const BatchArgs<V, T>* __restrict__ ba) { \
     const int r = batch_slot(ba);                                                                       \
-    const OpArgs<V> op = ba->op[r];                                                                     \
+    OpArgs<V> op = ba->op[r];                                                                           \
+    op.stage_rows = 0;   /* batched launches give no dynamic shared memory */                          \
     const VecArgs<T> v = ba->v[r];                                                                      \
     BODY<TARGS>(op, v, ba->st[r], reinterpret_cast<typename traits<T>::acc*>(ba->part[r]),             \
                 Blk{(int)blockIdx.x - ba->start[r], ba->start[r + 1] - ba->start[r]});                  \
@@ -823,6 +906,19 @@ __global__ void k_validate(int n, int64_t nnz, const int* rp, const int* ci, int
   }
 }
 
+// bandwidth: max |j - i| over the nonzeros (columns sorted, so a row's first and last decide)
+__global__ void k_bandwidth(int n, const int* rp, const int* ci, int* bw) {
+  int m = 0;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+    const int e0 = rp[row], e1 = rp[row + 1];
+    if (e1 > e0) {
+      const int lo = row - ci[e0], hi = ci[e1 - 1] - row;
+      m = max(m, max(lo, hi));
+    }
+  }
+  if (m > 0) atomicMax(bw, m);
+}
+
 RB_HD double conjv(double a) { return a; }
 RB_HD float conjv(float a) { return a; }
 template <class R> RB_HD cplx<R> conjv(cplx<R> a) { return conjg(a); }
@@ -940,11 +1036,11 @@ static bool pdl_enabled() {
   return on;
 }
 template <class... KArgs, class... Args>
-static void launch_phase_kernel(void (*k)(KArgs...), int grid, cudaStream_t s, Args... args) {
+static void launch_phase_kernel(void (*k)(KArgs...), int grid, cudaStream_t s, size_t dyn, Args... args) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(NTHREADS);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = dyn;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -954,13 +1050,80 @@ static void launch_phase_kernel(void (*k)(KArgs...), int grid, cudaStream_t s, A
   cudaLaunchKernelEx(&cfg, k, args...);
 }
 
+// Phase-1 staging (see phase1_body): the dynamic shared memory a launch may give, from the SM's
+// shared memory shared by the blocks that the grid puts on one SM and each instantiation's own
+// static shared memory.  prepare_phase1() reads the static sizes and raises the kernels' dynamic
+// limit once per (V, T), outside any stream capture; launches before it stage nothing.
+constexpr int PHASE1_LDS[9] = {0, 4, 8, 12, 16, 20, 24, 28, 32};
 template <class V, class T>
-void launch_phase1(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
+struct Phase1Smem {
+  static bool ready;
+  static int static_bytes[9];
+  static int sm_bytes;   // shared memory per SM usable by blocks
+  static int sms;
+};
+template <class V, class T> bool Phase1Smem<V, T>::ready = false;
+template <class V, class T> int Phase1Smem<V, T>::static_bytes[9] = {};
+template <class V, class T> int Phase1Smem<V, T>::sm_bytes = 0;
+template <class V, class T> int Phase1Smem<V, T>::sms = 1;
+
+template <class V, class T, int L>
+static void prepare_one(int i, int max_dyn) {
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, k_phase1<V, T, L>);
+  Phase1Smem<V, T>::static_bytes[i] = (int)fa.sharedSizeBytes;
+  cudaFuncSetAttribute(k_phase1<V, T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       max_dyn - (int)fa.sharedSizeBytes);
+}
+
+template <class V, class T>
+void prepare_phase1() {
+  if (Phase1Smem<V, T>::ready || traits<T>::cx) return;
+  int dev = 0, per_block = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&Phase1Smem<V, T>::sms, cudaDevAttrMultiProcessorCount, dev);
+  Phase1Smem<V, T>::sm_bytes = per_sm;
+  prepare_one<V, T, 0>(0, per_block);
+  prepare_one<V, T, 4>(1, per_block);
+  prepare_one<V, T, 8>(2, per_block);
+  prepare_one<V, T, 12>(3, per_block);
+  prepare_one<V, T, 16>(4, per_block);
+  prepare_one<V, T, 20>(5, per_block);
+  prepare_one<V, T, 24>(6, per_block);
+  prepare_one<V, T, 28>(7, per_block);
+  prepare_one<V, T, 32>(8, per_block);
+  Phase1Smem<V, T>::ready = cudaGetLastError() == cudaSuccess;
+}
+
+// rows per side a launch stages: the largest block's rows plus bw on either side, if that fits
+// beside the static shared memory of the blocks one SM holds (1 KB reserved per block); else 0
+template <class V, class T>
+static int phase1_stage_rows(const OpArgs<V>& op, int grid, int li) {
+  if (traits<T>::cx || !Phase1Smem<V, T>::ready || op.bw <= 0 || op.n <= 0 || grid <= 0) return 0;
+  static const bool off = getenv("RBICG_NO_STAGE") != nullptr;   // for tests and measurements
+  if (off) return 0;
+  const int64_t nch = ((int64_t)op.n + 31) / 32;
+  const int64_t rows = std::min<int64_t>(op.n, (nch + grid - 1) / grid * 32 + 2 * (int64_t)op.bw);
+  const int per_sm_blocks = (grid + Phase1Smem<V, T>::sms - 1) / Phase1Smem<V, T>::sms;
+  const int64_t budget = Phase1Smem<V, T>::sm_bytes / std::max(1, per_sm_blocks) - 1024 -
+                         Phase1Smem<V, T>::static_bytes[li];
+  return rows * 2 * (int64_t)sizeof(T) <= budget ? (int)rows : 0;
+}
+
+template <class V, class T>
+void launch_phase1(const OpArgs<V>& op_in, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
                    cudaStream_t s) {
   typedef typename traits<T>::acc A;
   // kt == 0: no recycle space (no projection); otherwise dispatch on the bases' row stride
   const int ld = kt == 0 ? 0 : v.ldc;
-#define RB_CALL(L) launch_phase_kernel(k_phase1<V, T, L>, grid, s, op, v, st, (A*)part)
+  int li = 0;
+  while (li < 8 && PHASE1_LDS[li] < ld) ++li;
+  OpArgs<V> op = op_in;
+  op.stage_rows = phase1_stage_rows<V, T>(op, grid, li);
+  const size_t dyn = (size_t)op.stage_rows * 2 * sizeof(T);
+#define RB_CALL(L) launch_phase_kernel(k_phase1<V, T, L>, grid, s, dyn, op, v, st, (A*)part)
   switch (ld) {
     case 0: RB_CALL(0); break;
     case 4: RB_CALL(4); break;
@@ -978,7 +1141,7 @@ template <class V, class T>
 void launch_phase2(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
                    cudaStream_t s) {
   typedef typename traits<T>::acc A;
-#define RB_CALL(K) launch_phase_kernel(k_phase2<V, T, K>, grid, s, op, v, st, (A*)part)
+#define RB_CALL(K) launch_phase_kernel(k_phase2<V, T, K>, grid, s, (size_t)0, op, v, st, (A*)part)
   RB_KT_DISPATCH(kt, RB_CALL)
 #undef RB_CALL
 }
@@ -986,11 +1149,11 @@ template <class V, class T>
 void launch_phase3(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int grid,
                    cudaStream_t s) {
   typedef typename traits<T>::acc A;
-  launch_phase_kernel(k_phase3<V, T>, grid, s, op, v, st, (A*)part);
+  launch_phase_kernel(k_phase3<V, T>, grid, s, (size_t)0, op, v, st, (A*)part);
 }
 template <class V, class T>
 void launch_phase1_batch(const BatchArgs<V, T>* ba, int blocks, int ld, cudaStream_t s) {
-#define RB_CALL(L) launch_phase_kernel(k_phase1_b<V, T, L>, blocks, s, ba)
+#define RB_CALL(L) launch_phase_kernel(k_phase1_b<V, T, L>, blocks, s, (size_t)0, ba)
   switch (ld) {
     case 0: RB_CALL(0); break;
     case 4: RB_CALL(4); break;
@@ -1006,13 +1169,13 @@ void launch_phase1_batch(const BatchArgs<V, T>* ba, int blocks, int ld, cudaStre
 }
 template <class V, class T>
 void launch_phase2_batch(const BatchArgs<V, T>* ba, int blocks, int kt, cudaStream_t s) {
-#define RB_CALL(K) launch_phase_kernel(k_phase2_b<V, T, K>, blocks, s, ba)
+#define RB_CALL(K) launch_phase_kernel(k_phase2_b<V, T, K>, blocks, s, (size_t)0, ba)
   RB_KT_DISPATCH(kt, RB_CALL)
 #undef RB_CALL
 }
 template <class V, class T>
 void launch_phase3_batch(const BatchArgs<V, T>* ba, int blocks, cudaStream_t s) {
-  launch_phase_kernel(k_phase3_b<V, T>, blocks, s, ba);
+  launch_phase_kernel(k_phase3_b<V, T>, blocks, s, (size_t)0, ba);
 }
 template <class V, class T>
 void launch_init(const OpArgs<V>& op, const VecArgs<T>& v, DevState* st, void* part, int kt, int grid,
@@ -1049,6 +1212,13 @@ int validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* flag_dev
   cudaMemsetAsync(flag_dev, 0, sizeof(int), s);
   k_validate<<<std::max(1, std::min((n + 255) / 256, 1024)), 256, 0, s>>>(n, nnz, rp, ci, flag_dev);
   return (int)cudaGetLastError();
+}
+
+int csr_bandwidth(int n, const int* rp, const int* ci, int* flag_dev, cudaStream_t s, int* bw) {
+  cudaMemsetAsync(flag_dev, 0, sizeof(int), s);
+  k_bandwidth<<<std::max(1, std::min((n + 255) / 256, 1024)), 256, 0, s>>>(n, rp, ci, flag_dev);
+  cudaMemcpyAsync(bw, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+  return (int)cudaStreamSynchronize(s);
 }
 
 template <class V>
@@ -1091,6 +1261,7 @@ int build_adjoint(int n, const int* rp, const int* ci, const V* va, int** trp, i
 // explicit instantiations
 // ------------------------------------------------------------------------------------
 #define RB_INST_VT(V, T)                                                                                  \
+  template void prepare_phase1<V, T>();                                                                     \
   template void launch_phase1<V, T>(const OpArgs<V>&, const VecArgs<T>&, DevState*, void*, int, int,       \
                                     cudaStream_t);                                                         \
   template void launch_phase2<V, T>(const OpArgs<V>&, const VecArgs<T>&, DevState*, void*, int, int,       \

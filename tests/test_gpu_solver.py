@@ -2,6 +2,8 @@
 (iterate-by-iterate at early iteration counts, final solutions, recycle spaces by principal
 angles, iteration counts over sequences), plus the FP32-refined path, complex shifted
 systems, the random restart, batches and status codes."""
+import os
+
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -505,3 +507,47 @@ def test_refresh_every_matches_oracle(R):
         assert abs(res["iters"] - ref[j].iters) <= 2, (j, res["iters"], ref[j].iters)
         assert (res["cycles"] == 0) == (ref[j].cycles == 0) == (j % 2 == 1)
         assert _rel(x, ref[j].x) < 1e-8
+
+
+_STAGE_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1010_0762_gb300 import rbicg as R, inputs as I
+seq = I.convdiff_sequence(128, [10.0, 10.0], 2, 0.01, 4100, bt_kind="normal")
+n = seq[0]["A"].n
+S = R.Solver(n, k=10, s=40, tol=1e-10, setup_fp32=0)
+out = []
+for pr in seq:
+    x = torch.zeros(n, dtype=torch.float64, device="cuda"); xt = torch.zeros_like(x)
+    res = S.solve_pair(R.Operator.from_csr(pr["A"]), torch.as_tensor(pr["b"], device="cuda"),
+                       torch.as_tensor(pr["bt"], device="cuda"), x, xt)
+    out += [x.cpu().numpy(), xt.cpu().numpy(),
+            np.array([res["iters"], res["recycle_dim"], res["status"], res["fallback"]])]
+np.savez(sys.argv[2], *out)
+"""
+
+
+def test_phase1_staging_is_bit_identical(R, tmp_path):
+    # Phase 1 stages p of a block's rows and their bandwidth halo in shared memory (real types,
+    # one solve's launches) instead of forming r_j + beta p_j for every nonzero; the same
+    # expressions must give the same bits.  The same plain and recycled solves (128^2: 64 blocks
+    # of 256 rows, bandwidth 128) with the staging switched off by RBICG_NO_STAGE and on.
+    import subprocess
+    import sys as _sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for off in (True, False):
+        env = dict(os.environ)
+        env.pop("RBICG_NO_STAGE", None)
+        if off:
+            env["RBICG_NO_STAGE"] = "1"
+        f = str(tmp_path / ("off.npz" if off else "on.npz"))
+        subprocess.run([_sys.executable, "-c", _STAGE_SCRIPT, root, f], env=env, check=True, timeout=600)
+        outs.append(np.load(f))
+    a, b = outs
+    assert a.files == b.files
+    for key in a.files:
+        assert np.array_equal(a[key], b[key]), key
+    # the second pair started with a recycle space (phase 1 with projections): it kept it to the
+    # end, or the stagnation guard dropped it mid-solve (recycle_dim then reads 0, fallback 1)
+    assert a["arr_5"][2] != R.RECYCLE_EMPTY and (a["arr_5"][1] > 0 or a["arr_5"][3] == 1), a["arr_5"]
