@@ -89,6 +89,58 @@ __global__ void __launch_bounds__(256) k_gram(ColList<T> X, ColList<T> Y, int64_
     for (int j = 0; j < 2; ++j) out[(ra + i) * GT + (cb + j)] = acc[i][j] + cvt<A>(loc[i][j]);
 }
 
+// Small Grams (X and Y at most GT columns, at most 2 entries per thread; the Section 4.3 SVD input
+// C~_j^H C_j is k x k): thread t owns entries t and t + 256 of the mx x my block, so no FP64
+// multiply-add is spent on padding (the 8 x 16 warp sub-tiles of k_gram compute 24 x 32 entries
+// for a 20 x 20 Gram).  Staging, row order and flushes are those of k_gram, so every entry is
+// the same sum in the same order; the partial tile has k_gram's layout.
+template <class T, class Cm>
+__global__ void __launch_bounds__(256) k_gram_small(ColList<T> X, ColList<T> Y, int64_t n, int64_t rows_per_block,
+                                                    typename traits<T>::acc* part) {
+  typedef typename traits<T>::acc A;
+  __shared__ Cm xs[GROWS][GT];
+  __shared__ Cm ys[GROWS][GT];
+  const int mx = X.m, my = Y.m, ne = mx * my;
+  const int e0 = threadIdx.x, e1 = threadIdx.x + 256;
+  const int a0 = e0 < ne ? e0 / my : 0, b0 = e0 < ne ? e0 % my : 0;
+  const int a1 = e1 < ne ? e1 / my : 0, b1 = e1 < ne ? e1 % my : 0;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
+  A acc0 = A(0.0), acc1 = A(0.0);
+  Cm loc0 = Cm(0), loc1 = Cm(0);
+  int step = 0;
+  for (int64_t rb0 = r0; rb0 < r1; rb0 += GROWS) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < GROWS * GT; e += 256) {
+      const int rr = e % GROWS, cc = e / GROWS;
+      const int64_t row = rb0 + rr;
+      Cm xv = Cm(0), yv = Cm(0);
+      if (row < r1) {
+        if (cc < mx) { const ColSrc<T> sx = X.c[cc]; xv = cvt<Cm>(sx.p[row * sx.ld]); }
+        if (cc < my) { const ColSrc<T> sy = Y.c[cc]; yv = cvt<Cm>(sy.p[row * sy.ld]); }
+      }
+      xs[rr][cc] = xv;
+      ys[rr][cc] = yv;
+    }
+    __syncthreads();
+    if (e0 < ne) {
+#pragma unroll 4
+      for (int rr = 0; rr < GROWS; ++rr) {
+        loc0 += cmul(xs[rr][a0], ys[rr][b0]);
+        if (e1 < ne) loc1 += cmul(xs[rr][a1], ys[rr][b1]);
+      }
+    }
+    if (++step == GFLUSH) {
+      step = 0;
+      acc0 += cvt<A>(loc0); loc0 = Cm(0);
+      acc1 += cvt<A>(loc1); loc1 = Cm(0);
+    }
+  }
+  A* out = part + (int64_t)blockIdx.x * (GT * GT);
+  if (e0 < ne) out[a0 * GT + b0] = acc0 + cvt<A>(loc0);
+  if (e1 < ne) out[a1 * GT + b1] = acc1 + cvt<A>(loc1);
+}
+
 // Warp-shuffle sum in a fixed order (xor 16, 8, 4, 2, 1): the same bits whatever the timing.
 __device__ __forceinline__ double warp_sum_fixed(double v) {
 #pragma unroll
@@ -128,7 +180,12 @@ void launch_gram(const ColList<T>& X, const ColList<T>& Y, int64_t n, int fp32, 
   rpb = ((rpb + GROWS - 1) / GROWS) * GROWS;
   nchunk = (int)((n + rpb - 1) / rpb);
   dim3 g(nchunk, ty, tz);
-  if (fp32)
+  const bool small = X.m <= GT && Y.m <= GT && X.m * Y.m <= 512;
+  if (small && fp32)
+    k_gram_small<T, typename comp_of<T, true>::type><<<g, 256, 0, s>>>(X, Y, n, rpb, (A*)part);
+  else if (small)
+    k_gram_small<T, T><<<g, 256, 0, s>>>(X, Y, n, rpb, (A*)part);
+  else if (fp32)
     k_gram<T, typename comp_of<T, true>::type><<<g, 256, 0, s>>>(X, Y, n, rpb, (A*)part);
   else
     k_gram<T, T><<<g, 256, 0, s>>>(X, Y, n, rpb, (A*)part);
