@@ -597,11 +597,46 @@ __device__ __forceinline__ void phase3_body(const OpArgs<V> op, const VecArgs<T>
   A rho = A(0.0), n1 = A(0.0), n2 = A(0.0);
   int r0, r1;
   block_rows(op.n, g, r0, r1);
-  for (int row = r0 + threadIdx.x; row < r1; row += NTHREADS) {
-    v.x[row] = v.x[row] + al * p[row];
-    v.xt[row] = v.xt[row] + cal * pt[row];
-    const T a = ro[row] - al * v.z[row];
-    const T b = rto[row] - cal * v.zt[row];
+  T* __restrict__ x = v.x;
+  T* __restrict__ xt = v.xt;
+  const T* __restrict__ q = v.z;
+  const T* __restrict__ qt = v.zt;
+  int row = r0 + (int)threadIdx.x;
+  // Real types take two rows a thread per step with all their loads issued first (the pointers
+  // above do not alias), so more loads are in flight; the rows and the sums keep their order.
+  constexpr int U = sizeof(T) <= 8 ? 2 : 1;
+  if (U == 2) {
+    for (; row + NTHREADS < r1; row += 2 * NTHREADS) {
+      const int w = row + NTHREADS;
+      const T x0 = x[row], x1 = x[w], p0 = p[row], p1 = p[w];
+      const T xt0 = xt[row], xt1 = xt[w], pt0 = pt[row], pt1 = pt[w];
+      const T ro0 = ro[row], ro1 = ro[w], q0 = q[row], q1 = q[w];
+      const T rto0 = rto[row], rto1 = rto[w], qt0 = qt[row], qt1 = qt[w];
+      x[row] = x0 + al * p0;
+      xt[row] = xt0 + cal * pt0;
+      const T a0 = ro0 - al * q0;
+      const T b0 = rto0 - cal * qt0;
+      rn[row] = a0;
+      rtn[row] = b0;
+      rho += cmul(cvt<A>(b0), cvt<A>(a0));
+      n1 += A((double)abs2(a0));
+      n2 += A((double)abs2(b0));
+      x[w] = x1 + al * p1;
+      xt[w] = xt1 + cal * pt1;
+      const T a1 = ro1 - al * q1;
+      const T b1 = rto1 - cal * qt1;
+      rn[w] = a1;
+      rtn[w] = b1;
+      rho += cmul(cvt<A>(b1), cvt<A>(a1));
+      n1 += A((double)abs2(a1));
+      n2 += A((double)abs2(b1));
+    }
+  }
+  for (; row < r1; row += NTHREADS) {
+    x[row] = x[row] + al * p[row];
+    xt[row] = xt[row] + cal * pt[row];
+    const T a = ro[row] - al * q[row];
+    const T b = rto[row] - cal * qt[row];
     rn[row] = a;
     rtn[row] = b;
     rho += cmul(cvt<A>(b), cvt<A>(a));
@@ -662,7 +697,7 @@ __device__ __forceinline__ int batch_slot(const BatchArgs<V, T>* ba) {
 #define RB_COMMA ,
 RB_PHASE_KERNELS(k_phase1, phase1_body, 3, class V RB_COMMA class T RB_COMMA int LD, V RB_COMMA T RB_COMMA LD)
 RB_PHASE_KERNELS(k_phase2, phase2_body, 3, class V RB_COMMA class T RB_COMMA int KT, V RB_COMMA T RB_COMMA KT)
-RB_PHASE_KERNELS(k_phase3, phase3_body, 4, class V RB_COMMA class T, V RB_COMMA T)
+RB_PHASE_KERNELS(k_phase3, phase3_body, 3, class V RB_COMMA class T, V RB_COMMA T)
 #undef RB_COMMA
 #undef RB_PHASE_KERNELS
 
