@@ -506,10 +506,8 @@ __device__ __forceinline__ void phase2_body(const OpArgs<V> op, const VecArgs<T>
   __shared__ A red[NW * 4];
   __shared__ A tot[3];
   __shared__ T ze[KA], zet[KA];   // zeta, zetat broadcast from shared memory (few registers)
-  // per warp: an 8-column slice of C (or Ct) for its 32 rows, row stride 9 (conflict-free reads);
-  // real types stage the slices of both sides at once (their loads in flight together)
-  constexpr int NSIDE = (KT > 0 && sizeof(T) <= 8) ? 2 : 1;
-  __shared__ T stg[KT > 0 ? NW : 1][NSIDE][KT > 0 ? 32 * 9 : 1];
+  // per warp: an 8-column slice of C (or Ct) for its 32 rows, row stride 9 (conflict-free reads)
+  __shared__ T stg[KT > 0 ? NW : 1][KT > 0 ? 32 * 9 : 1];
   pdl_wait();
   if (st->done) return;
   const int i = st->iter + 1;
@@ -536,55 +534,27 @@ __device__ __forceinline__ void phase2_body(const OpArgs<V> op, const VecArgs<T>
       // a row are 64 contiguous bytes, so each warp load reads 4 rows in whole sectors.
       const int nvalid = r1 - base < 32 ? r1 - base : 32;
       const int ldk = v.ldc;
-      if constexpr (NSIDE == 2) {
-        T* sg0 = stg[warp][0];
-        T* sg1 = stg[warp][NSIDE - 1];
-        const T* __restrict__ c_src = v.C;
-        const T* __restrict__ ct_src = v.Ct;
+      T* sg = stg[warp];
 #pragma unroll 1
-        for (int c0 = 0; c0 < KA; c0 += 8) {
+      for (int c0 = 0; c0 < KA; c0 += 8) {
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+          const T* __restrict__ src = side == 0 ? v.C : v.Ct;
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int e = lane + 32 * u, rr = e >> 3, cc = c0 + (e & 7);
-            const bool in = rr < nvalid && cc < ldk;
-            const int64_t off = (int64_t)(base + rr) * ldk + cc;
-            sg0[rr * 9 + (e & 7)] = in ? c_src[off] : T(0);
-            sg1[rr * 9 + (e & 7)] = in ? ct_src[off] : T(0);
+            sg[rr * 9 + (e & 7)] = (rr < nvalid && cc < ldk) ? src[(int64_t)(base + rr) * ldk + cc] : T(0);
           }
           __syncwarp();
           if (live) {
+            T acc = side == 0 ? q : qt;
+            const T* zz = side == 0 ? ze : zet;
 #pragma unroll
             for (int cl = 0; cl < 8; ++cl)
-              if (c0 + cl < k) q -= sg0[lane * 9 + cl] * ze[c0 + cl];
-#pragma unroll
-            for (int cl = 0; cl < 8; ++cl)
-              if (c0 + cl < k) qt -= sg1[lane * 9 + cl] * zet[c0 + cl];
+              if (c0 + cl < k) acc -= sg[lane * 9 + cl] * zz[c0 + cl];
+            if (side == 0) q = acc; else qt = acc;
           }
           __syncwarp();
-        }
-      } else {
-        T* sg = stg[warp][0];
-#pragma unroll 1
-        for (int c0 = 0; c0 < KA; c0 += 8) {
-#pragma unroll 1
-          for (int side = 0; side < 2; ++side) {
-            const T* __restrict__ src = side == 0 ? v.C : v.Ct;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int e = lane + 32 * u, rr = e >> 3, cc = c0 + (e & 7);
-              sg[rr * 9 + (e & 7)] = (rr < nvalid && cc < ldk) ? src[(int64_t)(base + rr) * ldk + cc] : T(0);
-            }
-            __syncwarp();
-            if (live) {
-              T acc = side == 0 ? q : qt;
-              const T* zz = side == 0 ? ze : zet;
-#pragma unroll
-              for (int cl = 0; cl < 8; ++cl)
-                if (c0 + cl < k) acc -= sg[lane * 9 + cl] * zz[c0 + cl];
-              if (side == 0) q = acc; else qt = acc;
-            }
-            __syncwarp();
-          }
         }
       }
       if (live) {
