@@ -31,8 +31,9 @@
  *  - Environment switches (read when first needed; none changes any result):
  *    RBICG_NO_GRAPHS: launch each cycle's iteration kernels one by one instead of as a CUDA
  *    graph (profilers then see and select the individual kernels); RBICG_NO_PDL: launch the
- *    iteration kernels without programmatic stream serialization; RBICG_DEBUG: print one
- *    line per solve on stderr.
+ *    iteration kernels without programmatic stream serialization; RBICG_NO_STAGE: the
+ *    dual-SpMV kernel forms each gathered r_j + beta p_j on the fly instead of staging p with
+ *    its bandwidth halo in shared memory; RBICG_DEBUG: print one line per solve on stderr.
  */
 #ifndef RBICG_H
 #define RBICG_H
