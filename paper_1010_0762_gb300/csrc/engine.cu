@@ -1180,7 +1180,7 @@ struct ImplT : Impl {
   bool fp64_only = false;   // FP32_REFINED handle that fell back to FP64 (until rbicg_reset)
 
   void* batch_solver(int* kind) override {
-    if (lo) return nullptr;   // FP32-refined handles are solved one by one
+    if (lo) return nullptr;   // FP32-refined handles go through refine_begin / refine_after
     *kind = traits<T>::cx ? (traits<V>::cx ? 2 : 1) : 0;
     return hi.get();
   }
