@@ -98,6 +98,40 @@ def test_serving_evicts_idle_families_lru_under_the_hbm_budget():
     assert len(srv.resident) <= 2
 
 
+class FailingBackend(FakeBackend):
+    """Family 1's requests end in a BiCG breakdown (status 2) after their steps."""
+
+    def poll(self):
+        out = []
+        for t, res, x in super().poll():
+            fid = self.fid_of_tag[t]
+            out.append((t, {"status": 2 if fid == 1 else 0, "iters": 1}, x))
+        return out
+
+    def submit(self, h, A, b, bt, tag):
+        self.fid_of_tag = getattr(self, "fid_of_tag", {})
+        self.fid_of_tag[tag] = h[0]
+        super().submit(h, A, b, bt, tag)
+
+
+def test_breakdowns_are_reported_and_not_counted_as_solves():
+    # throughput and latency percentiles count converged solves only; the failed ones are
+    # reported by status beside them
+    specs = _specs([8, 10])
+    clk = FakeClock()
+    be = FailingBackend(clk, {0: 2, 1: 4})
+    srv = SV.Server(specs, be, hbm_budget=10**12, s=10, max_in_flight=4)
+    reqs = [SV.Request(i, i % 2, "fp64", 0.0) for i in range(10)]
+    st = srv.run(reqs, clock=clk, sleep=clk.sleep)
+    assert st["requests"] == 10 and st["converged"] == 5 and st["failed"] == 5
+    assert st["statuses"] == {0: 5, 2: 5} and not st["all_converged"]
+    assert abs(st["solves_per_s"] - 5 / st["wall_s"]) < 1e-9
+    assert abs(st["requests_per_s"] - 10 / st["wall_s"]) < 1e-9
+    ok_lat = [(r.t_done - r.t_arrival) * 1e3 for r in reqs if r.fid == 0]
+    assert abs(st["p50_ms"] - float(np.percentile(ok_lat, 50))) < 1e-9
+    assert st["p99_ms_all_requests"] >= st["p99_ms"]
+
+
 def test_family_that_cannot_fit_is_rejected():
     specs = _specs([64])
     srv = SV.Server(specs, FakeBackend(FakeClock(), {0: 1}), hbm_budget=1000, s=10)
